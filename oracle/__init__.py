@@ -1,0 +1,218 @@
+"""Plain CPU FP64 oracle of the multilevel U(1) hot path (arXiv:1208.0166).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+(``paper_1208_0166_gb300``) never imports, links or calls it, and the two share no
+code.  The arithmetic lives in ``ul_oracle.c`` (plain C, compiled with
+floating-point contraction off); this module only loads it and marshals numpy
+arrays.
+
+Conventions: direction 0 is time, 1..3 are x, y, z; site index
+``i = x + L*(y + L*(z + L*t))``; angles are stored ``theta[mu*V + i]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ul_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+N_CHANNELS = 8
+CHANNEL_NAMES = ["Im E_x", "Re E_x", "Im E_y", "Re E_y", "Im E_z", "Re E_z", "Im B_x", "Re B_x"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ul_oracle.c into liboracle.so beside it (gcc, -ffp-contract=off)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(os.path.join(_HERE, "ul_oracle.h"))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    d, i, l, u64 = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_uint64
+    dp = ctypes.POINTER(ctypes.c_double)
+    up = ctypes.POINTER(ctypes.c_uint64)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.ulo_philox4x64_10.argtypes = [up, up, up]
+    lib.ulo_u53.argtypes = [u64]
+    lib.ulo_u53.restype = d
+    lib.ulo_sincos.argtypes = [d, dp, dp]
+    lib.ulo_exp.argtypes = [d]
+    lib.ulo_exp.restype = d
+    lib.ulo_atan2.argtypes = [d, d]
+    lib.ulo_atan2.restype = d
+    lib.ulo_hot_start.argtypes = [i, i, u64, dp]
+    lib.ulo_staple.argtypes = [i, i, dp, i, l, dp, dp]
+    lib.ulo_local_action.argtypes = [i, i, d, dp, i, l]
+    lib.ulo_local_action.restype = d
+    lib.ulo_metropolis_link.argtypes = [d, d, d, d, d, d, d, ip]
+    lib.ulo_metropolis_link.restype = d
+    lib.ulo_overrelax_link.argtypes = [d, d, d]
+    lib.ulo_overrelax_link.restype = d
+    lib.ulo_wrap.argtypes = [d]
+    lib.ulo_wrap.restype = d
+    lib.ulo_sweep.argtypes = [i, i, d, u64, d, dp, up, i, i, i]
+    lib.ulo_sweep.restype = l
+    lib.ulo_plaquette.argtypes = [i, i, dp]
+    lib.ulo_plaquette.restype = d
+    lib.ulo_plaquette_at.argtypes = [i, i, dp, i, i, l, dp, dp]
+    lib.ulo_polyakov.argtypes = [i, i, dp, dp]
+    lib.ulo_polyakov_correlator.argtypes = [i, i, dp, i, dp]
+    lib.ulo_field_correlator.argtypes = [i, i, dp, i, i, dp]
+    lib.ulo_multilevel.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, dp, dp, dp, dp]
+    lib.ulo_multilevel.restype = i
+    lib.ulo_gauge_transform.argtypes = [i, i, u64, dp]
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _dp_or_null(a):
+    return None if a is None else _dp(a)
+
+
+def _cplx(a: np.ndarray) -> np.ndarray:
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def philox4x64_10(ctr, key) -> np.ndarray:
+    lib = _load()
+    c = (ctypes.c_uint64 * 4)(*[int(x) for x in ctr])
+    k = (ctypes.c_uint64 * 2)(*[int(x) for x in key])
+    o = (ctypes.c_uint64 * 4)()
+    lib.ulo_philox4x64_10(c, k, o)
+    return np.array(list(o), dtype=np.uint64)
+
+
+def u53(w: int) -> float:
+    return _load().ulo_u53(int(w))
+
+
+def sincos(x: float):
+    s, c = ctypes.c_double(), ctypes.c_double()
+    _load().ulo_sincos(float(x), ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def exp(x: float) -> float:
+    return _load().ulo_exp(float(x))
+
+
+def atan2(y: float, x: float) -> float:
+    return _load().ulo_atan2(float(y), float(x))
+
+
+def wrap(theta: float) -> float:
+    return _load().ulo_wrap(float(theta))
+
+
+class Lattice:
+    """A lattice state in the oracle: angles in canonical layout plus the RNG state."""
+
+    def __init__(self, L: int, Nt: int, beta: float, seed: int, width: float = 1.0,
+                 theta: np.ndarray | None = None, metro_pass: int = 0):
+        self.L, self.Nt, self.beta, self.seed, self.width = int(L), int(Nt), float(beta), int(seed), float(width)
+        self.V = self.L ** 3 * self.Nt
+        self.metro_pass = ctypes.c_uint64(int(metro_pass))
+        if theta is None:
+            self.theta = np.empty(4 * self.V, dtype=np.float64)
+            _load().ulo_hot_start(self.L, self.Nt, self.seed, _dp(self.theta))
+        else:
+            self.theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(4 * self.V).copy()
+
+    def copy(self) -> "Lattice":
+        return Lattice(self.L, self.Nt, self.beta, self.seed, self.width, self.theta, self.metro_pass.value)
+
+    def sweep(self, n_metro: int, n_or: int, slab_t: int = 0) -> int:
+        return _load().ulo_sweep(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+                                 ctypes.byref(self.metro_pass), int(n_metro), int(n_or), int(slab_t))
+
+    def plaquette(self) -> float:
+        return _load().ulo_plaquette(self.L, self.Nt, _dp(self.theta))
+
+    def plaquette_at(self, mu: int, nu: int, i: int) -> complex:
+        re, im = ctypes.c_double(), ctypes.c_double()
+        _load().ulo_plaquette_at(self.L, self.Nt, _dp(self.theta), mu, nu, int(i), ctypes.byref(re), ctypes.byref(im))
+        return complex(re.value, im.value)
+
+    def staple(self, mu: int, i: int) -> complex:
+        re, im = ctypes.c_double(), ctypes.c_double()
+        _load().ulo_staple(self.L, self.Nt, _dp(self.theta), mu, int(i), ctypes.byref(re), ctypes.byref(im))
+        return complex(re.value, im.value)
+
+    def local_action(self, mu: int, i: int) -> float:
+        return _load().ulo_local_action(self.L, self.Nt, self.beta, _dp(self.theta), mu, int(i))
+
+    def polyakov(self) -> np.ndarray:
+        out = np.empty(2 * self.L ** 3, dtype=np.float64)
+        _load().ulo_polyakov(self.L, self.Nt, _dp(self.theta), _dp(out))
+        return _cplx(out.reshape(-1, 2))
+
+    def polyakov_correlator(self, r_max: int) -> np.ndarray:
+        out = np.empty(2 * r_max, dtype=np.float64)
+        _load().ulo_polyakov_correlator(self.L, self.Nt, _dp(self.theta), int(r_max), _dp(out))
+        return _cplx(out.reshape(-1, 2))
+
+    def field_correlator(self, r_max: int, d_max: int) -> np.ndarray:
+        out = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64)
+        _load().ulo_field_correlator(self.L, self.Nt, _dp(self.theta), int(r_max), int(d_max), _dp(out))
+        return _cplx(out.reshape(r_max, d_max + 1, N_CHANNELS, 2))
+
+    def gauge_transform(self, seed: int) -> None:
+        _load().ulo_gauge_transform(self.L, self.Nt, int(seed), _dp(self.theta))
+
+    def multilevel(self, slab_t: int, n_sub: int, r_max: int, d_max: int = -1,
+                   sub_metro: int = 1, sub_or: int = 3, record_samples: bool = False):
+        """One-level multilevel estimator; returns dict(corr, fields, vac[, samples_T])."""
+        S = self.Nt // slab_t
+        corr = np.empty(2 * r_max, dtype=np.float64)
+        fields = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64) if d_max >= 0 else None
+        vac = np.empty(N_CHANNELS, dtype=np.float64) if d_max >= 0 else None
+        samples = (np.empty(n_sub * S * self.L ** 3 * r_max * 2, dtype=np.float64)
+                   if record_samples else None)
+        rc = _load().ulo_multilevel(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+                                    ctypes.byref(self.metro_pass), int(slab_t), int(n_sub), int(sub_metro),
+                                    int(sub_or), int(r_max), int(max(d_max, 0)), _dp(corr),
+                                    _dp_or_null(fields), _dp_or_null(vac), _dp_or_null(samples))
+        if rc != 0:
+            raise ValueError("invalid multilevel arguments")
+        out = {"corr": _cplx(corr.reshape(-1, 2))}
+        if fields is not None:
+            out["fields"] = _cplx(fields.reshape(r_max, d_max + 1, N_CHANNELS, 2))
+            out["vac"] = vac
+        if samples is not None:
+            out["samples_T"] = _cplx(samples.reshape(n_sub, S, self.L ** 3, r_max, 2))
+        return out
+
+
+def metropolis_link(theta, a: complex, beta, width, u1, u2):
+    acc = ctypes.c_int()
+    t = _load().ulo_metropolis_link(float(theta), a.real, a.imag, float(beta), float(width),
+                                    float(u1), float(u2), ctypes.byref(acc))
+    return t, bool(acc.value)
+
+
+def overrelax_link(theta, a: complex) -> float:
+    return _load().ulo_overrelax_link(float(theta), a.real, a.imag)
