@@ -1,0 +1,380 @@
+"""Benchmark of the multilevel U(1) hot path on GB300 (one JSON line on stdout).
+
+A step is one configuration of the 24^4, beta = 1 workload: 100 compound sweeps
+(1 Metropolis + 3 overrelaxation passes each), one multilevel level (12 slabs of 2
+time slices, 200 sub-samples of 1 + 3 masked passes plus a measurement of the slab
+transporters and the E_x/E_y/E_z/B_x insertions at d = 0..6 for r = 1..8), the
+cross-slab products and the plaquette.  value = link updates per second (whole job);
+the correlator-sample rate and the FP32+FP64-accumulation rate are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Multi-GPU: replicas only (independent Markov chains, one per GPU, no collective on
+the data path); launched by torchrun, rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1208_0166_gb300.workloads import LARGE_24  # noqa: E402
+
+METRIC = "link updates/s and multilevel correlator samples/s at 24^4, FP32+FP64-acc vs FP64"
+UNIT = "link updates/s"
+
+W = LARGE_24
+SLAB_T = W.slab_t          # 2
+S = W.Nt // SLAB_T         # 12 slabs
+L3 = W.L ** 3
+V = W.L ** 3 * W.Nt
+UPDATES_PER_PASS_FULL = 4 * V
+UPDATES_PER_PASS_SUB = 4 * V - 3 * L3 * S      # spatial links on slab boundaries frozen
+SWEEP_UPDATES = W.therm_sweeps * (W.sweep_metro + W.sweep_or) * UPDATES_PER_PASS_FULL
+SUB_UPDATES = W.n_sub * (W.sweep_metro + W.sweep_or) * UPDATES_PER_PASS_SUB
+UPDATES_PER_STEP = SWEEP_UPDATES + SUB_UPDATES
+SAMPLES_PER_STEP = W.n_sub * S * L3 * W.r_max              # T(s, x0, r) accumulations
+INSERTION_SAMPLES_PER_STEP = SAMPLES_PER_STEP * (W.d_max + 1) * 8
+H2D_BYTES = 4 * V * 8                                       # canonical FP64 link angles
+D2H_BYTES = (2 * W.r_max + 2 * W.r_max * (W.d_max + 1) * 8 + 8) * 8 + 8  # results + plaquette
+
+# Algorithmic FP64 floating-point operations per link update of the update kernel
+# (FMA counted as 2): staple 12 complex products + sums; Metropolis adds the proposal,
+# one sincos, exp and the wrap; overrelaxation adds atan2, the wrap and one sincos.
+FLOP_STAPLE = 12 * 6 + 12
+FLOP_METRO = FLOP_STAPLE + 58 + 40 + 30 + 14
+FLOP_OR = FLOP_STAPLE + 60 + 14 + 40
+
+# Peaks.  HBM from MEASURED_PEAKS.json; ALU peaks derived from unit counts and the
+# maximum SM clock: FP64 4 flop/clk/SM (nominal 1.25 TFLOP/s), FP32 256 flop/clk/SM.
+N_SM = 152
+
+
+def _peaks():
+    p = {"hbm_gbs": 6792.4, "sm_max_mhz": 2070.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p.update({"hbm_gbs": float(m["hbm_gbs"]), "sm_max_mhz": float(m.get("sm_max_mhz", 2070.0)),
+                  "source": "measured"})
+    except Exception:
+        pass
+    clk = p["sm_max_mhz"] * 1e6
+    p["fp64_tflops"] = N_SM * 4 * clk / 1e12
+    p["fp32_tflops"] = N_SM * 256 * clk / 1e12
+    return p
+
+
+# DRAM bytes per launch of the dominant kernel from the committed ncu capture, keyed by
+# the hash of the kernel source it was taken on (null when the source has changed).
+TRAFFIC = {}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("ul_kernels.cuh", "ul_math.cuh", "ul_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1208_0166_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _config(args):
+    return {"workload": W.name + f" beta={W.beta} 100 sweeps (1 Metropolis + 3 OR) per configuration",
+            "lattice": f"{W.L}^3x{W.Nt}", "beta": W.beta, "slab_t": SLAB_T, "slabs": S, "n_sub": W.n_sub,
+            "sweeps_per_config": W.therm_sweeps, "r_max": W.r_max, "d_max": W.d_max,
+            "insertions": "E_x,E_y,E_z,B_x (Im and Re) on the mid-plane", "precision": args.precision,
+            "l2": "flushed between steps (256 MiB write); the lattice itself is L2-resident by design",
+            "start": "hot start (Philox seed 1 + rank); synthetic, no stored ensemble",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def cpu_baseline_sample():
+    """The oracle on a bounded sample of the workload: one full compound sweep plus one
+    masked sub-sample (1 + 3 passes) and its transporter measurement at 24^4."""
+    import oracle as O
+
+    lat = O.Lattice(W.L, W.Nt, W.beta, 1)
+    t0 = time.perf_counter()
+    lat.sweep(W.sweep_metro, W.sweep_or)
+    lat.multilevel(SLAB_T, 1, W.r_max, sub_metro=W.sweep_metro, sub_or=W.sweep_or)
+    dt = time.perf_counter() - t0
+    updates = (W.sweep_metro + W.sweep_or) * (UPDATES_PER_PASS_FULL + UPDATES_PER_PASS_SUB)
+    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"24^4: 1 compound sweep + 1 masked sub-sample with T measurement "
+                      f"({updates} link updates, {dt:.1f} s, single thread)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    O.build()
+    lat = O.Lattice(W.L, W.Nt, W.beta, 1)
+    per_step = (W.sweep_metro + W.sweep_or) * UPDATES_PER_PASS_SUB
+
+    def step():
+        lat.multilevel(SLAB_T, 1, W.r_max, sub_metro=W.sweep_metro, sub_or=W.sweep_or)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    sample = (f"24^4 beta=1: per step one masked sub-sample (1 Metropolis + 3 OR over the "
+              f"{UPDATES_PER_PASS_SUB} unfrozen links) and its slab-transporter measurement, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
+    """Returns dict with timings for K steps of the workload at precision prec."""
+    stream = torch.cuda.current_stream()
+    lat = lib.Lattice(W.L, W.Nt, W.beta, 1 + rank, prec)
+    lat.set_stream(stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        for _ in range(W.therm_sweeps):
+            lat.sweep(W.sweep_metro, W.sweep_or)
+        e_mid = torch.cuda.Event(enable_timing=True)
+        e_mid.record(stream)
+        res = lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+        plaq = lat.plaquette()
+        return e_mid, res, plaq
+
+    for _ in range(Wm):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lat.launch_count()
+    total_ms, sweep_ms, step_ms = 0.0, 0.0, []
+    last = None
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e_mid, res, plaq = step()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e2)
+        total_ms += ms
+        sweep_ms += e0.elapsed_time(e_mid)
+        step_ms.append(ms)
+        last = (res, plaq)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = lat.launch_count() - launches0
+    out = {"total_ms": total_ms, "sweep_ms": sweep_ms, "step_ms": step_ms, "launches": launches,
+           "corr": last[0]["corr"], "plaquette": last[1]}
+    if e2e:
+        import numpy as np
+
+        theta0 = lat.get_links()
+        pinned = torch.empty(4 * V, dtype=torch.float64, pin_memory=True)
+        host = pinned.numpy()
+        host[:] = theta0
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            lat.set_links(host)
+            for _ in range(W.therm_sweeps):
+                lat.sweep(W.sweep_metro, W.sweep_or)
+            r = lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+            p = lat.plaquette()
+            assert np.isfinite(r["corr"]).all() and np.isfinite(p)
+        torch.cuda.synchronize()
+        out["e2e_s"] = time.perf_counter() - t0
+    lat.close()
+    return out
+
+
+def run_ours(args):
+    ws, rank, local = _dist()
+    import torch
+
+    dist = None
+    if ws > 1:
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    from paper_1208_0166_gb300 import _lib as lib
+
+    lib.load()
+    prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
+    K, Wm = args.steps, args.warmup
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    main = _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib)
+    clk = clocks.stop()
+
+    def gmax(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    total_s = gmax(main["total_ms"]) / 1e3
+    e2e_s = gmax(main["e2e_s"])
+    value = UPDATES_PER_STEP * K * ws / total_s
+    samples = SAMPLES_PER_STEP * K * ws / total_s
+
+    compare = None
+    if not args.no_compare:
+        other = lib.UL_FP32_ACC64 if prec == lib.UL_FP64 else lib.UL_FP64
+        o = _run_gpu(args, other, K, Wm, rank, ws, dist, torch, lib, e2e=False)
+        o_s = gmax(o["total_ms"]) / 1e3
+        compare = {"precision": "fp32_acc64" if other == lib.UL_FP32_ACC64 else "fp64",
+                   "value": UPDATES_PER_STEP * K * ws / o_s, "unit": UNIT,
+                   "correlator_samples_per_s": SAMPLES_PER_STEP * K * ws / o_s,
+                   "ms_per_step": o_s / K * 1e3, "gpu_launches": o["launches"],
+                   "C_r": [[z.real, z.imag] for z in o["corr"][:4]]}
+
+    peaks = _peaks()
+    update_launches = W.therm_sweeps * (W.sweep_metro + W.sweep_or) * 8
+    avg_launch_s = main["sweep_ms"] / 1e3 / (K * update_launches)
+    flops_per_launch = (UPDATES_PER_PASS_FULL / 8) * (
+        W.sweep_metro * FLOP_METRO + W.sweep_or * FLOP_OR) / (W.sweep_metro + W.sweep_or)
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    peak = peaks["fp64_tflops"] if prec == lib.UL_FP64 else peaks["fp32_tflops"]
+    kname = "update_class_kernel<%s>" % ("double" if prec == lib.UL_FP64 else "float")
+    traffic = TRAFFIC.get((kname, _kernel_hash()))
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x %s flop/clk x %.0f MHz" % (
+                    "4 FP64" if prec == lib.UL_FP64 else "256 FP32", peaks["sm_max_mhz"]),
+                "avg_launch_us": avg_launch_s * 1e6, "flop_per_launch": flops_per_launch,
+                "l2_equiv_gbs": (UPDATES_PER_PASS_FULL / 8) * (72 if prec == lib.UL_FP64 else 36)
+                / avg_launch_s / 1e9}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline_sample()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": total_s / K * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)",
+            "data": "synthetic", "config": _config(args),
+            "correlator_samples_per_s": samples, "insertion_samples_per_s": INSERTION_SAMPLES_PER_STEP * K * ws / total_s,
+            "link_updates_per_step": UPDATES_PER_STEP, "compare": compare,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": UPDATES_PER_STEP * K * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H2D_BYTES,
+                    "d2h_bytes_per_step": D2H_BYTES},
+            "gpu_launches": main["launches"], "clocks": clk,
+            "observables": {"C_r": [[z.real, z.imag] for z in main["corr"][:4]], "plaquette": main["plaquette"]}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * ul.h — C ABI of libul: the Luscher–Weisz multilevel hot path for 4D compact U(1)
+ * lattice gauge theory with the Wilson action, on one GB300 GPU (sm_103a).
+ *
+ * Method: A. Amado, N. Cardoso, M. Cardoso, P. Bicudo, "Study of compact U(1) flux
+ * tubes in 3+1 dimensions in lattice gauge theory using GPU's", arXiv:1208.0166.
+ *
+ * Conventions used by every entry point
+ *   - Direction mu = 0 is time (the paper writes U_0 for temporal links), mu = 1,2,3
+ *     are x, y, z.  The lattice is L^3 x Nt, periodic in all directions.
+ *   - Canonical host layout of link angles: theta[mu*V + i], V = L^3 Nt,
+ *     i = x + L*(y + L*(z + L*t)); U_mu(x) = exp(i theta_mu(x)), theta in [-pi, pi).
+ *   - Every call returns UL_OK (0) or a negative status.  On error nothing is written
+ *     to the caller's output buffers; ul_last_error() gives a text.  A handle stays
+ *     valid after an error (except UL_ENOMEM from ul_init, which sets *h = NULL).
+ *   - The library owns all device memory and the handle; the caller owns every host
+ *     buffer it passes (outputs are written before the call returns).
+ *   - Calls on one handle are serialised on the handle's CUDA stream.  Calls that return
+ *     results (ul_multilevel*, ul_plaquette, ul_get_*) block until the results are on
+ *     the host.  ul_sweep and ul_set_state only enqueue work and return; an execution
+ *     error of enqueued work is reported by the next blocking call.  Different handles
+ *     may be used from different host threads.
+ */
+#ifndef UL_H
+#define UL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ul_lattice ul_lattice; /* opaque, library-owned */
+
+enum {
+    UL_OK = 0,
+    UL_EINVAL = -1,   /* an argument is out of range (message says which) */
+    UL_ENOMEM = -2,   /* device memory could not be allocated */
+    UL_ECUDA = -3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    UL_ETIMEOUT = -4, /* a device-side bounded wait gave up */
+    UL_ESTATE = -5    /* the handle is not in a state that allows the call */
+};
+
+enum {
+    UL_FP64 = 0,      /* link angles, updates and accumulation in FP64 */
+    UL_FP32_ACC64 = 1 /* link angles and updates in FP32; measurement products,
+                         slab accumulators, cross-slab products and reductions in FP64 */
+};
+
+/*
+ * ul_init — create a lattice L^3 x Nt at coupling beta with a hot start.
+ * Section 2 (Wilson action beta S = beta sum_x sum_{mu<nu}[1 - Re U_mu nu(x)],
+ * beta = 1/g^2) and Section 2.1 (configurations of an isotropic lattice).
+ * Hot start: theta_mu(x) = -pi + 2 pi u, u = (w0 >> 11) 2^-53 with w0 the first word of
+ * Philox4x64-10(counter = (mu V + i, 0, 0, 0), key = (seed, 0)).
+ * L, Nt: even, >= 2 (checkerboard), L^3 Nt <= 2^28.  beta >= 0.
+ * ul_init is ul_init_ex(..., UL_FP64).
+ */
+int ul_init(ul_lattice** h, int L, int Nt, double beta, uint64_t seed);
+int ul_init_ex(ul_lattice** h, int L, int Nt, double beta, uint64_t seed, int precision);
+
+/*
+ * ul_sweep — n_metro Metropolis passes then n_or overrelaxation passes over the whole
+ * lattice (Section 2.1: configurations are generated with Metropolis and overrelaxation).
+ * A pass updates the 8 classes (mu = 0..3) x (even, odd sites) in that order; links of
+ * one class share no plaquette and are updated in parallel.
+ *   Metropolis: theta' = wrap(theta + w (2 u1 - 1)), w = option "metro_width" (1.0);
+ *     accept iff u2 < exp(-dS), dS = -beta Re[(e^{i theta'} - e^{i theta}) A], with A the
+ *     staple sum of the link; u1, u2 from words 0, 1 of Philox4x64-10(counter =
+ *     (mu V + i, pass, 0, 0), key = (seed, 1)), pass = number of earlier Metropolis passes.
+ *   Overrelaxation: theta' = wrap(-2 arg(A) - theta) (leaves Re(e^{i theta} A) unchanged).
+ * n_metro, n_or >= 0.  Returns once the passes are enqueued on the handle's stream.
+ */
+int ul_sweep(ul_lattice* h, int n_metro, int n_or);
+
+/*
+ * ul_multilevel — one level of the Luscher–Weisz multilevel algorithm (Section 2.2: the
+ * lattice is cut into time layers whose spatial boundary links are held fixed while
+ * the remaining links are updated many times) for the Polyakov-loop
+ * correlator <P*(0) P(r)> of Section 2.2 (the estimator of V(r) = -(1/Nt) ln <P*P>).
+ * The lattice is cut into S = Nt/slab_t time slabs; spatial links on slices
+ * t = 0 mod slab_t stay frozen.  n_sub times: options "sub_metro" Metropolis plus
+ * "sub_or" overrelaxation passes (defaults 1 and 3) of the unfrozen links, then a
+ * measurement of the slab transporters
+ *     T(s, x0, r) = prod_{t in slab s} U*_0(x0, t) U_0(x0 + r xhat, t).
+ * out (caller-owned host, 2*r_max doubles) receives (re, im) of
+ *     C(r) = (1/L^3) sum_x0 prod_s <T(s, x0, r)>,  r = 1..r_max,
+ * <.> the mean over the n_sub measurements.  The links keep the last sub-sample state.
+ * slab_t >= 1 divides Nt; n_sub >= 1; 1 <= r_max <= L/2.
+ */
+int ul_multilevel(ul_lattice* h, int slab_t, int n_sub, int r_max, double* out);
+
+/*
+ * ul_multilevel_fields — ul_multilevel plus the field insertions of Section 2.2
+ * (operator O(x0,x,t,r) = U*_0(x0,t) U_0(x0+r,t) O(x,t); per slab the insertion term is
+ * T(s,x0,r) * sum_{t in slab} O(x,t), the general-thickness form of TO^(2); the
+ * estimator <P*(0) P(r) O(x)> = (1/V) sum_x0 sum_s <T O>_s prod_{s' != s} <T>_s').
+ * The operator sits on the plaquette with lower corner x = x0 + floor(r/2) xhat + d yhat,
+ * d = 0..d_max, in channel ch = 2c + part: c = 0 (t,x) plane E_x, 1 (t,y) E_y, 2 (t,z)
+ * E_z, 3 (y,z) B_x; part 0 = Im P (a^2 F = sqrt(beta) Im P), 1 = Re P (for
+ * a^4 F^2 = beta (1 - Re P)).
+ *   out_corr  : 2*r_max doubles, as ul_multilevel;
+ *   out_fields: 2*r_max*(d_max+1)*8 doubles, layout [r-1][d][ch][re, im];
+ *   out_vac   : 8 doubles (may be NULL), <O_ch> over all sites, slices and sub-samples,
+ *               the subtraction term <O> of the connected average.
+ * 0 <= d_max < L.
+ */
+int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max,
+                         double* out_corr, double* out_fields, double* out_vac);
+
+/* ul_plaquette — *out = <Re U_p> = (1/6V) sum_x sum_{mu<nu} Re U_mu nu(x) (Section 2),
+ * accumulated in FP64 in a fixed order (bitwise reproducible). */
+int ul_plaquette(ul_lattice* h, double* out);
+
+/* ul_free — release the handle and its device memory.  NULL is accepted. */
+int ul_free(ul_lattice* h);
+
+/*
+ * ul_set_option — set a run option (double value):
+ *   "metro_width"  half-width of the Metropolis proposal in rad (> 0, default 1.0)
+ *   "sub_metro"    Metropolis passes per multilevel sub-sample (>= 0, default 1)
+ *   "sub_or"       overrelaxation passes per multilevel sub-sample (>= 0, default 3)
+ *   "beta"         coupling (>= 0)
+ */
+int ul_set_option(ul_lattice* h, const char* key, double value);
+
+/* ul_get_links / ul_set_links — copy all 4V angles to / from a caller-owned host buffer
+ * in the canonical layout, as FP64 (FP32 lattices are widened / rounded to nearest).
+ * ul_set_links wraps nothing: inputs must lie in [-pi, pi). */
+int ul_get_links(ul_lattice* h, double* theta_host);
+int ul_set_links(ul_lattice* h, const double* theta_host);
+
+/* ul_get_state / ul_set_state — the random-number state: seed and the count of
+ * Metropolis passes done (the second Philox counter word).  With the links this is
+ * the whole state: a restored state continues bit-identically. */
+int ul_get_state(ul_lattice* h, uint64_t* seed, uint64_t* metro_pass);
+int ul_set_state(ul_lattice* h, uint64_t seed, uint64_t metro_pass);
+
+/* ul_get_stats — accepted Metropolis hits and proposed hits since ul_init. */
+int ul_get_stats(ul_lattice* h, uint64_t* accepted, uint64_t* proposed);
+
+/* ul_get_launch_count — number of CUDA kernels launched for this handle since ul_init. */
+int ul_get_launch_count(ul_lattice* h, uint64_t* launches);
+
+/* ul_synchronize — wait for all work enqueued on the handle's stream; reports
+ * execution errors of earlier ul_sweep calls. */
+int ul_synchronize(ul_lattice* h);
+
+/* ul_set_stream — run this handle's work on the caller's CUDA stream (a cudaStream_t,
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL returns to the handle's own stream. */
+int ul_set_stream(ul_lattice* h, void* cuda_stream);
+
+/* ul_last_error — text of the last error on h (or of the last failed ul_init if h is NULL). */
+const char* ul_last_error(const ul_lattice* h);
+
+/* ul_precision — UL_FP64 or UL_FP32_ACC64 for this handle (negative status on NULL). */
+int ul_precision(const ul_lattice* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -77,6 +77,7 @@ def _load():
     lib.ulo_polyakov.argtypes = [i, i, dp, dp]
     lib.ulo_polyakov_correlator.argtypes = [i, i, dp, i, dp]
     lib.ulo_field_correlator.argtypes = [i, i, dp, i, i, dp]
+    lib.ulo_field_correlator_one.argtypes = [i, i, dp, i, i, i, dp, dp]
     lib.ulo_multilevel.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, dp, dp, dp, dp]
     lib.ulo_multilevel.restype = i
     lib.ulo_gauge_transform.argtypes = [i, i, u64, dp]
@@ -179,6 +180,12 @@ class Lattice:
         out = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64)
         _load().ulo_field_correlator(self.L, self.Nt, _dp(self.theta), int(r_max), int(d_max), _dp(out))
         return _cplx(out.reshape(r_max, d_max + 1, N_CHANNELS, 2))
+
+    def field_correlator_one(self, r: int, d: int, ch: int) -> complex:
+        re, im = ctypes.c_double(), ctypes.c_double()
+        _load().ulo_field_correlator_one(self.L, self.Nt, _dp(self.theta), int(r), int(d), int(ch),
+                                         ctypes.byref(re), ctypes.byref(im))
+        return complex(re.value, im.value)
 
     def gauge_transform(self, seed: int) -> None:
         _load().ulo_gauge_transform(self.L, self.Nt, int(seed), _dp(self.theta))

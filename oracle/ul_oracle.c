@@ -553,6 +553,23 @@ void ulo_field_correlator(int L, int Nt, const double* theta, int r_max, int d_m
             }
 }
 
+/* One element of the direct field correlator (same definition, one (r, d, ch)). */
+void ulo_field_correlator_one(int L, int Nt, const double* theta, int r, int d, int ch, double* re, double* im)
+{
+    lat_t g = mk(L, Nt);
+    long L3 = (long)L * L * L;
+    cplx sum = cmk(0.0, 0.0);
+    for (long x0 = 0; x0 < L3; x0++) {
+        cplx pp = cmul(cconj(polyakov_at(&g, theta, x0)), polyakov_at(&g, theta, spatial_shift(&g, x0, r, 0)));
+        long y = spatial_shift(&g, x0, r / 2, d);
+        for (int t = 0; t < Nt; t++)
+            sum = cadd(sum, cscale(pp, channel_value(&g, theta, ch, spatial_to_site(&g, y, t))));
+    }
+    sum = cdivr(sum, (double)g.V);
+    *re = sum.re;
+    *im = sum.im;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One-level multilevel estimator (Section 2.2)                              */
 /* ------------------------------------------------------------------------ */

@@ -81,6 +81,9 @@ void ulo_polyakov_correlator(int L, int Nt, const double* theta, int r_max, doub
  * out: 2 * r_max * (d_max+1) * 8, layout [r-1][d][ch][re,im]. */
 void ulo_field_correlator(int L, int Nt, const double* theta, int r_max, int d_max, double* out);
 
+/* One element (r, d, ch) of the direct field correlator. */
+void ulo_field_correlator_one(int L, int Nt, const double* theta, int r, int d, int ch, double* re, double* im);
+
 /*
  * One-level Luscher-Weisz multilevel estimator (Section 2.2, Eqs. for V(r),
  * the insertion operator and the multilevel field average).

@@ -1,0 +1,175 @@
+"""ctypes binding of libul.so (include/ul.h), the CUDA multilevel library.
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1208_0166_gb300.build``); if it is missing or cannot load,
+``load()`` raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+UL_OK, UL_EINVAL, UL_ENOMEM, UL_ECUDA, UL_ETIMEOUT, UL_ESTATE = 0, -1, -2, -3, -4, -5
+UL_FP64, UL_FP32_ACC64 = 0, 1
+N_CHANNELS = 8
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libul.so")
+
+_lib = None
+
+# (name, restype, argtypes) of every function declared in include/ul.h
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_U64 = ctypes.c_uint64
+_DP = ctypes.POINTER(ctypes.c_double)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+SIGNATURES = [
+    ("ul_init", _I, [ctypes.POINTER(_P), _I, _I, _D, _U64]),
+    ("ul_init_ex", _I, [ctypes.POINTER(_P), _I, _I, _D, _U64, _I]),
+    ("ul_sweep", _I, [_P, _I, _I]),
+    ("ul_multilevel", _I, [_P, _I, _I, _I, _DP]),
+    ("ul_multilevel_fields", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
+    ("ul_plaquette", _I, [_P, _DP]),
+    ("ul_free", _I, [_P]),
+    ("ul_set_option", _I, [_P, ctypes.c_char_p, _D]),
+    ("ul_get_links", _I, [_P, _DP]),
+    ("ul_set_links", _I, [_P, _DP]),
+    ("ul_get_state", _I, [_P, _U64P, _U64P]),
+    ("ul_set_state", _I, [_P, _U64, _U64]),
+    ("ul_get_stats", _I, [_P, _U64P, _U64P]),
+    ("ul_get_launch_count", _I, [_P, _U64P]),
+    ("ul_synchronize", _I, [_P]),
+    ("ul_set_stream", _I, [_P, _P]),
+    ("ul_last_error", ctypes.c_char_p, [_P]),
+    ("ul_precision", _I, [_P]),
+]
+
+
+class ULError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libul.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _check(rc: int, handle=None):
+    if rc != UL_OK:
+        msg = load().ul_last_error(handle).decode(errors="replace")
+        raise ULError(rc, msg)
+
+
+class Lattice:
+    """A lattice owned by libul (one handle).  Methods mirror the C entry points."""
+
+    def __init__(self, L: int, Nt: int, beta: float, seed: int, precision: int = UL_FP64):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.ul_init_ex(ctypes.byref(h), int(L), int(Nt), float(beta), int(seed), int(precision)))
+        self._h = h
+        self.L, self.Nt, self.beta, self.seed, self.precision = int(L), int(Nt), float(beta), int(seed), int(precision)
+        self.V = self.L ** 3 * self.Nt
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ul_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sweep(self, n_metro: int, n_or: int) -> None:
+        _check(load().ul_sweep(self._h, int(n_metro), int(n_or)), self._h)
+
+    def multilevel(self, slab_t: int, n_sub: int, r_max: int) -> np.ndarray:
+        out = np.zeros(2 * r_max)
+        _check(load().ul_multilevel(self._h, int(slab_t), int(n_sub), int(r_max), _dp(out)), self._h)
+        return out[0::2] + 1j * out[1::2]
+
+    def multilevel_fields(self, slab_t: int, n_sub: int, r_max: int, d_max: int):
+        corr = np.zeros(2 * r_max)
+        fields = np.zeros(2 * r_max * (d_max + 1) * N_CHANNELS)
+        vac = np.zeros(N_CHANNELS)
+        _check(load().ul_multilevel_fields(self._h, int(slab_t), int(n_sub), int(r_max), int(d_max), _dp(corr),
+                                           _dp(fields), _dp(vac)), self._h)
+        f = fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)
+        return {"corr": corr[0::2] + 1j * corr[1::2], "fields": f[..., 0] + 1j * f[..., 1], "vac": vac}
+
+    def plaquette(self) -> float:
+        v = ctypes.c_double()
+        _check(load().ul_plaquette(self._h, ctypes.byref(v)), self._h)
+        return v.value
+
+    def set_option(self, key: str, value: float) -> None:
+        _check(load().ul_set_option(self._h, key.encode(), float(value)), self._h)
+
+    def get_links(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(4 * self.V)
+        assert out.dtype == np.float64 and out.size == 4 * self.V and out.flags["C_CONTIGUOUS"]
+        _check(load().ul_get_links(self._h, _dp(out)), self._h)
+        return out
+
+    def set_links(self, theta: np.ndarray) -> None:
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        assert theta.size == 4 * self.V
+        _check(load().ul_set_links(self._h, _dp(theta)), self._h)
+
+    def get_state(self):
+        s, p = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().ul_get_state(self._h, ctypes.byref(s), ctypes.byref(p)), self._h)
+        return s.value, p.value
+
+    def set_state(self, seed: int, metro_pass: int) -> None:
+        _check(load().ul_set_state(self._h, int(seed), int(metro_pass)), self._h)
+
+    def stats(self):
+        a, p = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().ul_get_stats(self._h, ctypes.byref(a), ctypes.byref(p)), self._h)
+        return a.value, p.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_uint64()
+        _check(load().ul_get_launch_count(self._h, ctypes.byref(n)), self._h)
+        return n.value
+
+    def synchronize(self) -> None:
+        _check(load().ul_synchronize(self._h), self._h)
+
+    def set_stream(self, cuda_stream: int | None) -> None:
+        _check(load().ul_set_stream(self._h, ctypes.c_void_p(cuda_stream or 0)), self._h)

@@ -1,0 +1,401 @@
+// ul_api.cu — the C ABI declared in include/ul.h: handle life cycle, argument checks,
+// device memory, the host-side schedule of sweeps and multilevel levels, and copies of
+// results to caller-owned host buffers.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/ul.h"
+#include "ul_device.cuh"
+#include "ul_internal.h"
+
+struct ul_lattice {
+    ul::Geo g{};
+    int precision = UL_FP64;
+    double beta = 0.0;
+    uint64_t seed = 0;
+    uint64_t metro_pass = 0;
+    double width = 1.0;
+    int sub_metro = 1;
+    int sub_or = 3;
+    uint64_t proposed = 0;
+    uint64_t launches = 0; // kernels launched on behalf of this handle
+
+    void* theta = nullptr; // R[4][2][Vh]
+    void* cs = nullptr;    // (cos, sin) per link, same layout
+    double* canon = nullptr;          // 4V doubles, layout conversion staging
+    unsigned long long* d_accepted = nullptr;
+    double* d_scalar = nullptr;       // small device outputs (plaquette)
+    double* plaq_partials = nullptr;
+
+    // multilevel scratch, grown on demand
+    void* ml_buf = nullptr;
+    size_t ml_bytes = 0;
+
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+int fail(ul_lattice* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(ul_lattice* h, cudaError_t e, const char* what)
+{
+    std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? UL_ENOMEM : UL_ECUDA, msg);
+}
+
+#define UL_CK(h, call)                                                                                          \
+    do {                                                                                                        \
+        cudaError_t e_ = (call);                                                                                \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);                                                \
+    } while (0)
+
+size_t real_size(const ul_lattice* h) { return h->precision == UL_FP64 ? sizeof(double) : sizeof(float); }
+
+bool is_f64(const ul_lattice* h) { return h->precision == UL_FP64; }
+
+void release(ul_lattice* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->theta);
+    cudaFree(h->cs);
+    cudaFree(h->canon);
+    cudaFree(h->d_accepted);
+    cudaFree(h->d_scalar);
+    cudaFree(h->plaq_partials);
+    cudaFree(h->ml_buf);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+int ensure_ml(ul_lattice* h, size_t bytes)
+{
+    if (bytes <= h->ml_bytes) return UL_OK;
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(h->ml_buf);
+    h->ml_buf = nullptr;
+    h->ml_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->ml_buf, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, UL_ENOMEM, "multilevel accumulators: cannot allocate " + std::to_string(bytes) + " bytes");
+    }
+    h->ml_bytes = bytes;
+    return UL_OK;
+}
+
+int update_pass(ul_lattice* h, bool metro, int slab_t)
+{
+    for (int mu = 0; mu < 4; ++mu)
+        for (int par = 0; par < 2; ++par) {
+            cudaError_t e = is_f64(h)
+                ? ul::launch_update_class<double>(h->g, static_cast<double*>(h->theta), h->cs, mu, par, metro,
+                                                  h->metro_pass, h->seed, h->beta, h->width, slab_t, h->d_accepted,
+                                                  h->stream)
+                : ul::launch_update_class<float>(h->g, static_cast<float*>(h->theta), h->cs, mu, par, metro,
+                                                 h->metro_pass, h->seed, h->beta, h->width, slab_t, h->d_accepted,
+                                                 h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
+            h->launches += 1;
+        }
+    if (metro) {
+        long updatable = 4L * h->g.V;
+        if (slab_t > 0) updatable -= 3L * h->g.L3 * (h->g.Nt / slab_t);
+        h->proposed += static_cast<uint64_t>(updatable);
+        h->metro_pass += 1;
+    }
+    return UL_OK;
+}
+
+int compound_sweep(ul_lattice* h, int n_metro, int n_or, int slab_t)
+{
+    for (int k = 0; k < n_metro; ++k) {
+        int rc = update_pass(h, true, slab_t);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < n_or; ++k) {
+        int rc = update_pass(h, false, slab_t);
+        if (rc) return rc;
+    }
+    return UL_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int precision)
+{
+    if (!out) return fail(nullptr, UL_EINVAL, "ul_init: handle pointer is NULL");
+    *out = nullptr;
+    if (L < 2 || Nt < 2 || (L & 1) || (Nt & 1))
+        return fail(nullptr, UL_EINVAL, "ul_init: L and Nt must be even and >= 2");
+    const long long V = static_cast<long long>(L) * L * L * Nt;
+    if (V > (1LL << 28)) return fail(nullptr, UL_EINVAL, "ul_init: L^3 Nt must not exceed 2^28");
+    if (!(beta >= 0.0)) return fail(nullptr, UL_EINVAL, "ul_init: beta must be >= 0");
+    if (precision != UL_FP64 && precision != UL_FP32_ACC64)
+        return fail(nullptr, UL_EINVAL, "ul_init: precision must be UL_FP64 or UL_FP32_ACC64");
+
+    ul_lattice* h = new (std::nothrow) ul_lattice();
+    if (!h) return fail(nullptr, UL_ENOMEM, "ul_init: host allocation failed");
+    h->g.L = L;
+    h->g.Nt = Nt;
+    h->g.Lh = L / 2;
+    h->g.L3 = L * L * L;
+    h->g.V = static_cast<int>(V);
+    h->g.Vh = static_cast<int>(V / 2);
+    h->precision = precision;
+    h->beta = beta;
+    h->seed = seed;
+
+    auto bail = [&](cudaError_t e, const char* what) {
+        std::string msg = std::string("ul_init: ") + what + ": " + cudaGetErrorString(e);
+        cudaGetLastError();
+        release(h);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? UL_ENOMEM : UL_ECUDA, msg);
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+    h->stream = h->own_stream;
+    const size_t nlink = 4ull * static_cast<size_t>(V);
+    const size_t rs = real_size(h);
+    if ((e = cudaMalloc(&h->theta, nlink * rs)) != cudaSuccess) return bail(e, "link angles");
+    if ((e = cudaMalloc(&h->cs, nlink * 2 * rs)) != cudaSuccess) return bail(e, "link phases");
+    if ((e = cudaMalloc(&h->canon, nlink * sizeof(double))) != cudaSuccess) return bail(e, "staging buffer");
+    if ((e = cudaMalloc(&h->d_accepted, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "counters");
+    if ((e = cudaMalloc(&h->d_scalar, 16 * sizeof(double))) != cudaSuccess) return bail(e, "scalars");
+    if ((e = cudaMalloc(&h->plaq_partials, ul::plaquette_partials(h->g) * sizeof(double))) != cudaSuccess)
+        return bail(e, "plaquette partials");
+    if ((e = cudaMemsetAsync(h->d_accepted, 0, sizeof(unsigned long long), h->stream)) != cudaSuccess)
+        return bail(e, "memset");
+    e = is_f64(h) ? ul::launch_hot_start<double>(h->g, static_cast<double*>(h->theta), h->cs, seed, h->stream)
+                  : ul::launch_hot_start<float>(h->g, static_cast<float*>(h->theta), h->cs, seed, h->stream);
+    if (e != cudaSuccess) return bail(e, "hot start launch");
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "hot start");
+    *out = h;
+    return UL_OK;
+}
+
+int ul_init(ul_lattice** out, int L, int Nt, double beta, uint64_t seed)
+{
+    return ul_init_ex(out, L, Nt, beta, seed, UL_FP64);
+}
+
+int ul_free(ul_lattice* h)
+{
+    release(h);
+    return UL_OK;
+}
+
+int ul_sweep(ul_lattice* h, int n_metro, int n_or)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_sweep: NULL handle");
+    if (n_metro < 0 || n_or < 0) return fail(h, UL_EINVAL, "ul_sweep: pass counts must be >= 0");
+    return compound_sweep(h, n_metro, n_or, 0);
+}
+
+int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max, double* out_corr,
+                         double* out_fields, double* out_vac)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_multilevel: NULL handle");
+    const ul::Geo& g = h->g;
+    if (slab_t < 1 || g.Nt % slab_t != 0) return fail(h, UL_EINVAL, "ul_multilevel: slab_t must divide Nt");
+    if (g.Nt / slab_t > ul::kMaxSlabs) return fail(h, UL_EINVAL, "ul_multilevel: more than 256 slabs");
+    if (n_sub < 1) return fail(h, UL_EINVAL, "ul_multilevel: n_sub must be >= 1");
+    if (r_max < 1 || r_max > g.L / 2) return fail(h, UL_EINVAL, "ul_multilevel: r_max must be in [1, L/2]");
+    if (!out_corr) return fail(h, UL_EINVAL, "ul_multilevel: output pointer is NULL");
+    const bool fields = out_fields != nullptr;
+    if (fields && (d_max < 0 || d_max >= g.L)) return fail(h, UL_EINVAL, "ul_multilevel: d_max must be in [0, L)");
+    const int nd = fields ? d_max + 1 : 0;
+    const int S = g.Nt / slab_t;
+
+    // Scratch layout (bytes): asum | bsum | O | osum | partials | out
+    const size_t n_a = static_cast<size_t>(S) * r_max * g.L3;
+    const size_t n_b = n_a * nd * 8;
+    const size_t n_o = fields ? 8ull * S * g.L3 : 0;
+    const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
+    const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
+    const size_t bytes = (n_a + n_b) * sizeof(double2) + (2 * n_o + n_p + n_out) * sizeof(double);
+    int rc = ensure_ml(h, bytes);
+    if (rc) return rc;
+    double2* asum = static_cast<double2*>(h->ml_buf);
+    double2* bsum = asum + n_a;
+    double* O = reinterpret_cast<double*>(bsum + n_b);
+    double* osum = O + n_o;
+    double* partials = osum + n_o;
+    double* dout = partials + n_p;
+    UL_CK(h, cudaMemsetAsync(asum, 0, (n_a + n_b) * sizeof(double2), h->stream));
+    if (fields) UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
+
+    for (int k = 0; k < n_sub; ++k) {
+        rc = compound_sweep(h, h->sub_metro, h->sub_or, slab_t);
+        if (rc) return rc;
+        cudaError_t e;
+        if (fields) {
+            e = is_f64(h) ? ul::launch_slab_channels<double>(g, h->cs, slab_t, O, osum, h->stream)
+                          : ul::launch_slab_channels<float>(g, h->cs, slab_t, O, osum, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "slab channel launch");
+            h->launches += 1;
+        }
+        e = is_f64(h) ? ul::launch_measure<double>(g, h->cs, slab_t, r_max, nd, O, asum, fields ? bsum : nullptr, h->stream)
+                      : ul::launch_measure<float>(g, h->cs, slab_t, r_max, nd, O, asum, fields ? bsum : nullptr, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
+        h->launches += 1;
+    }
+    cudaError_t e = ul::launch_ml_reduce(g, slab_t, n_sub, r_max, nd, asum, bsum, fields ? osum : nullptr, partials,
+                                         dout, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
+    h->launches += fields ? 3 : 2;
+    double* host = static_cast<double*>(std::malloc(n_out * sizeof(double)));
+    if (!host) return fail(h, UL_ENOMEM, "ul_multilevel: host staging allocation failed");
+    e = cudaMemcpyAsync(host, dout, n_out * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        std::free(host);
+        return cuda_fail(h, e, "ul_multilevel: result copy");
+    }
+    std::memcpy(out_corr, host, 2ull * r_max * sizeof(double));
+    if (fields) {
+        std::memcpy(out_fields, host + 2 * r_max, 2ull * r_max * nd * 8 * sizeof(double));
+        if (out_vac) std::memcpy(out_vac, host + 2 * r_max + 2 * r_max * nd * 8, 8 * sizeof(double));
+    }
+    std::free(host);
+    return UL_OK;
+}
+
+int ul_multilevel(ul_lattice* h, int slab_t, int n_sub, int r_max, double* out)
+{
+    return ul_multilevel_fields(h, slab_t, n_sub, r_max, -1, out, nullptr, nullptr);
+}
+
+int ul_plaquette(ul_lattice* h, double* out)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_plaquette: NULL handle");
+    if (!out) return fail(h, UL_EINVAL, "ul_plaquette: output pointer is NULL");
+    cudaError_t e = is_f64(h) ? ul::launch_plaquette<double>(h->g, h->cs, h->plaq_partials, h->d_scalar, h->stream)
+                              : ul::launch_plaquette<float>(h->g, h->cs, h->plaq_partials, h->d_scalar, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "plaquette launch");
+    h->launches += 2;
+    double v = 0.0;
+    UL_CK(h, cudaMemcpyAsync(&v, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    *out = v;
+    return UL_OK;
+}
+
+int ul_set_option(ul_lattice* h, const char* key, double v)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_set_option: NULL handle");
+    if (!key) return fail(h, UL_EINVAL, "ul_set_option: NULL key");
+    if (!std::strcmp(key, "metro_width")) {
+        if (!(v > 0.0)) return fail(h, UL_EINVAL, "metro_width must be > 0");
+        h->width = v;
+    } else if (!std::strcmp(key, "sub_metro")) {
+        if (!(v >= 0.0) || v != static_cast<int>(v)) return fail(h, UL_EINVAL, "sub_metro must be an integer >= 0");
+        h->sub_metro = static_cast<int>(v);
+    } else if (!std::strcmp(key, "sub_or")) {
+        if (!(v >= 0.0) || v != static_cast<int>(v)) return fail(h, UL_EINVAL, "sub_or must be an integer >= 0");
+        h->sub_or = static_cast<int>(v);
+    } else if (!std::strcmp(key, "beta")) {
+        if (!(v >= 0.0)) return fail(h, UL_EINVAL, "beta must be >= 0");
+        h->beta = v;
+    } else {
+        return fail(h, UL_EINVAL, std::string("ul_set_option: unknown key '") + key + "'");
+    }
+    return UL_OK;
+}
+
+int ul_get_links(ul_lattice* h, double* theta_host)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_get_links: NULL handle");
+    if (!theta_host) return fail(h, UL_EINVAL, "ul_get_links: NULL buffer");
+    cudaError_t e = is_f64(h) ? ul::launch_to_canonical<double>(h->g, static_cast<double*>(h->theta), h->canon, h->stream)
+                              : ul::launch_to_canonical<float>(h->g, static_cast<float*>(h->theta), h->canon, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "layout kernel launch");
+    h->launches += 1;
+    UL_CK(h, cudaMemcpyAsync(theta_host, h->canon, 4ull * h->g.V * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    return UL_OK;
+}
+
+int ul_set_links(ul_lattice* h, const double* theta_host)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_set_links: NULL handle");
+    if (!theta_host) return fail(h, UL_EINVAL, "ul_set_links: NULL buffer");
+    UL_CK(h, cudaMemcpyAsync(h->canon, theta_host, 4ull * h->g.V * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    cudaError_t e = is_f64(h)
+        ? ul::launch_from_canonical<double>(h->g, h->canon, static_cast<double*>(h->theta), h->cs, h->stream)
+        : ul::launch_from_canonical<float>(h->g, h->canon, static_cast<float*>(h->theta), h->cs, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "layout kernel launch");
+    h->launches += 1;
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    return UL_OK;
+}
+
+int ul_get_state(ul_lattice* h, uint64_t* seed, uint64_t* metro_pass)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_get_state: NULL handle");
+    if (seed) *seed = h->seed;
+    if (metro_pass) *metro_pass = h->metro_pass;
+    return UL_OK;
+}
+
+int ul_set_state(ul_lattice* h, uint64_t seed, uint64_t metro_pass)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_set_state: NULL handle");
+    h->seed = seed;
+    h->metro_pass = metro_pass;
+    return UL_OK;
+}
+
+int ul_get_stats(ul_lattice* h, uint64_t* accepted, uint64_t* proposed)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_get_stats: NULL handle");
+    unsigned long long a = 0;
+    UL_CK(h, cudaMemcpyAsync(&a, h->d_accepted, sizeof(a), cudaMemcpyDeviceToHost, h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    if (accepted) *accepted = a;
+    if (proposed) *proposed = h->proposed;
+    return UL_OK;
+}
+
+int ul_get_launch_count(ul_lattice* h, uint64_t* launches)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_get_launch_count: NULL handle");
+    if (launches) *launches = h->launches;
+    return UL_OK;
+}
+
+int ul_synchronize(ul_lattice* h)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_synchronize: NULL handle");
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    return UL_OK;
+}
+
+int ul_set_stream(ul_lattice* h, void* cuda_stream)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_set_stream: NULL handle");
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    h->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->own_stream;
+    return UL_OK;
+}
+
+const char* ul_last_error(const ul_lattice* h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+int ul_precision(const ul_lattice* h) { return h ? h->precision : UL_EINVAL; }
+
+} // extern "C"

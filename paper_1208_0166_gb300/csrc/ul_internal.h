@@ -1,0 +1,57 @@
+// ul_internal.h — launchers shared between the C-ABI layer and the kernel translation
+// units.  Each launcher is instantiated for double (FP64 path, ul_kernels_f64.cu) and
+// float (FP32 path, ul_kernels_f32.cu).  Device buffers are passed as plain pointers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ul {
+
+struct Geo;
+
+// Largest number of time slabs one multilevel level may have.
+constexpr int kMaxSlabs = 256;
+
+template <typename R>
+cudaError_t launch_hot_start(const Geo& g, R* theta, void* cs, uint64_t seed, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_refresh_cs(const Geo& g, const R* theta, void* cs, cudaStream_t st);
+
+// One sub-sweep of class (mu, parity).  slab_t > 0 freezes spatial links on slices
+// t % slab_t == 0.  metro selects Metropolis (else overrelaxation).
+template <typename R>
+cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int parity, bool metro,
+                                uint64_t pass, uint64_t seed, double beta, double width, int slab_t,
+                                unsigned long long* accepted, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_to_canonical(const Geo& g, const R* theta, double* canon, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_from_canonical(const Geo& g, const double* canon, R* theta, void* cs, cudaStream_t st);
+
+// Mean plaquette into *out_dev; partials must hold plaquette_partials(g) doubles.
+int plaquette_partials(const Geo& g);
+template <typename R>
+cudaError_t launch_plaquette(const Geo& g, const void* cs, double* partials, double* out_dev, cudaStream_t st);
+
+// Slab sums of the 8 field channels O[ch][s*L3 + y] and their running sum osum.
+template <typename R>
+cudaError_t launch_slab_channels(const Geo& g, const void* cs, int slab_t, double* O, double* osum,
+                                 cudaStream_t st);
+
+// Accumulate T(s,x0,r) into asum[(s*R + r-1)*L3 + x0] and T * O into
+// bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] (bsum may be null when nd == 0).
+template <typename R>
+cudaError_t launch_measure(const Geo& g, const void* cs, int slab_t, int r_max, int nd, const double* O,
+                           double2* asum, double2* bsum, cudaStream_t st);
+
+// Cross-slab products, x0 reduction and normalisation.  out_dev receives
+// 2*r_max doubles (correlator) followed by 2*r_max*nd*8 doubles (fields) and 8 (vacuum).
+size_t ml_partials_doubles(const Geo& g, int r_max, int nd);
+cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int nd, const double2* asum,
+                             const double2* bsum, const double* osum, double* partials, double* out_dev,
+                             cudaStream_t st);
+
+} // namespace ul

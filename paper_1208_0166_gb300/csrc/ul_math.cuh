@@ -1,0 +1,223 @@
+// ul_math.cuh — per-precision arithmetic for the link updates.
+//
+// FP64 path: sin/cos/exp/atan2 with a fixed IEEE operation sequence.  The update is
+// chaotic (a one-ulp change in a cos/sin grows to ~1e-4 rad within one compound
+// sweep), so the FP64 path is only comparable link by link with an independent FP64
+// program if both evaluate the same operations.  The functions follow published
+// methods:
+//   sincos: additive range reduction by pi/2 with a three-part constant (Cody & Waite,
+//           "Software Manual for the Elementary Functions", 1980) and the Taylor
+//           series of sin and cos on [-pi/4, pi/4] evaluated by Horner's rule;
+//   exp:    reduction by ln 2 (same method), Taylor series on [-ln2/2, ln2/2], 2^k scale;
+//   atan2:  octant reduction to t in [0,1], the addition formula
+//           atan(t) = atan(j/8) + atan((t - j/8)/(1 + t j/8)) with j = rint(8t), and
+//           the Taylor series of atan for |u| <= 1/16.
+// Every fused multiply-add is an explicit fma(); the FP64 translation unit is compiled
+// with -fmad=false so no other multiply-add is fused.  All results are within 1 ulp.
+//
+// FP32 path: CUDA's single-precision sincosf/expf/atan2f; FMA contraction allowed.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ul {
+
+struct c64 {
+    double re, im;
+};
+struct c32 {
+    float re, im;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 elementary functions
+// ---------------------------------------------------------------------------
+namespace dm {
+// pi/2 = P1 + P2 + P3 (P1 = pi/2 rounded to double, P2 and P3 the next two roundings)
+constexpr double P1 = 0x1.921fb54442d18p+0;
+constexpr double P2 = 0x1.1a62633145c07p-54;
+constexpr double P3 = -0x1.f1976b7ed8fbcp-110;
+constexpr double TWO_OVER_PI = 0x1.45f306dc9c883p-1;
+constexpr double LN2_A = 0x1.62e42fefa39efp-1;  // ln 2 rounded to double
+constexpr double LN2_B = 0x1.abc9e3b39803fp-56; // ln 2 - LN2_A rounded
+constexpr double LOG2_E = 0x1.71547652b82fep+0; // 1/ln 2
+constexpr double PI = 0x1.921fb54442d18p+1;     // pi rounded to double
+
+static __device__ const double kAtanJ8[2][9] = {
+    // atan(j/8) rounded to double, j = 0..8
+    {0.0, 0x1.fd5ba9aac2f6ep-4, 0x1.f5b75f92c80ddp-3, 0x1.6f61941e4def1p-2, 0x1.dac670561bb4fp-2,
+     0x1.1e00babdefeb4p-1, 0x1.4978fa3269ee1p-1, 0x1.700a7c5784634p-1, 0x1.921fb54442d18p-1},
+    // the rounding remainder atan(j/8) - first row
+    {0.0, -0x1.cd37686760c17p-59, 0x1.8ab6e3cf7afbdp-57, -0x1.c63aae6f6e918p-56, 0x1.a2b7f222f65e2p-56,
+     -0x1.928df287a668fp-58, 0x1.2419a87f2a458p-56, -0x1.8c34d25aadef6p-56, 0x1.1a62633145c07p-55}};
+
+__device__ __forceinline__ void sincos_det(double x, double* sp, double* cp)
+{
+    const double k = rint(x * TWO_OVER_PI);
+    double r = fma(-k, P1, x);
+    r = fma(-k, P2, r);
+    r = fma(-k, P3, r);
+    const double r2 = r * r;
+    // odd series, highest term 1/17!
+    double a = 1.0 / 355687428096000.0;
+    a = fma(a, r2, -1.0 / 1307674368000.0);
+    a = fma(a, r2, 1.0 / 6227020800.0);
+    a = fma(a, r2, -1.0 / 39916800.0);
+    a = fma(a, r2, 1.0 / 362880.0);
+    a = fma(a, r2, -1.0 / 5040.0);
+    a = fma(a, r2, 1.0 / 120.0);
+    a = fma(a, r2, -1.0 / 6.0);
+    const double sr = fma(r * r2, a, r);
+    // even series, highest term 1/16!
+    double b = 1.0 / 20922789888000.0;
+    b = fma(b, r2, -1.0 / 87178291200.0);
+    b = fma(b, r2, 1.0 / 479001600.0);
+    b = fma(b, r2, -1.0 / 3628800.0);
+    b = fma(b, r2, 1.0 / 40320.0);
+    b = fma(b, r2, -1.0 / 720.0);
+    b = fma(b, r2, 1.0 / 24.0);
+    b = fma(b, r2, -0.5);
+    const double cr = fma(r2, b, 1.0);
+    const int quadrant = static_cast<int>(static_cast<long long>(k) & 3);
+    switch (quadrant) {
+    case 0: *sp = sr; *cp = cr; break;
+    case 1: *sp = cr; *cp = -sr; break;
+    case 2: *sp = -sr; *cp = -cr; break;
+    default: *sp = -cr; *cp = sr; break;
+    }
+}
+
+__device__ __forceinline__ double exp_det(double x)
+{
+    if (x > 700.0) return __longlong_as_double(0x7ff0000000000000LL);
+    if (x < -700.0) return 0.0;
+    const double k = rint(x * LOG2_E);
+    double r = fma(-k, LN2_A, x);
+    r = fma(-k, LN2_B, r);
+    double e = 1.0 / 6227020800.0;
+    e = fma(e, r, 1.0 / 479001600.0);
+    e = fma(e, r, 1.0 / 39916800.0);
+    e = fma(e, r, 1.0 / 3628800.0);
+    e = fma(e, r, 1.0 / 362880.0);
+    e = fma(e, r, 1.0 / 40320.0);
+    e = fma(e, r, 1.0 / 5040.0);
+    e = fma(e, r, 1.0 / 720.0);
+    e = fma(e, r, 1.0 / 120.0);
+    e = fma(e, r, 1.0 / 24.0);
+    e = fma(e, r, 1.0 / 6.0);
+    e = fma(e, r, 0.5);
+    e = fma(e, r, 1.0);
+    e = fma(e, r, 1.0);
+    return ldexp(e, static_cast<int>(k));
+}
+
+__device__ __forceinline__ double atan_small(double u)
+{
+    const double u2 = u * u;
+    double q = -1.0 / 15.0;
+    q = fma(q, u2, 1.0 / 13.0);
+    q = fma(q, u2, -1.0 / 11.0);
+    q = fma(q, u2, 1.0 / 9.0);
+    q = fma(q, u2, -1.0 / 7.0);
+    q = fma(q, u2, 1.0 / 5.0);
+    q = fma(q, u2, -1.0 / 3.0);
+    return fma(u * u2, q, u);
+}
+
+// atan2 with signed zeros treated as +0 and atan2(0, 0) = 0.
+__device__ __forceinline__ double atan2_det(double y, double x)
+{
+    const double ax = fabs(x), ay = fabs(y);
+    if (ax == 0.0 && ay == 0.0) return 0.0;
+    const bool steep = ay > ax;
+    const double t = steep ? ax / ay : ay / ax;
+    const int j = static_cast<int>(rint(t * 8.0));
+    double a;
+    if (j == 0) {
+        a = atan_small(t);
+    } else {
+        const double cj = static_cast<double>(j) * 0.125;
+        const double u = (t - cj) / (1.0 + t * cj);
+        a = kAtanJ8[0][j] + (kAtanJ8[1][j] + atan_small(u));
+    }
+    if (steep) a = (P1 - a) + P2;
+    if (x < 0.0) a = (2.0 * P1 - a) + 2.0 * P2;
+    return y < 0.0 ? -a : a;
+}
+} // namespace dm
+
+// ---------------------------------------------------------------------------
+// Precision traits used by the templated kernels
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Prec;
+
+template <>
+struct Prec<double> {
+    using real = double;
+    using cs_t = double2; // (cos, sin) of a link angle
+    static constexpr double PI = dm::PI;
+    static __device__ __forceinline__ void sincos(double x, double* s, double* c) { dm::sincos_det(x, s, c); }
+    static __device__ __forceinline__ double exp(double x) { return dm::exp_det(x); }
+    static __device__ __forceinline__ double atan2(double y, double x) { return dm::atan2_det(y, x); }
+    // uniform in [0,1) from a 64-bit word
+    static __device__ __forceinline__ double uniform(uint64_t w)
+    {
+        return static_cast<double>(w >> 11) * 0x1.0p-53;
+    }
+    static __device__ __forceinline__ double wrap(double th)
+    {
+        const double two_pi = 2.0 * PI;
+        return th - two_pi * floor((th + PI) / two_pi);
+    }
+};
+
+template <>
+struct Prec<float> {
+    using real = float;
+    using cs_t = float2;
+    static constexpr float PI = 3.14159265358979323846f;
+    static __device__ __forceinline__ void sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
+    static __device__ __forceinline__ float atan2(float y, float x) { return atan2f(y, x); }
+    static __device__ __forceinline__ float uniform(uint64_t w)
+    {
+        return static_cast<float>(static_cast<uint32_t>(w >> 40)) * 0x1.0p-24f;
+    }
+    static __device__ __forceinline__ float wrap(float th)
+    {
+        const float two_pi = 2.0f * PI;
+        return th - two_pi * floorf((th + PI) / two_pi);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Complex helpers: (a.re b.re - a.im b.im, a.re b.im + a.im b.re)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cx {
+    T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ Cx<T> cx(T re, T im)
+{
+    return Cx<T>{re, im};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b)
+{
+    return Cx<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cconj(Cx<T> a)
+{
+    return Cx<T>{a.re, -a.im};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b)
+{
+    return Cx<T>{a.re + b.re, a.im + b.im};
+}
+
+} // namespace ul

@@ -1,0 +1,144 @@
+// ul_reduce.cu — cross-slab products, reduction over x0 and normalisation of the
+// multilevel estimators (Section 2.2 of arXiv:1208.0166):
+//   C(r)        = (1/L^3) sum_x0 prod_s A_s(x0, r),                 A_s = <T>_s
+//   N(r, d, ch) = (1/V)   sum_x0 sum_s B_s(x0, r, d, ch) prod_{s' != s} A_s'(x0, r),
+//                                                                  B_s = <T O>_s
+// The product over the other slabs is prefix(s) * suffix(s+1) (no division).  All sums
+// run in a fixed order, so results are bitwise reproducible for a fixed lattice shape.
+#include "ul_device.cuh"
+#include "ul_internal.h"
+#include "ul_math.cuh"
+
+namespace ul {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ double bsum(double v, double* smem)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    double total = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kT / 32; ++w) total += smem[w];
+    return total;
+}
+
+__device__ __forceinline__ Cx<double> mean_of(double2 v, double n) { return Cx<double>{v.x / n, v.y / n}; }
+
+// grid (chunks, r_max); partials[((r*Q + q)*chunks + chunk)*2 + part], Q = 1 + nd*8.
+__global__ void __launch_bounds__(kT) ml_reduce_kernel(Geo g, int S, int n_sub, int r_max, int nd,
+                                                        const double2* __restrict__ asum,
+                                                        const double2* __restrict__ bsum_in,
+                                                        double* __restrict__ partials)
+{
+    __shared__ double smem[kT / 32];
+    const int chunks = gridDim.x, chunk = blockIdx.x, r = blockIdx.y;
+    const int x0 = chunk * kT + threadIdx.x;
+    const bool valid = x0 < g.L3;
+    const int Q = 1 + nd * 8;
+    const double n = static_cast<double>(n_sub);
+    Cx<double> pre[kMaxSlabs + 1];
+    pre[0] = Cx<double>{1.0, 0.0};
+    for (int s = 0; s < S; ++s) {
+        const Cx<double> A = valid ? mean_of(asum[static_cast<long>(s * r_max + r) * g.L3 + x0], n) : Cx<double>{0.0, 0.0};
+        pre[s + 1] = cmul(pre[s], A);
+    }
+    const Cx<double> c = valid ? pre[S] : Cx<double>{0.0, 0.0};
+    double re = bsum(c.re, smem);
+    double im = bsum(c.im, smem);
+    if (threadIdx.x == 0) {
+        const long o = ((static_cast<long>(r) * Q + 0) * chunks + chunk) * 2;
+        partials[o] = re;
+        partials[o + 1] = im;
+    }
+    for (int d = 0; d < nd; ++d) {
+        Cx<double> acc[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) acc[ch] = Cx<double>{0.0, 0.0};
+        if (valid) {
+            Cx<double> suf{1.0, 0.0};
+            for (int s = S - 1; s >= 0; --s) {
+                const Cx<double> W = cmul(pre[s], suf);
+                const long base = ((static_cast<long>(s * r_max + r) * nd + d) * 8) * g.L3 + x0;
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) acc[ch] = cadd(acc[ch], cmul(mean_of(bsum_in[base + ch * g.L3], n), W));
+                suf = cmul(mean_of(asum[static_cast<long>(s * r_max + r) * g.L3 + x0], n), suf);
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+            re = bsum(acc[ch].re, smem);
+            im = bsum(acc[ch].im, smem);
+            if (threadIdx.x == 0) {
+                const long o = ((static_cast<long>(r) * Q + 1 + d * 8 + ch) * chunks + chunk) * 2;
+                partials[o] = re;
+                partials[o + 1] = im;
+            }
+        }
+    }
+}
+
+// One thread per output double: sum over chunks in order, then normalise.
+__global__ void ml_finalize_kernel(int r_max, int nd, int chunks, const double* __restrict__ partials, double L3,
+                                   double V, double* __restrict__ out)
+{
+    const int Q = 1 + nd * 8;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x; // (r*Q + q)*2 + part
+    if (k >= r_max * Q * 2) return;
+    const int part = k & 1;
+    const int rq = k >> 1;
+    const int r = rq / Q, q = rq - r * Q;
+    double v = 0.0;
+    for (int c = 0; c < chunks; ++c) v += partials[(static_cast<long>(rq) * chunks + c) * 2 + part];
+    if (q == 0) {
+        out[2 * r + part] = v / L3;
+    } else {
+        out[2 * r_max + ((r * nd) * 8 + (q - 1)) * 2 + part] = v / V;
+    }
+}
+
+// Vacuum channel averages: block ch sums osum[ch][0..SL3) and divides by n_sub V.
+__global__ void __launch_bounds__(kT) ml_vacuum_kernel(int SL3, const double* __restrict__ osum, double nV,
+                                                        double* __restrict__ out)
+{
+    __shared__ double smem[kT / 32];
+    const int ch = blockIdx.x;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < SL3; k += kT) v += osum[static_cast<long>(ch) * SL3 + k];
+    const double t = bsum(v, smem);
+    if (threadIdx.x == 0) out[ch] = t / nV;
+}
+
+} // namespace
+
+size_t ml_partials_doubles(const Geo& g, int r_max, int nd)
+{
+    const size_t chunks = (g.L3 + kT - 1) / kT;
+    return static_cast<size_t>(r_max) * (1 + nd * 8) * chunks * 2;
+}
+
+cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int nd, const double2* asum,
+                             const double2* bsum_in, const double* osum, double* partials, double* out_dev,
+                             cudaStream_t st)
+{
+    const int S = g.Nt / slab_t;
+    if (S > kMaxSlabs) return cudaErrorInvalidValue;
+    const int chunks = (g.L3 + kT - 1) / kT;
+    ml_reduce_kernel<<<dim3(chunks, r_max), kT, 0, st>>>(g, S, n_sub, r_max, nd, asum, bsum_in, partials);
+    const int nout = r_max * (1 + nd * 8) * 2;
+    ml_finalize_kernel<<<(nout + kT - 1) / kT, kT, 0, st>>>(r_max, nd, chunks, partials, static_cast<double>(g.L3),
+                                                             static_cast<double>(g.V), out_dev);
+    if (nd > 0 && osum)
+        ml_vacuum_kernel<<<8, kT, 0, st>>>(S * g.L3, osum, static_cast<double>(n_sub) * static_cast<double>(g.V),
+                                           out_dev + 2 * r_max + 2 * r_max * nd * 8);
+    return cudaGetLastError();
+}
+
+int plaquette_partials(const Geo& g) { return (g.V + kT - 1) / kT; }
+
+} // namespace ul

@@ -1,0 +1,229 @@
+"""CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+FP64 tolerances: link angles 1e-10 rad after 10 compound sweeps (the FP64 path
+evaluates the oracle's IEEE operation sequence, so the expected difference is 0);
+observables 1e-12 absolute (only the summation order of the reductions differs).
+FP32+FP64-accumulation is compared statistically (3 combined standard errors).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1208_0166_gb300 import _lib
+from paper_1208_0166_gb300.workloads import random_angles
+
+pytestmark = pytest.mark.gpu
+
+ANGLE_TOL = 1e-10
+OBS_TOL = 1e-12
+
+
+def angle_diff(a, b):
+    return np.abs(np.remainder(np.asarray(a) - np.asarray(b) + np.pi, 2 * np.pi) - np.pi)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_loaded():
+    _lib.load()
+
+
+@pytest.mark.parametrize("L,Nt", [(2, 2), (4, 4), (6, 4), (8, 8), (10, 6), (4, 12)])
+def test_hot_start_is_bitwise_identical(L, Nt):
+    g = _lib.Lattice(L, Nt, 1.0, 17)
+    c = O.Lattice(L, Nt, 1.0, 17)
+    assert np.array_equal(g.get_links(), c.theta)
+
+
+@pytest.mark.parametrize("L,Nt,seed,beta", [(8, 8, 1, 1.0), (6, 4, 5, 1.0), (10, 6, 2, 0.8), (4, 12, 9, 2.0)])
+def test_compound_sweeps_match_oracle(L, Nt, seed, beta):
+    """Config 0 shape (8^4, seed 1) and ragged shapes (V/2 not a multiple of the block)."""
+    g = _lib.Lattice(L, Nt, beta, seed)
+    c = O.Lattice(L, Nt, beta, seed)
+    acc_cpu = 0
+    for _ in range(10):
+        g.sweep(1, 3)
+        acc_cpu += c.sweep(1, 3)
+    d = angle_diff(g.get_links(), c.theta)
+    acc_gpu, proposed = g.stats()
+    flips = abs(acc_gpu - acc_cpu) / proposed
+    print(f"{L}^3x{Nt}: max |dtheta| = {d.max():.3e}, accept rate {acc_gpu / proposed:.4f}, "
+          f"flipped accept fraction {flips:.2e}")
+    assert d.max() <= ANGLE_TOL
+    assert acc_gpu == acc_cpu
+    assert g.get_state() == (seed, c.metro_pass.value)
+    assert abs(g.plaquette() - c.plaquette()) < OBS_TOL
+
+
+def test_metropolis_width_and_pass_mix():
+    g = _lib.Lattice(6, 6, 1.1, 4)
+    c = O.Lattice(6, 6, 1.1, 4, width=0.4)
+    g.set_option("metro_width", 0.4)
+    g.sweep(3, 0)
+    c.sweep(3, 0)
+    g.sweep(0, 2)
+    c.sweep(0, 2)
+    g.sweep(2, 1)
+    c.sweep(2, 1)
+    assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
+
+
+def test_set_links_roundtrip_and_resume():
+    L, Nt = 6, 4
+    th = random_angles(L, Nt, 3)
+    g = _lib.Lattice(L, Nt, 1.0, 8)
+    g.set_links(th)
+    assert np.array_equal(g.get_links(), th)
+    g.set_state(8, 5)
+    g.sweep(1, 2)
+    c = O.Lattice(L, Nt, 1.0, 8, theta=th, metro_pass=5)
+    c.sweep(1, 2)
+    assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
+    # checkpoint / resume continues bit-identically
+    saved, state = g.get_links(), g.get_state()
+    g.sweep(1, 3)
+    after = g.get_links()
+    h = _lib.Lattice(L, Nt, 1.0, 99)
+    h.set_links(saved)
+    h.set_state(*state)
+    h.sweep(1, 3)
+    assert np.array_equal(h.get_links(), after)
+
+
+def test_fp32_links_are_rounded_angles():
+    L, Nt = 4, 6
+    th = random_angles(L, Nt, 12)
+    g = _lib.Lattice(L, Nt, 1.0, 1, _lib.UL_FP32_ACC64)
+    g.set_links(th)
+    assert np.array_equal(g.get_links(), th.astype(np.float32).astype(np.float64))
+    c = O.Lattice(L, Nt, 1.0, 1)
+    h = _lib.Lattice(L, Nt, 1.0, 1, _lib.UL_FP32_ACC64)
+    assert np.max(np.abs(h.get_links() - c.theta)) < 4e-7
+
+
+@pytest.mark.parametrize("tau", [1, 2, 3, 6])
+def test_multilevel_matches_oracle(tau):
+    L, Nt, n_sub, r_max, d_max = 4, 6, 3, 2, 2
+    g = _lib.Lattice(L, Nt, 1.0, 21)
+    c = O.Lattice(L, Nt, 1.0, 21)
+    g.sweep(1, 3)
+    c.sweep(1, 3)
+    gr = g.multilevel_fields(tau, n_sub, r_max, d_max)
+    cr = c.multilevel(tau, n_sub, r_max, d_max=d_max)
+    assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
+    assert np.max(np.abs(gr["corr"] - cr["corr"])) < OBS_TOL
+    assert np.max(np.abs(gr["fields"] - cr["fields"])) < OBS_TOL
+    assert np.max(np.abs(gr["vac"] - cr["vac"])) < OBS_TOL
+    # correlator-only entry point agrees with the fields entry point
+    g2 = _lib.Lattice(L, Nt, 1.0, 21)
+    g2.sweep(1, 3)
+    assert np.max(np.abs(g2.multilevel(tau, n_sub, r_max) - gr["corr"])) < 1e-15
+
+
+def test_multilevel_config0_shape():
+    """8^4, beta = 1, seed 1: 20 sweeps then slab_t = 2, r <= 3 (n_sub reduced to 6)."""
+    g = _lib.Lattice(8, 8, 1.0, 1)
+    c = O.Lattice(8, 8, 1.0, 1)
+    for _ in range(20):
+        g.sweep(1, 3)
+        c.sweep(1, 3)
+    gr = g.multilevel_fields(2, 6, 3, 2)
+    cr = c.multilevel(2, 6, 3, d_max=2)
+    assert np.max(np.abs(gr["corr"] - cr["corr"])) < OBS_TOL
+    assert np.max(np.abs(gr["fields"] - cr["fields"])) < OBS_TOL
+
+
+def test_multilevel_sub_options_and_no_update_identity():
+    L, Nt = 6, 4
+    th = random_angles(L, Nt, 33)
+    g = _lib.Lattice(L, Nt, 1.0, 2)
+    g.set_links(th)
+    g.set_option("sub_metro", 0)
+    g.set_option("sub_or", 0)
+    gr = g.multilevel_fields(2, 2, 3, 3)
+    c = O.Lattice(L, Nt, 1.0, 2, theta=th)
+    assert np.max(np.abs(gr["corr"] - c.polyakov_correlator(3))) < OBS_TOL
+    assert np.max(np.abs(gr["fields"] - c.field_correlator(3, 3))) < OBS_TOL
+    assert np.array_equal(g.get_links(), th)
+    g.set_option("sub_metro", 2)
+    g.set_option("sub_or", 1)
+    gr = g.multilevel_fields(4, 2, 2, 1)
+    cr = c.multilevel(4, 2, 2, d_max=1, sub_metro=2, sub_or=1)
+    assert np.max(np.abs(gr["corr"] - cr["corr"])) < OBS_TOL
+    assert np.max(np.abs(gr["fields"] - cr["fields"])) < OBS_TOL
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(_lib.ULError) as e:
+        _lib.Lattice(5, 4, 1.0, 1)
+    assert e.value.code == _lib.UL_EINVAL
+    with pytest.raises(_lib.ULError):
+        _lib.Lattice(4, 4, -1.0, 1)
+    g = _lib.Lattice(4, 6, 1.0, 1)
+    for args in [(4, 2, 1), (0, 2, 1), (2, 0, 1), (2, 2, 0), (2, 2, 3)]:
+        with pytest.raises(_lib.ULError) as e:
+            g.multilevel(*args)
+        assert e.value.code == _lib.UL_EINVAL
+    with pytest.raises(_lib.ULError):
+        g.multilevel_fields(2, 1, 1, 4)
+    with pytest.raises(_lib.ULError):
+        g.set_option("no_such_option", 1.0)
+    with pytest.raises(_lib.ULError):
+        g.sweep(-1, 0)
+    # the handle stays usable after errors
+    g.sweep(1, 1)
+    assert -1.0 <= g.plaquette() <= 1.0
+
+
+def test_full_size_24_sampled():
+    """24^4 (the benchmark's lattice), FP64, same launch configuration as the benchmark:
+    one compound sweep against the oracle on every link, the plaquette, a two-sample
+    multilevel level (correlators against the oracle), and field insertions of a
+    frozen configuration on sampled (r, d, channel) elements."""
+    L = 24
+    g = _lib.Lattice(L, L, 1.0, 1)
+    c = O.Lattice(L, L, 1.0, 1)
+    assert np.array_equal(g.get_links(), c.theta)
+    g.sweep(1, 3)
+    c.sweep(1, 3)
+    assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
+    assert abs(g.plaquette() - c.plaquette()) < OBS_TOL
+    gr = g.multilevel(2, 2, 8)
+    cr = c.multilevel(2, 2, 8)
+    assert np.max(np.abs(gr - cr["corr"])) < OBS_TOL
+    assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
+    g.set_option("sub_metro", 0)
+    g.set_option("sub_or", 0)
+    f = g.multilevel_fields(2, 1, 8, 6)
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        r, d, ch = int(rng.integers(1, 9)), int(rng.integers(0, 7)), int(rng.integers(0, 8))
+        assert abs(f["fields"][r - 1, d, ch] - c.field_correlator_one(r, d, ch)) < OBS_TOL
+
+
+def _binned(x, nb=10):
+    x = np.asarray(x)
+    n = len(x) // nb * nb
+    b = x[:n].reshape(nb, -1).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nb)
+
+
+def test_fp32_agrees_statistically_with_fp64():
+    """FP32 links with FP64 accumulation sample the same distribution as FP64."""
+    L, Nt = 8, 8
+    res = {}
+    for prec in (_lib.UL_FP64, _lib.UL_FP32_ACC64):
+        plaq = []
+        for seed in (1, 2, 3, 4):
+            g = _lib.Lattice(L, Nt, 1.0, seed, prec)
+            g.sweep(50, 150)
+            for _ in range(60):
+                g.sweep(1, 3)
+                plaq.append(g.plaquette())
+        res[prec] = _binned(plaq, 12)
+    (m64, e64), (m32, e32) = res[_lib.UL_FP64], res[_lib.UL_FP32_ACC64]
+    print(f"plaquette FP64 {m64:.6f}+-{e64:.6f}  FP32 {m32:.6f}+-{e32:.6f}")
+    assert abs(m64 - m32) < 3 * math.hypot(e64, e32) + 1e-6

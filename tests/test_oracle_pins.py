@@ -514,3 +514,11 @@ def test_multilevel_product_matches_enumeration_of_sample_combinations():
     fields /= n ** S * V
     assert np.max(np.abs(ml["corr"] - corr)) < 1e-13
     assert np.max(np.abs(ml["fields"] - fields)) < 1e-13
+
+
+def test_field_correlator_one_element_matches_full():
+    L, Nt = 4, 4
+    lat = O.Lattice(L, Nt, 1.0, 1, theta=random_angles(L, Nt, 95))
+    full = lat.field_correlator(2, 2)
+    for r, d, ch in [(1, 0, 0), (2, 2, 7), (2, 1, 3)]:
+        assert lat.field_correlator_one(r, d, ch) == full[r - 1, d, ch]
