@@ -77,7 +77,10 @@ def _peaks():
 
 # DRAM bytes per launch of the dominant kernel from the committed ncu capture, keyed by
 # the hash of the kernel source it was taken on (null when the source has changed).
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/update_class_f64_24x24.md: mean of the two captured launches (cold cache)
+    ("update_class_kernel<double>", "b5f314d3ed273253"): 21.28e6,
+}
 
 
 def _kernel_hash():
@@ -275,6 +278,24 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
     return out
 
 
+def profile_step(args):
+    """One step of the workload with no timing and no output (for profiler captures)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1208_0166_gb300 import _lib as lib
+
+    prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
+    lat = lib.Lattice(W.L, W.Nt, W.beta, 1, prec)
+    for _ in range(W.therm_sweeps):
+        lat.sweep(W.sweep_metro, W.sweep_or)
+    lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+    lat.plaquette()
+    lat.synchronize()
+    lat.close()
+    return 0
+
+
 def run_ours(args):
     ws, rank, local = _dist()
     import torch
@@ -370,7 +391,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run one step of the workload and exit (command line for ncu captures)")
     args = ap.parse_args()
+    if args.profile_step:
+        return profile_step(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
