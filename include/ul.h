@@ -113,6 +113,29 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
  * accumulated in FP64 in a fixed order (bitwise reproducible). */
 int ul_plaquette(ul_lattice* h, double* out);
 
+/*
+ * ul_plaquette_noalloc — the mean plaquette <Re U_p> of link angles that already live in
+ * device memory, computed without allocating any device memory.  The paper has no
+ * counterpart: this exists for callers that cannot let a library allocate, such as a host
+ * whose device memory is handed out only by its own allocator under a fixed budget, or a
+ * loop that cannot accept the device synchronisation an allocation may cause.
+ *   theta_dev : caller-owned device array of 4 L^3 Nt doubles, canonical layout
+ *               theta[mu*V + i] (read only).
+ *   out_dev   : caller-owned device pointer to one double; receives the mean plaquette.
+ *   cuda_stream: cudaStream_t to run on (NULL: the legacy default stream).  The call only
+ *               enqueues two kernels and returns; read *out_dev after synchronising the stream.
+ * Scratch: one partial sum per block of 256 sites, kept in a fixed array inside the library
+ * (512 KiB per GPU that loads it, held until the process exits).  Lattices larger than
+ * 2^24 sites (e.g. beyond 64^4) are rejected with UL_EINVAL, as are NULL pointers and
+ * L or Nt < 2; UL_ECUDA means a CUDA call failed.  The first call on each device looks up
+ * the array's device address (with that device current); make that first call before any
+ * stream capture.  All calls share the one array and each call overwrites every slot it
+ * reads, so nothing carries over between calls, but two calls that overlap on the GPU
+ * (different streams, same device) race on it: serialise them.  Values agree with
+ * ul_plaquette to rounding (the sum order differs).
+ */
+int ul_plaquette_noalloc(const double* theta_dev, int L, int Nt, double* out_dev, void* cuda_stream);
+
 /* ul_free — release the handle and its device memory.  NULL is accepted. */
 int ul_free(ul_lattice* h);
 

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("ul_set_stream", _I, [_P, _P]),
     ("ul_last_error", ctypes.c_char_p, [_P]),
     ("ul_precision", _I, [_P]),
+    ("ul_plaquette_noalloc", _I, [_DP, _I, _I, _DP, _P]),
 ]
 
 

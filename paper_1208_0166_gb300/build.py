@@ -26,6 +26,7 @@ SOURCES = {
     "ul_kernels_f32.cu": [],
     "ul_reduce.cu": [],
     "ul_api.cu": [],
+    "ul_noalloc.cu": [],
 }
 
 
