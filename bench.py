@@ -211,48 +211,55 @@ def run_reference(args):
 
 
 def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
-    """Returns dict with timings for K steps of the workload at precision prec."""
-    stream = torch.cuda.current_stream()
+    """Returns dict with timings for K steps of the workload at precision prec.  All work
+    (the library's kernels, the L2 flush and the CUDA events) runs on one torch stream."""
+    stream = torch.cuda.Stream()
     lat = lib.Lattice(W.L, W.Nt, W.beta, 1 + rank, prec)
     lat.set_stream(stream.cuda_stream)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
 
     def step():
+        e0 = ev()
         for _ in range(W.therm_sweeps):
             lat.sweep(W.sweep_metro, W.sweep_or)
-        e_mid = torch.cuda.Event(enable_timing=True)
-        e_mid.record(stream)
+        e1 = ev()
         res = lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+        e2 = ev()
         plaq = lat.plaquette()
-        return e_mid, res, plaq
+        e3 = ev()
+        return (e0, e1, e2, e3), res, plaq
 
     for _ in range(Wm):
         step()
-    torch.cuda.synchronize()
+    stream.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = lat.launch_count()
-    total_ms, sweep_ms, step_ms = 0.0, 0.0, []
+    total_ms, sweep_ms, ml_ms, step_ms = 0.0, 0.0, 0.0, []
     last = None
     for _ in range(K):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e2 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e_mid, res, plaq = step()
-        e2.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e2)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        (e0, e1, e2, e3), res, plaq = step()
+        stream.synchronize()
+        ms = e0.elapsed_time(e3)
         total_ms += ms
-        sweep_ms += e0.elapsed_time(e_mid)
+        sweep_ms += e0.elapsed_time(e1)
+        ml_ms += e1.elapsed_time(e2)
         step_ms.append(ms)
         last = (res, plaq)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     launches = lat.launch_count() - launches0
-    out = {"total_ms": total_ms, "sweep_ms": sweep_ms, "step_ms": step_ms, "launches": launches,
+    out = {"total_ms": total_ms, "sweep_ms": sweep_ms, "ml_ms": ml_ms, "step_ms": step_ms, "launches": launches,
            "corr": last[0]["corr"], "plaquette": last[1]}
     if e2e:
         import numpy as np
@@ -272,7 +279,7 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
             r = lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
             p = lat.plaquette()
             assert np.isfinite(r["corr"]).all() and np.isfinite(p)
-        torch.cuda.synchronize()
+        stream.synchronize()
         out["e2e_s"] = time.perf_counter() - t0
     lat.close()
     return out
@@ -339,6 +346,7 @@ def run_ours(args):
         o_s = gmax(o["total_ms"]) / 1e3
         compare = {"precision": "fp32_acc64" if other == lib.UL_FP32_ACC64 else "fp64",
                    "value": UPDATES_PER_STEP * K * ws / o_s, "unit": UNIT,
+                   "sweep_ms_per_step": o["sweep_ms"] / K, "multilevel_ms_per_step": o["ml_ms"] / K,
                    "correlator_samples_per_s": SAMPLES_PER_STEP * K * ws / o_s,
                    "ms_per_step": o_s / K * 1e3, "gpu_launches": o["launches"],
                    "C_r": [[z.real, z.imag] for z in o["corr"][:4]]}
@@ -369,7 +377,8 @@ def run_ours(args):
             "ms_per_step": total_s / K * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)",
             "data": "synthetic", "config": _config(args),
-            "correlator_samples_per_s": samples, "insertion_samples_per_s": INSERTION_SAMPLES_PER_STEP * K * ws / total_s,
+            "correlator_samples_per_s": samples,
+            "phases_ms_per_step": {"sweeps": main["sweep_ms"] / K, "multilevel": main["ml_ms"] / K}, "insertion_samples_per_s": INSERTION_SAMPLES_PER_STEP * K * ws / total_s,
             "link_updates_per_step": UPDATES_PER_STEP, "compare": compare,
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": UPDATES_PER_STEP * K * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H2D_BYTES,

@@ -145,6 +145,12 @@ int ul_free(ul_lattice* h);
  *   "sub_metro"    Metropolis passes per multilevel sub-sample (>= 0, default 1)
  *   "sub_or"       overrelaxation passes per multilevel sub-sample (>= 0, default 3)
  *   "beta"         coupling (>= 0)
+ *   "graphs"       1 (default): recurring launch sequences (a compound sweep, a chunk of
+ *                  sub-samples) are captured once into CUDA graphs and replayed; 0: every
+ *                  kernel is launched directly.  Results are identical either way.
+ *   "insertion_chunk_mb"  bound (MiB, default 4096) on the buffers that hold the per-sample
+ *                  transporters and channel sums between insertion contractions; fewer
+ *                  MiB means more, smaller contractions (results change only by rounding)
  */
 int ul_set_option(ul_lattice* h, const char* key, double value);
 

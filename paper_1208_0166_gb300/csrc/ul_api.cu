@@ -3,9 +3,11 @@
 // results to caller-owned host buffers.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/ul.h"
 #include "ul_device.cuh"
@@ -20,6 +22,7 @@ struct ul_lattice {
     double width = 1.0;
     int sub_metro = 1;
     int sub_or = 3;
+    int chunk_mb = 4096; // bound on the per-sample T/O buffers of the insertion contraction
     uint64_t proposed = 0;
     uint64_t launches = 0; // kernels launched on behalf of this handle
 
@@ -33,6 +36,19 @@ struct ul_lattice {
     // multilevel scratch, grown on demand
     void* ml_buf = nullptr;
     size_t ml_bytes = 0;
+
+    // CUDA graphs of recurring launch sequences (compound sweeps, chunks of sub-samples).
+    // Update kernels in a graph read their Metropolis pass number relative to *d_pass_base,
+    // which a one-thread kernel sets before each replay.
+    struct Graph {
+        std::vector<long long> key;
+        cudaGraphExec_t exec = nullptr;
+        long kernels = 0;
+    };
+    std::vector<Graph> graphs;
+    bool use_graphs = true;
+    unsigned long long* d_pass_base = nullptr;
+    cudaStream_t cap_stream = nullptr;
 
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
@@ -66,10 +82,25 @@ size_t real_size(const ul_lattice* h) { return h->precision == UL_FP64 ? sizeof(
 
 bool is_f64(const ul_lattice* h) { return h->precision == UL_FP64; }
 
+enum : long long { kGraphSweep = 1, kGraphChunk = 2 };
+
+void drop_graphs(ul_lattice* h, long long kind)
+{
+    std::vector<ul_lattice::Graph> keep;
+    for (auto& gr : h->graphs) {
+        if (kind == 0 || gr.key[0] == kind) cudaGraphExecDestroy(gr.exec);
+        else keep.push_back(gr);
+    }
+    h->graphs.swap(keep);
+}
+
 void release(ul_lattice* h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h, 0);
+    cudaFree(h->d_pass_base);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->theta);
     cudaFree(h->cs);
     cudaFree(h->canon);
@@ -85,6 +116,7 @@ int ensure_ml(ul_lattice* h, size_t bytes)
 {
     if (bytes <= h->ml_bytes) return UL_OK;
     UL_CK(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h, kGraphChunk); // they reference the old buffer
     cudaFree(h->ml_buf);
     h->ml_buf = nullptr;
     h->ml_bytes = 0;
@@ -97,39 +129,103 @@ int ensure_ml(ul_lattice* h, size_t bytes)
     return UL_OK;
 }
 
-int update_pass(ul_lattice* h, bool metro, int slab_t)
+long long bits_of(double v)
 {
-    for (int mu = 0; mu < 4; ++mu)
-        for (int par = 0; par < 2; ++par) {
-            cudaError_t e = is_f64(h)
-                ? ul::launch_update_class<double>(h->g, static_cast<double*>(h->theta), h->cs, mu, par, metro,
-                                                  h->metro_pass, h->seed, h->beta, h->width, slab_t, h->d_accepted,
-                                                  h->stream)
-                : ul::launch_update_class<float>(h->g, static_cast<float*>(h->theta), h->cs, mu, par, metro,
-                                                 h->metro_pass, h->seed, h->beta, h->width, slab_t, h->d_accepted,
-                                                 h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
-            h->launches += 1;
-        }
-    if (metro) {
-        long updatable = 4L * h->g.V;
-        if (slab_t > 0) updatable -= 3L * h->g.L3 * (h->g.Nt / slab_t);
-        h->proposed += static_cast<uint64_t>(updatable);
-        h->metro_pass += 1;
+    long long b;
+    std::memcpy(&b, &v, sizeof b);
+    return b;
+}
+
+uint64_t updatable_links(const ul_lattice* h, int slab_t)
+{
+    long n = 4L * h->g.V;
+    if (slab_t > 0) n -= 3L * h->g.L3 * (h->g.Nt / slab_t);
+    return static_cast<uint64_t>(n);
+}
+
+// Enqueue n_metro Metropolis then n_or overrelaxation passes on st.  The Metropolis passes get
+// pass numbers first_pass, first_pass + 1, ... (plus *pass_base when pass_base is set).
+// Returns the number of kernels enqueued, or a negative status.
+long enqueue_passes(ul_lattice* h, cudaStream_t st, int n_metro, int n_or, int slab_t, uint64_t first_pass,
+                    const unsigned long long* pass_base)
+{
+    long n = 0;
+    for (int k = 0; k < n_metro + n_or; ++k) {
+        const bool metro = k < n_metro;
+        const uint64_t pass = first_pass + (metro ? static_cast<uint64_t>(k) : 0);
+        for (int mu = 0; mu < 4; ++mu)
+            for (int par = 0; par < 2; ++par) {
+                cudaError_t e = is_f64(h)
+                    ? ul::launch_update_class<double>(h->g, static_cast<double*>(h->theta), h->cs, mu, par, metro, pass,
+                                                      pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st)
+                    : ul::launch_update_class<float>(h->g, static_cast<float*>(h->theta), h->cs, mu, par, metro, pass,
+                                                     pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
+                ++n;
+            }
     }
+    return n;
+}
+
+void account_passes(ul_lattice* h, int n_metro, int slab_t)
+{
+    h->proposed += static_cast<uint64_t>(n_metro) * updatable_links(h, slab_t);
+    h->metro_pass += static_cast<uint64_t>(n_metro);
+}
+
+// Run `body(stream, pass_base)` either directly on the handle's stream (pass numbers
+// absolute) or as a cached graph keyed by `key` (pass numbers relative to the handle's
+// current pass count, supplied through d_pass_base).  body returns kernels enqueued or a
+// negative status.
+template <class Body>
+int run_sequence(ul_lattice* h, const std::vector<long long>& key, Body body)
+{
+    if (!h->use_graphs) {
+        const long n = body(h->stream, h->metro_pass, nullptr);
+        if (n < 0) return static_cast<int>(n);
+        h->launches += static_cast<uint64_t>(n);
+        return UL_OK;
+    }
+    ul_lattice::Graph* found = nullptr;
+    for (auto& gr : h->graphs)
+        if (gr.key == key) found = &gr;
+    if (!found) {
+        UL_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const long n = body(h->cap_stream, 0, h->d_pass_base);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (n < 0) {
+            if (graph) cudaGraphDestroy(graph);
+            return static_cast<int>(n);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiation");
+        if (h->graphs.size() >= 16) {
+            cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.push_back(ul_lattice::Graph{key, exec, n});
+        found = &h->graphs.back();
+    }
+    cudaError_t e = ul::launch_set_u64(h->d_pass_base, h->metro_pass, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pass base launch");
+    UL_CK(h, cudaGraphLaunch(found->exec, h->stream));
+    h->launches += static_cast<uint64_t>(found->kernels) + 1;
     return UL_OK;
 }
 
-int compound_sweep(ul_lattice* h, int n_metro, int n_or, int slab_t)
+int compound_sweep(ul_lattice* h, int n_metro, int n_or)
 {
-    for (int k = 0; k < n_metro; ++k) {
-        int rc = update_pass(h, true, slab_t);
-        if (rc) return rc;
-    }
-    for (int k = 0; k < n_or; ++k) {
-        int rc = update_pass(h, false, slab_t);
-        if (rc) return rc;
-    }
+    const std::vector<long long> key = {kGraphSweep, n_metro, n_or, bits_of(h->beta), bits_of(h->width),
+                                        static_cast<long long>(h->seed)};
+    int rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* base) {
+        return enqueue_passes(h, st, n_metro, n_or, 0, first, base);
+    });
+    if (rc) return rc;
+    account_passes(h, n_metro, 0);
     return UL_OK;
 }
 
@@ -177,6 +273,9 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
     if ((e = cudaMalloc(&h->canon, nlink * sizeof(double))) != cudaSuccess) return bail(e, "staging buffer");
     if ((e = cudaMalloc(&h->d_accepted, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "counters");
     if ((e = cudaMalloc(&h->d_scalar, 16 * sizeof(double))) != cudaSuccess) return bail(e, "scalars");
+    if ((e = cudaMalloc(&h->d_pass_base, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "pass base");
+    if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "capture stream");
     if ((e = cudaMalloc(&h->plaq_partials, ul::plaquette_partials(h->g) * sizeof(double))) != cudaSuccess)
         return bail(e, "plaquette partials");
     if ((e = cudaMemsetAsync(h->d_accepted, 0, sizeof(unsigned long long), h->stream)) != cudaSuccess)
@@ -204,7 +303,7 @@ int ul_sweep(ul_lattice* h, int n_metro, int n_or)
 {
     if (!h) return fail(nullptr, UL_EINVAL, "ul_sweep: NULL handle");
     if (n_metro < 0 || n_or < 0) return fail(h, UL_EINVAL, "ul_sweep: pass counts must be >= 0");
-    return compound_sweep(h, n_metro, n_or, 0);
+    return compound_sweep(h, n_metro, n_or);
 }
 
 int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max, double* out_corr,
@@ -222,38 +321,80 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
     const int nd = fields ? d_max + 1 : 0;
     const int S = g.Nt / slab_t;
 
-    // Scratch layout (bytes): asum | bsum | O | osum | partials | out
+    // Scratch (each region 256-byte aligned): asum | bsum | osum | tk | ok | partials | out.
+    // tk / ok hold the T and O of up to `chunk` sub-samples for the deferred insertion
+    // contraction; the chunk is bounded by the option "insertion_chunk_mb".
+    const size_t rs = real_size(h);
     const size_t n_a = static_cast<size_t>(S) * r_max * g.L3;
     const size_t n_b = n_a * nd * 8;
     const size_t n_o = fields ? 8ull * S * g.L3 : 0;
     const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
     const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
-    const size_t bytes = (n_a + n_b) * sizeof(double2) + (2 * n_o + n_p + n_out) * sizeof(double);
+    const size_t per_sample = fields ? (n_a * 2 + 8ull * S * g.L3) * rs : 0;
+    int chunk = 0;
+    if (fields) {
+        const size_t cap = static_cast<size_t>(h->chunk_mb) << 20;
+        chunk = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(n_sub), cap / per_sample)));
+    }
+    auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+    const size_t off_b = al(n_a * sizeof(double2));
+    const size_t off_o = off_b + al(n_b * sizeof(double2));
+    const size_t off_t = off_o + al(n_o * sizeof(double));
+    const size_t off_k = off_t + al(fields ? n_a * 2 * rs * chunk : 0);
+    const size_t off_p = off_k + al(fields ? 8ull * S * g.L3 * rs * chunk : 0);
+    const size_t off_out = off_p + al(n_p * sizeof(double));
+    const size_t bytes = off_out + al(n_out * sizeof(double));
     int rc = ensure_ml(h, bytes);
     if (rc) return rc;
-    double2* asum = static_cast<double2*>(h->ml_buf);
-    double2* bsum = asum + n_a;
-    double* O = reinterpret_cast<double*>(bsum + n_b);
-    double* osum = O + n_o;
-    double* partials = osum + n_o;
-    double* dout = partials + n_p;
-    UL_CK(h, cudaMemsetAsync(asum, 0, (n_a + n_b) * sizeof(double2), h->stream));
-    if (fields) UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
+    char* base = static_cast<char*>(h->ml_buf);
+    double2* asum = reinterpret_cast<double2*>(base);
+    double2* bsum = reinterpret_cast<double2*>(base + off_b);
+    double* osum = reinterpret_cast<double*>(base + off_o);
+    void* tk = base + off_t;
+    void* ok = base + off_k;
+    double* partials = reinterpret_cast<double*>(base + off_p);
+    double* dout = reinterpret_cast<double*>(base + off_out);
+    UL_CK(h, cudaMemsetAsync(asum, 0, n_a * sizeof(double2), h->stream));
+    if (fields) {
+        UL_CK(h, cudaMemsetAsync(bsum, 0, n_b * sizeof(double2), h->stream));
+        UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
+    }
 
-    for (int k = 0; k < n_sub; ++k) {
-        rc = compound_sweep(h, h->sub_metro, h->sub_or, slab_t);
+    // Sub-samples in chunks; each chunk (passes + measurement per sample, then the insertion
+    // contraction of the chunk) is one launch sequence, replayed as a graph.
+    const int seq = fields ? chunk : std::min(n_sub, 64);
+    for (int k = 0; k < n_sub;) {
+        const int count = std::min(seq, n_sub - k);
+        const int sm = h->sub_metro, so = h->sub_or;
+        const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
+                                            bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
+                                            reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
+                                            reinterpret_cast<long long>(tk), reinterpret_cast<long long>(ok),
+                                            reinterpret_cast<long long>(osum)};
+        rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* base) -> long {
+            long n = 0;
+            for (int j = 0; j < count; ++j) {
+                const long m = enqueue_passes(h, st, sm, so, slab_t, first + static_cast<uint64_t>(j) * sm, base);
+                if (m < 0) return m;
+                n += m;
+                cudaError_t e = is_f64(h)
+                    ? ul::launch_measure_store<double>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, st)
+                    : ul::launch_measure_store<float>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
+                ++n;
+            }
+            if (fields) {
+                cudaError_t e = is_f64(h)
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, st)
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+                ++n;
+            }
+            return n;
+        });
         if (rc) return rc;
-        cudaError_t e;
-        if (fields) {
-            e = is_f64(h) ? ul::launch_slab_channels<double>(g, h->cs, slab_t, O, osum, h->stream)
-                          : ul::launch_slab_channels<float>(g, h->cs, slab_t, O, osum, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "slab channel launch");
-            h->launches += 1;
-        }
-        e = is_f64(h) ? ul::launch_measure<double>(g, h->cs, slab_t, r_max, nd, O, asum, fields ? bsum : nullptr, h->stream)
-                      : ul::launch_measure<float>(g, h->cs, slab_t, r_max, nd, O, asum, fields ? bsum : nullptr, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
-        h->launches += 1;
+        account_passes(h, sm * count, slab_t);
+        k += count;
     }
     cudaError_t e = ul::launch_ml_reduce(g, slab_t, n_sub, r_max, nd, asum, bsum, fields ? osum : nullptr, partials,
                                          dout, h->stream);
@@ -309,6 +450,13 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
     } else if (!std::strcmp(key, "sub_or")) {
         if (!(v >= 0.0) || v != static_cast<int>(v)) return fail(h, UL_EINVAL, "sub_or must be an integer >= 0");
         h->sub_or = static_cast<int>(v);
+    } else if (!std::strcmp(key, "graphs")) {
+        if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "graphs must be 0 or 1");
+        h->use_graphs = v != 0.0;
+    } else if (!std::strcmp(key, "insertion_chunk_mb")) {
+        if (!(v >= 1.0) || v > 1e6 || v != static_cast<int>(v))
+            return fail(h, UL_EINVAL, "insertion_chunk_mb must be an integer in [1, 1e6]");
+        h->chunk_mb = static_cast<int>(v);
     } else if (!std::strcmp(key, "beta")) {
         if (!(v >= 0.0)) return fail(h, UL_EINVAL, "beta must be >= 0");
         h->beta = v;

@@ -19,11 +19,15 @@ template <typename R>
 cudaError_t launch_refresh_cs(const Geo& g, const R* theta, void* cs, cudaStream_t st);
 
 // One sub-sweep of class (mu, parity).  slab_t > 0 freezes spatial links on slices
-// t % slab_t == 0.  metro selects Metropolis (else overrelaxation).
+// t % slab_t == 0.  metro selects Metropolis (else overrelaxation).  The Metropolis pass
+// number is pass + *pass_base (pass_base may be null).
 template <typename R>
 cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int parity, bool metro,
-                                uint64_t pass, uint64_t seed, double beta, double width, int slab_t,
-                                unsigned long long* accepted, cudaStream_t st);
+                                uint64_t pass, const unsigned long long* pass_base, uint64_t seed, double beta,
+                                double width, int slab_t, unsigned long long* accepted, cudaStream_t st);
+
+// *p = v (one thread); sets the pass base read by graph-replayed update kernels.
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_to_canonical(const Geo& g, const R* theta, double* canon, cudaStream_t st);
@@ -36,16 +40,17 @@ int plaquette_partials(const Geo& g);
 template <typename R>
 cudaError_t launch_plaquette(const Geo& g, const void* cs, double* partials, double* out_dev, cudaStream_t st);
 
-// Slab sums of the 8 field channels O[ch][s*L3 + y] and their running sum osum.
+// Measurement after one sub-sample: T into asum (FP64); with fields, T and the slab
+// channel sums O stored in sample slot `slot` of tk / ok (precision R) and O added to osum.
 template <typename R>
-cudaError_t launch_slab_channels(const Geo& g, const void* cs, int slab_t, double* O, double* osum,
-                                 cudaStream_t st);
+cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r_max, bool fields, int slot,
+                                 double2* asum, void* tk, void* ok, double* osum, cudaStream_t st);
 
-// Accumulate T(s,x0,r) into asum[(s*R + r-1)*L3 + x0] and T * O into
-// bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] (bsum may be null when nd == 0).
+// bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] += sum over the first `count` stored samples of
+// T(s,x0,r) O(s, x0 + floor(r/2) xhat + d yhat, ch).
 template <typename R>
-cudaError_t launch_measure(const Geo& g, const void* cs, int slab_t, int r_max, int nd, const double* O,
-                           double2* asum, double2* bsum, cudaStream_t st);
+cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
+                                      const void* ok, double2* bsum, cudaStream_t st);
 
 // Cross-slab products, x0 reduction and normalisation.  out_dev receives
 // 2*r_max doubles (correlator) followed by 2*r_max*nd*8 doubles (fields) and 8 (vacuum).

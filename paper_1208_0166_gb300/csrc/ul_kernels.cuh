@@ -70,86 +70,155 @@ __global__ void __launch_bounds__(kThreads) refresh_cs_kernel(Geo g, const R* __
 }
 
 // ---------------------------------------------------------------------------
-// Staple sum of link (mu, x), Section 2:
+// Link update of one (mu, parity) class, Sections 2 and 2.1.
+//
+// Staple sum of link (mu, x):
 //   A = sum_{nu != mu} [ U_nu(x+mu) U*_mu(x+nu) U*_nu(x) + U*_nu(x+mu-nu) U*_mu(x-nu) U_nu(x-nu) ]
-// so that the plaquettes containing U_mu(x) contribute Re(U_mu(x) A).  The terms are
-// formed and summed in this order (nu ascending, forward before backward).
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ Cx<R> staple_sum(const Geo& g, const cs_t<R>* __restrict__ cs, int mu, const Site& x)
-{
-    Cx<R> A{R(0), R(0)};
-    const Site xpm = site_step(g, x, mu, +1);
-#pragma unroll
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == mu) continue;
-        const Site xpn = site_step(g, x, nu, +1);
-        const Site xmn = site_step(g, x, nu, -1);
-        const Site xpm_mn = site_step(g, xpm, nu, -1);
-        const Cx<R> fwd = cmul(cmul(link_u<R>(cs, link_offset(g, nu, xpm)), cconj(link_u<R>(cs, link_offset(g, mu, xpn)))),
-                               cconj(link_u<R>(cs, link_offset(g, nu, x))));
-        const Cx<R> bwd = cmul(cmul(cconj(link_u<R>(cs, link_offset(g, nu, xpm_mn))),
-                                    cconj(link_u<R>(cs, link_offset(g, mu, xmn)))),
-                               link_u<R>(cs, link_offset(g, nu, xmn)));
-        A = cadd(A, cadd(fwd, bwd));
-    }
-    return A;
-}
-
-// ---------------------------------------------------------------------------
-// One sub-sweep of the links of class (mu, parity); Section 2.1.
+// so that the plaquettes containing U_mu(x) contribute Re(U_mu(x) A); the terms are formed
+// and summed in this order (nu ascending, forward before backward).
 //   Metropolis:      theta' = wrap(theta + width (2 u1 - 1)),
 //                    dS = -beta Re(e^{i theta'} A) - (-beta Re(e^{i theta} A)),
 //                    accept iff u2 < exp(-dS);
 //   Overrelaxation:  theta' = wrap(-2 arg(A) - theta).
-// With slab_t > 0, spatial links on slices t % slab_t == 0 are frozen (Section 2.2).
+// With a nonzero frozen mask, spatial links on slices t with bit t set stay frozen
+// (Section 2.2: the spatial links on the slab boundaries are held fixed).
+//
+// Index arithmetic: the spatial extent is a compile-time constant LC for the common
+// lattice sizes (LC = 0: runtime L), the direction MU is a template parameter, and
+// neighbour sites are reached by adding direction strides to the lexicographic index
+// with a wrap correction, so no coordinate array is indexed at run time.
 // ---------------------------------------------------------------------------
+struct UpdateArgs {
+    int parity, metro, slab_t;
+    unsigned long long frozen_mask; // bit t: spatial links on slice t frozen (Nt <= 64)
+    uint64_t pass;
+    const unsigned long long* pass_base;
+    uint64_t seed;
+    double beta, width;
+    unsigned long long* accepted;
+};
+
+template <int LC>
+struct Extent {
+    int L, Nt;
+    __device__ __forceinline__ Extent(const Geo& g) : L(LC ? LC : g.L), Nt(g.Nt) {}
+};
+
+// Lexicographic offset of a +1 / -1 step along direction D from coordinate c.
+template <int D>
+__device__ __forceinline__ int step_up(int c, int L, int Nt)
+{
+    const int n = D == 0 ? Nt : L;
+    const int st = D == 0 ? L * L * L : (D == 1 ? 1 : (D == 2 ? L : L * L));
+    return c == n - 1 ? -(n - 1) * st : st;
+}
+template <int D>
+__device__ __forceinline__ int step_down(int c, int L, int Nt)
+{
+    const int n = D == 0 ? Nt : L;
+    const int st = D == 0 ? L * L * L : (D == 1 ? 1 : (D == 2 ? L : L * L));
+    return c == 0 ? (n - 1) * st : -st;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-    update_class_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int mu, int parity, int metro,
-                        uint64_t pass, uint64_t seed, R beta, R width, int slab_t,
-                        unsigned long long* __restrict__ accepted)
+__device__ __forceinline__ Cx<R> load_link(const cs_t<R>* __restrict__ cs, int Vh, int dir, int par, int j)
+{
+    return link_u<R>(cs, (dir * 2 + par) * Vh + (j >> 1));
+}
+
+template <typename R, int MU, int NU>
+__device__ __forceinline__ void staple_term(Cx<R>& A, const cs_t<R>* __restrict__ cs, int Vh, int p, int i,
+                                            const int c[4], int L, int Nt, int up_mu)
+{
+    const int q = p ^ 1;
+    const int up_nu = step_up<NU>(c[NU], L, Nt);
+    const int dn_nu = step_down<NU>(c[NU], L, Nt);
+    const Cx<R> fwd = cmul(cmul(load_link<R>(cs, Vh, NU, q, i + up_mu), cconj(load_link<R>(cs, Vh, MU, q, i + up_nu))),
+                           cconj(load_link<R>(cs, Vh, NU, p, i)));
+    const Cx<R> bwd = cmul(cmul(cconj(load_link<R>(cs, Vh, NU, p, i + up_mu + dn_nu)),
+                                cconj(load_link<R>(cs, Vh, MU, q, i + dn_nu))),
+                           load_link<R>(cs, Vh, NU, q, i + dn_nu));
+    A = cadd(A, cadd(fwd, bwd));
+}
+
+template <typename R, int LC, int MU>
+__device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int h,
+                                            const UpdateArgs& a)
 {
     using P = Prec<R>;
+    const Extent<LC> e(g);
+    const int L = e.L, Nt = e.Nt, Lh = L / 2, Vh = g.Vh;
+    const int p = a.parity;
+    const int row = h / Lh;
+    const int xh = h - row * Lh;
+    const int y = row % L;
+    const int zt = row / L;
+    const int z = zt % L;
+    const int t = zt / L;
+    if (MU != 0 && a.slab_t > 0) {
+        const bool frozen = a.frozen_mask ? ((a.frozen_mask >> t) & 1ull) != 0 : (t % a.slab_t) == 0;
+        if (frozen) return false;
+    }
+    const int b = (p + y + z + t) & 1; // x = 2 xh + b
+    const int x = 2 * xh + b;
+    const int i = 2 * h + b;           // lexicographic site index
+    const int c[4] = {t, x, y, z};
+    const int up_mu = step_up<MU>(c[MU], L, Nt);
+    Cx<R> A{R(0), R(0)};
+    if (MU != 0) staple_term<R, MU, (MU == 0 ? 1 : 0)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    if (MU != 1) staple_term<R, MU, (MU == 1 ? 2 : 1)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    if (MU != 2) staple_term<R, MU, (MU == 2 ? 3 : 2)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    if (MU != 3) staple_term<R, MU, (MU == 3 ? 0 : 3)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    const int off = (MU * 2 + p) * Vh + h;
+    const R th = theta[off];
+    if (a.metro) {
+        uint64_t pass = a.pass;
+        if (a.pass_base) pass += *a.pass_base;
+        const uint64_t link_id = static_cast<uint64_t>(MU) * g.V + static_cast<uint64_t>(i);
+        const Philox4 w = philox4x64_10(link_id, pass, 0, 0, a.seed, kStreamMetropolis);
+        const R u1 = P::uniform(w.w[0]);
+        const R u2 = P::uniform(w.w[1]);
+        const R width = static_cast<R>(a.width), beta = static_cast<R>(a.beta);
+        const R prop = P::wrap(th + width * (R(2) * u1 - R(1)));
+        const cs_t<R> old = cs[off];
+        const R s_old = -beta * (old.x * A.re - old.y * A.im);
+        R sn, cn;
+        P::sincos(prop, &sn, &cn);
+        const R s_new = -beta * (cn * A.re - sn * A.im);
+        const R dS = s_new - s_old;
+        if (u2 < P::exp(-dS)) {
+            theta[off] = prop;
+            cs[off] = cs_t<R>{cn, sn};
+            return true;
+        }
+        return false;
+    }
+    const R alpha = P::atan2(A.im, A.re);
+    const R nth = P::wrap(R(-2) * alpha - th);
+    R sn, cn;
+    P::sincos(nth, &sn, &cn);
+    theta[off] = nth;
+    cs[off] = cs_t<R>{cn, sn};
+    return false;
+}
+
+template <typename R, int LC>
+__global__ void __launch_bounds__(kThreads)
+    update_class_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int mu, UpdateArgs a)
+{
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     bool acc = false;
     if (h < g.Vh) {
-        const Site x = site_from_half(g, parity, h);
-        const bool frozen = slab_t > 0 && mu != 0 && (x.c[0] % slab_t) == 0;
-        if (!frozen) {
-            const Cx<R> A = staple_sum<R>(g, cs, mu, x);
-            const int off = (mu * 2 + parity) * g.Vh + h;
-            const R th = theta[off];
-            if (metro) {
-                const uint64_t link_id = static_cast<uint64_t>(mu) * g.V + lex_index(g, x);
-                const Philox4 w = philox4x64_10(link_id, pass, 0, 0, seed, kStreamMetropolis);
-                const R u1 = P::uniform(w.w[0]);
-                const R u2 = P::uniform(w.w[1]);
-                const R prop = P::wrap(th + width * (R(2) * u1 - R(1)));
-                const cs_t<R> old = cs[off];
-                const R s_old = -beta * (old.x * A.re - old.y * A.im);
-                R sn, cn;
-                P::sincos(prop, &sn, &cn);
-                const R s_new = -beta * (cn * A.re - sn * A.im);
-                const R dS = s_new - s_old;
-                if (u2 < P::exp(-dS)) {
-                    theta[off] = prop;
-                    cs[off] = cs_t<R>{cn, sn};
-                    acc = true;
-                }
-            } else {
-                const R alpha = P::atan2(A.im, A.re);
-                const R nth = P::wrap(R(-2) * alpha - th);
-                R sn, cn;
-                P::sincos(nth, &sn, &cn);
-                theta[off] = nth;
-                cs[off] = cs_t<R>{cn, sn};
-            }
+        switch (mu) {
+        case 0: acc = update_link<R, LC, 0>(g, theta, cs, h, a); break;
+        case 1: acc = update_link<R, LC, 1>(g, theta, cs, h, a); break;
+        case 2: acc = update_link<R, LC, 2>(g, theta, cs, h, a); break;
+        default: acc = update_link<R, LC, 3>(g, theta, cs, h, a); break;
         }
     }
-    if (metro) {
+    if (a.metro) {
         const unsigned mask = __ballot_sync(0xffffffffu, acc);
-        if ((threadIdx.x & 31) == 0 && mask) atomicAdd(accepted, static_cast<unsigned long long>(__popc(mask)));
+        if ((threadIdx.x & 31) == 0 && mask) atomicAdd(a.accepted, static_cast<unsigned long long>(__popc(mask)));
     }
 }
 
@@ -247,75 +316,172 @@ static __global__ void __launch_bounds__(kThreads) sum_partials_kernel(const dou
 __device__ __constant__ static const int kPlaneMu[4] = {0, 0, 0, 2};
 __device__ __constant__ static const int kPlaneNu[4] = {1, 2, 3, 3};
 
-// O[ch][s*L3 + y] = sum_{t in slab s} channel_ch(y, t); osum accumulates O over samples.
+// One measurement after sub-sample k, thread per (s, x0).  With the slab line
+// W(s, x) = prod_{t in slab s} U_0(x, t) (partial Polyakov line),
+//   T(s, x0, r) = prod_{t in slab} U*_0(x0,t) U_0(x0 + r xhat, t) = W*(s, x0) W(s, x0 + r xhat),
+//   asum[(s*R + r-1)*L3 + x0] += T            (FP64 slab accumulator, r = 1..r_max)
+// and, with fields, the slab sums of the 8 plaquette channels at x0,
+//   O(s, x0, ch) = sum_{t in slab s} channel_ch(x0, t),   osum[ch*SL3 + s*L3 + x0] += O,
+// with T and O stored for the deferred insertion contraction:
+//   tk[((slot*S + s)*R + r-1)*L3 + x0] = T,   ok[((slot*S + s)*L3 + x0)*8 + ch] = O.
+// The per-sample products are formed in the link precision R (FP64 or FP32); every
+// accumulator is FP64.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) slab_channels_kernel(Geo g, const cs_t<R>* __restrict__ cs,
-                                                                 int slab_t, double* __restrict__ O,
-                                                                 double* __restrict__ osum)
+__device__ __forceinline__ Cx<R> slab_line(const Geo& g, const cs_t<R>* __restrict__ cs, int x, int t0, int slab_t)
 {
-    const int S = g.Nt / slab_t;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + y
-    if (k >= S * g.L3) return;
-    const int s = k / g.L3;
-    const int y = k - s * g.L3;
-    const int SL3 = S * g.L3;
-    double acc[8];
-#pragma unroll
-    for (int ch = 0; ch < 8; ++ch) acc[ch] = 0.0;
-    for (int t = s * slab_t; t < (s + 1) * slab_t; ++t) {
-        const Site x = site_from_lex(g, y + g.L3 * t);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const Cx<double> P = plaquette64<R>(g, cs, kPlaneMu[c], kPlaneNu[c], x);
-            acc[2 * c] += P.im;
-            acc[2 * c + 1] += P.re;
-        }
-    }
-#pragma unroll
-    for (int ch = 0; ch < 8; ++ch) {
-        O[ch * SL3 + k] = acc[ch];
-        osum[ch * SL3 + k] += acc[ch];
-    }
+    Cx<R> w = link_u<R>(cs, link_offset(g, 0, site_from_lex(g, x + g.L3 * t0)));
+    for (int t = t0 + 1; t < t0 + slab_t; ++t) w = cmul(w, link_u<R>(cs, link_offset(g, 0, site_from_lex(g, x + g.L3 * t))));
+    return w;
 }
 
-// T(s, x0, r) = prod_{t in slab} U*_0(x0,t) U_0(x0 + r xhat, t);
-// asum += T;  bsum += T * O(s, x0 + floor(r/2) xhat + d yhat).
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-    measure_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int nd, const double* __restrict__ O,
-                   double2* __restrict__ asum, double2* __restrict__ bsum)
+    measure_store_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int fields, int slot,
+                         double2* __restrict__ asum, Cx<R>* __restrict__ tk, R* __restrict__ ok,
+                         double* __restrict__ osum)
 {
     const int S = g.Nt / slab_t;
     const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + x0
     if (k >= S * g.L3) return;
     const int s = k / g.L3;
     const int x0 = k - s * g.L3;
-    const int SL3 = S * g.L3;
-    const int px = x0 % g.L, py = (x0 / g.L) % g.L, pz = x0 / (g.L * g.L);
+    const int px = x0 % g.L, pyz = x0 - px;
+    const int t0 = s * slab_t;
+    const Cx<R> w0 = cconj(slab_line<R>(g, cs, x0, t0, slab_t));
     for (int r = 1; r <= r_max; ++r) {
-        const int x1 = (px + r) % g.L + g.L * (py + g.L * pz);
-        Cx<double> T{1.0, 0.0};
-        for (int t = s * slab_t; t < (s + 1) * slab_t; ++t) {
-            const Cx<double> a = link_u64<R>(cs, link_offset(g, 0, site_from_lex(g, x0 + g.L3 * t)));
-            const Cx<double> b = link_u64<R>(cs, link_offset(g, 0, site_from_lex(g, x1 + g.L3 * t)));
-            T = cmul(T, cmul(cconj(a), b));
-        }
+        const int x1 = (px + r) % g.L + pyz;
+        const Cx<R> T = cmul(w0, slab_line<R>(g, cs, x1, t0, slab_t));
         const long ai = static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0;
         double2 av = asum[ai];
-        av.x += T.re;
-        av.y += T.im;
+        av.x += static_cast<double>(T.re);
+        av.y += static_cast<double>(T.im);
         asum[ai] = av;
-        for (int d = 0; d < nd; ++d) {
-            const int yy = (px + r / 2) % g.L + g.L * ((py + d) % g.L + g.L * pz);
-            for (int ch = 0; ch < 8; ++ch) {
-                const double o = O[ch * SL3 + s * g.L3 + yy];
-                const long bi = ((static_cast<long>(s * r_max + (r - 1)) * nd + d) * 8 + ch) * g.L3 + x0;
-                double2 bv = bsum[bi];
-                bv.x += T.re * o;
-                bv.y += T.im * o;
-                bsum[bi] = bv;
-            }
+        if (fields) tk[(static_cast<long>(slot * S + s) * r_max + (r - 1)) * g.L3 + x0] = T;
+    }
+    if (!fields) return;
+    R acc[8];
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) acc[ch] = R(0);
+    for (int t = t0; t < t0 + slab_t; ++t) {
+        const Site x = site_from_lex(g, x0 + g.L3 * t);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int mu = kPlaneMu[c], nu = kPlaneNu[c];
+            const Site xpm = site_step(g, x, mu, +1);
+            const Site xpn = site_step(g, x, nu, +1);
+            const Cx<R> P = cmul(cmul(cmul(link_u<R>(cs, link_offset(g, mu, x)), link_u<R>(cs, link_offset(g, nu, xpm))),
+                                      cconj(link_u<R>(cs, link_offset(g, mu, xpn)))),
+                                 cconj(link_u<R>(cs, link_offset(g, nu, x))));
+            acc[2 * c] += P.im;
+            acc[2 * c + 1] += P.re;
         }
+    }
+    const int SL3 = S * g.L3;
+    R* o = ok + (static_cast<long>(slot) * SL3 + k) * 8;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+        o[ch] = acc[ch];
+        osum[ch * SL3 + k] += static_cast<double>(acc[ch]);
+    }
+}
+
+// Accumulator of a complex x real product sum over the samples of one chunk.
+// FP64: fused multiply-add.  FP32: Kahan-compensated sums (error independent of the
+// number of terms), folded into the FP64 slab accumulator once per chunk.
+template <typename R>
+struct InsertionAcc;
+
+template <>
+struct InsertionAcc<double> {
+    double re = 0.0, im = 0.0;
+    __device__ __forceinline__ void add(Cx<double> T, double o)
+    {
+        re = fma(T.re, o, re);
+        im = fma(T.im, o, im);
+    }
+    __device__ __forceinline__ double total_re() const { return re; }
+    __device__ __forceinline__ double total_im() const { return im; }
+};
+
+template <>
+struct InsertionAcc<float> {
+    float re = 0.f, re_c = 0.f, im = 0.f, im_c = 0.f;
+    static __device__ __forceinline__ void kahan(float& sum, float& comp, float v)
+    {
+        const float y = v - comp;
+        const float t = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(t, sum), y);
+        sum = t;
+    }
+    __device__ __forceinline__ void add(Cx<float> T, float o)
+    {
+        kahan(re, re_c, __fmul_rn(T.re, o));
+        kahan(im, im_c, __fmul_rn(T.im, o));
+    }
+    __device__ __forceinline__ double total_re() const { return static_cast<double>(re) - static_cast<double>(re_c); }
+    __device__ __forceinline__ double total_im() const { return static_cast<double>(im) - static_cast<double>(im_c); }
+};
+
+template <typename R>
+struct Vec8;
+template <>
+struct Vec8<float> {
+    static __device__ __forceinline__ void load(const float* p, float v[8])
+    {
+        const float4 a = reinterpret_cast<const float4*>(p)[0];
+        const float4 b = reinterpret_cast<const float4*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+};
+template <>
+struct Vec8<double> {
+    static __device__ __forceinline__ void load(const double* p, double v[8])
+    {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 a = reinterpret_cast<const double2*>(p)[q];
+            v[2 * q] = a.x;
+            v[2 * q + 1] = a.y;
+        }
+    }
+};
+
+// Deferred insertion contraction over the `count` samples stored in tk/ok, thread per
+// (s, r, d, x0) with x0 fastest:
+//   bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] += sum_k T_k(s,x0,r) O_k(s, x0 + floor(r/2) xhat + d yhat, ch)
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    insertion_contract_kernel(Geo g, int S, int r_max, int nd, int count, const Cx<R>* __restrict__ tk,
+                              const R* __restrict__ ok, double2* __restrict__ bsum)
+{
+    const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const long total = static_cast<long>(S) * r_max * nd * g.L3;
+    if (idx >= total) return;
+    const int x0 = static_cast<int>(idx % g.L3);
+    long rest = idx / g.L3;
+    const int d = static_cast<int>(rest % nd);
+    rest /= nd;
+    const int r = static_cast<int>(rest % r_max) + 1;
+    const int s = static_cast<int>(rest / r_max);
+    const int px = x0 % g.L, py = (x0 / g.L) % g.L, pz = x0 / (g.L * g.L);
+    const int y = (px + r / 2) % g.L + g.L * ((py + d) % g.L + g.L * pz);
+    const long SL3 = static_cast<long>(S) * g.L3;
+    InsertionAcc<R> acc[8];
+    for (int k = 0; k < count; ++k) {
+        const Cx<R> T = tk[(static_cast<long>(k * S + s) * r_max + (r - 1)) * g.L3 + x0];
+        R o[8];
+        Vec8<R>::load(ok + (k * SL3 + static_cast<long>(s) * g.L3 + y) * 8, o);
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, o[ch]);
+    }
+    const long base = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d) * 8) * g.L3 + x0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+        double2 b = bsum[base + ch * g.L3];
+        b.x += acc[ch].total_re();
+        b.y += acc[ch].total_im();
+        bsum[base + ch * g.L3] = b;
     }
 }
 
@@ -338,12 +504,33 @@ cudaError_t launch_refresh_cs(const Geo& g, const R* theta, void* cs, cudaStream
 
 template <typename R>
 cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int parity, bool metro, uint64_t pass,
-                                uint64_t seed, double beta, double width, int slab_t,
-                                unsigned long long* accepted, cudaStream_t st)
+                                const unsigned long long* pass_base, uint64_t seed, double beta, double width,
+                                int slab_t, unsigned long long* accepted, cudaStream_t st)
 {
-    update_class_kernel<R><<<blocks_for(g.Vh), kThreads, 0, st>>>(g, theta, static_cast<cs_t<R>*>(cs), mu, parity,
-                                                                   metro ? 1 : 0, pass, seed, static_cast<R>(beta),
-                                                                   static_cast<R>(width), slab_t, accepted);
+    UpdateArgs a;
+    a.parity = parity;
+    a.metro = metro ? 1 : 0;
+    a.slab_t = slab_t;
+    a.frozen_mask = 0;
+    if (slab_t > 0 && g.Nt <= 64)
+        for (int t = 0; t < g.Nt; t += slab_t) a.frozen_mask |= 1ull << t;
+    a.pass = pass;
+    a.pass_base = pass_base;
+    a.seed = seed;
+    a.beta = beta;
+    a.width = width;
+    a.accepted = accepted;
+    cs_t<R>* c = static_cast<cs_t<R>*>(cs);
+    const dim3 grid(blocks_for(g.Vh));
+    switch (g.L) {
+    case 8: update_class_kernel<R, 8><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    case 12: update_class_kernel<R, 12><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    case 16: update_class_kernel<R, 16><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    case 20: update_class_kernel<R, 20><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    case 24: update_class_kernel<R, 24><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    case 32: update_class_kernel<R, 32><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    default: update_class_kernel<R, 0><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    }
     return cudaGetLastError();
 }
 
@@ -371,34 +558,39 @@ cudaError_t launch_plaquette(const Geo& g, const void* cs, double* partials, dou
 }
 
 template <typename R>
-cudaError_t launch_slab_channels(const Geo& g, const void* cs, int slab_t, double* O, double* osum, cudaStream_t st)
+cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r_max, bool fields, int slot,
+                                 double2* asum, void* tk, void* ok, double* osum, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
-    slab_channels_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
-        g, static_cast<const cs_t<R>*>(cs), slab_t, O, osum);
+    measure_store_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
+        g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, fields ? 1 : 0, slot, asum, static_cast<Cx<R>*>(tk),
+        static_cast<R*>(ok), osum);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_measure(const Geo& g, const void* cs, int slab_t, int r_max, int nd, const double* O,
-                           double2* asum, double2* bsum, cudaStream_t st)
+cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
+                                      const void* ok, double2* bsum, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
-    measure_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
-        g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, nd, O, asum, bsum);
+    const long total = static_cast<long>(S) * r_max * nd * g.L3;
+    insertion_contract_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
+        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk), static_cast<const R*>(ok), bsum);
     return cudaGetLastError();
 }
 
 #define UL_INSTANTIATE_KERNELS(R)                                                                                  \
     template cudaError_t launch_hot_start<R>(const Geo&, R*, void*, uint64_t, cudaStream_t);                        \
     template cudaError_t launch_refresh_cs<R>(const Geo&, const R*, void*, cudaStream_t);                           \
-    template cudaError_t launch_update_class<R>(const Geo&, R*, void*, int, int, bool, uint64_t, uint64_t, double, \
-                                                double, int, unsigned long long*, cudaStream_t);                   \
+    template cudaError_t launch_update_class<R>(const Geo&, R*, void*, int, int, bool, uint64_t,                    \
+                                                const unsigned long long*, uint64_t, double, double, int,          \
+                                                unsigned long long*, cudaStream_t);                                \
     template cudaError_t launch_to_canonical<R>(const Geo&, const R*, double*, cudaStream_t);                       \
     template cudaError_t launch_from_canonical<R>(const Geo&, const double*, R*, void*, cudaStream_t);              \
     template cudaError_t launch_plaquette<R>(const Geo&, const void*, double*, double*, cudaStream_t);               \
-    template cudaError_t launch_slab_channels<R>(const Geo&, const void*, int, double*, double*, cudaStream_t);      \
-    template cudaError_t launch_measure<R>(const Geo&, const void*, int, int, int, const double*, double2*,         \
-                                           double2*, cudaStream_t);
+    template cudaError_t launch_measure_store<R>(const Geo&, const void*, int, int, bool, int, double2*, void*,     \
+                                                 void*, double*, cudaStream_t);                                     \
+    template cudaError_t launch_insertion_contract<R>(const Geo&, int, int, int, int, const void*, const void*,     \
+                                                      double2*, cudaStream_t);
 
 } // namespace ul

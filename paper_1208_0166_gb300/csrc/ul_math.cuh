@@ -165,10 +165,21 @@ struct Prec<double> {
     {
         return static_cast<double>(w >> 11) * 0x1.0p-53;
     }
+    // th - 2pi floor((th + pi) / 2pi).  For a = th + pi in [-2pi, 4pi) the floor of the
+    // correctly rounded quotient a / 2pi is -1, 0 or 1 exactly where a < 0, a < 2pi,
+    // a < 4pi (no quotient in that range rounds across an integer: the double nearest
+    // below 2pi (4pi) divided by 2pi lies more than half an ulp below 1 (2)), so the
+    // comparisons reproduce the division's result bit for bit; other a take the division.
     static __device__ __forceinline__ double wrap(double th)
     {
         const double two_pi = 2.0 * PI;
-        return th - two_pi * floor((th + PI) / two_pi);
+        const double a = th + PI;
+        double k;
+        if (a >= -two_pi && a < 2.0 * two_pi)
+            k = a < 0.0 ? -1.0 : (a < two_pi ? 0.0 : 1.0);
+        else
+            k = floor(a / two_pi);
+        return th - two_pi * k;
     }
 };
 

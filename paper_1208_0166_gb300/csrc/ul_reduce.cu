@@ -114,7 +114,15 @@ __global__ void __launch_bounds__(kT) ml_vacuum_kernel(int SL3, const double* __
     if (threadIdx.x == 0) out[ch] = t / nV;
 }
 
+__global__ void set_u64_kernel(unsigned long long* p, unsigned long long v) { *p = v; }
+
 } // namespace
+
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st)
+{
+    set_u64_kernel<<<1, 1, 0, st>>>(p, v);
+    return cudaGetLastError();
+}
 
 size_t ml_partials_doubles(const Geo& g, int r_max, int nd)
 {

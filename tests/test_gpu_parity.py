@@ -227,3 +227,59 @@ def test_fp32_agrees_statistically_with_fp64():
     (m64, e64), (m32, e32) = res[_lib.UL_FP64], res[_lib.UL_FP32_ACC64]
     print(f"plaquette FP64 {m64:.6f}+-{e64:.6f}  FP32 {m32:.6f}+-{e32:.6f}")
     assert abs(m64 - m32) < 3 * math.hypot(e64, e32) + 1e-6
+
+
+def test_insertion_contraction_in_several_chunks():
+    """A 1 MiB bound on the sample buffers forces one contraction per sub-sample."""
+    L, Nt = 16, 8
+    g = _lib.Lattice(L, Nt, 1.0, 12)
+    c = O.Lattice(L, Nt, 1.0, 12)
+    g.set_option("insertion_chunk_mb", 1)
+    gr = g.multilevel_fields(2, 3, 2, 2)
+    cr = c.multilevel(2, 3, 2, d_max=2)
+    assert np.max(np.abs(gr["corr"] - cr["corr"])) < OBS_TOL
+    assert np.max(np.abs(gr["fields"] - cr["fields"])) < OBS_TOL
+    assert np.max(np.abs(gr["vac"] - cr["vac"])) < OBS_TOL
+
+
+def test_fp32_measurement_path_on_a_fixed_configuration():
+    """FP32 links with FP64 accumulation on a frozen configuration differ from FP64 only by
+    the FP32 rounding of the link phases (relative ~1e-7)."""
+    L, Nt = 8, 8
+    th = random_angles(L, Nt, 44)
+    out = {}
+    for prec in (_lib.UL_FP64, _lib.UL_FP32_ACC64):
+        g = _lib.Lattice(L, Nt, 1.0, 3, prec)
+        g.set_links(th)
+        g.set_option("sub_metro", 0)
+        g.set_option("sub_or", 0)
+        out[prec] = g.multilevel_fields(2, 5, 4, 3)
+    a, b = out[_lib.UL_FP64], out[_lib.UL_FP32_ACC64]
+    for key in ("corr", "fields", "vac"):
+        err = np.max(np.abs(a[key] - b[key]))
+        print(f"FP32 vs FP64 {key}: max abs diff {err:.2e}")
+        assert err < 2e-6
+
+
+@pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
+def test_graph_replay_equals_direct_launches(prec):
+    """Captured-and-replayed launch sequences give bit-identical states and results."""
+    L, Nt = 8, 8
+    out = []
+    for graphs in (1, 0):
+        g = _lib.Lattice(L, Nt, 1.0, 31, prec)
+        g.set_option("graphs", graphs)
+        g.set_option("insertion_chunk_mb", 1)
+        for _ in range(3):
+            g.sweep(1, 3)
+        g.sweep(2, 1)
+        r1 = g.multilevel_fields(2, 5, 3, 2)
+        r2 = g.multilevel(4, 3, 2)
+        g.sweep(1, 3)
+        out.append((g.get_links(), g.stats(), g.get_state(), r1, r2, g.plaquette()))
+    a, b = out
+    assert np.array_equal(a[0], b[0])
+    assert a[1] == b[1] and a[2] == b[2]
+    for key in ("corr", "fields", "vac"):
+        assert np.array_equal(a[3][key], b[3][key])
+    assert np.array_equal(a[4], b[4]) and a[5] == b[5]
