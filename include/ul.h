@@ -186,6 +186,71 @@ const char* ul_last_error(const ul_lattice* h);
 /* ul_precision — UL_FP64 or UL_FP32_ACC64 for this handle (negative status on NULL). */
 int ul_precision(const ul_lattice* h);
 
+/* ---------------------------------------------------------------------------------
+ * Batches: many independent lattices (different L, Nt, beta, seeds and schedules) on one
+ * GPU.  Each job runs the program of a single handle — n_sweeps compound sweeps of
+ * sweep_metro Metropolis + sweep_or overrelaxation passes (Section 2.1), then one
+ * multilevel level of n_sub sub-samples of sub_metro + sub_or passes with frozen slab
+ * boundaries and a transporter measurement (Section 2.2), the product across slabs and
+ * the plaquette — and its results equal, bit for bit in FP64, those of a handle driven
+ * by ul_init / ul_sweep / ul_multilevel / ul_plaquette with the same arguments.
+ * All resident jobs advance together: one pass is one launch per (mu, parity) class
+ * covering every lattice.  Jobs wait in a FIFO queue until their device memory fits in
+ * the batch's budget (and one of 48 lattice slots is free) and release it when their
+ * results are on the host, so work submitted while others run overlaps with them.
+ * --------------------------------------------------------------------------------- */
+typedef struct ul_batch ul_batch; /* opaque, library-owned */
+
+typedef struct ul_job {
+    int L, Nt;          /* even, >= 2, L^3 Nt <= 2^28 */
+    double beta;        /* >= 0 */
+    uint64_t seed;      /* Philox key of the hot start and of the Metropolis stream */
+    int n_sweeps;       /* compound sweeps before the level (>= 0) */
+    int sweep_metro;    /* Metropolis passes per compound sweep */
+    int sweep_or;       /* overrelaxation passes per compound sweep */
+    int slab_t;         /* slab thickness, divides Nt */
+    int n_sub;          /* sub-samples of the level (>= 1) */
+    int r_max;          /* correlator separations 1..r_max along x, r_max <= L/2 */
+    int sub_metro;      /* Metropolis passes per sub-sample */
+    int sub_or;         /* overrelaxation passes per sub-sample (sub_metro + sub_or >= 1) */
+    double metro_width; /* Metropolis half-width in rad (> 0) */
+} ul_job;
+
+enum { UL_JOB_QUEUED = 0, UL_JOB_RUNNING = 1, UL_JOB_DONE = 2 };
+
+/* ul_batch_create — a batch whose jobs all use `precision`, with a device-memory budget
+ * of hbm_budget_bytes (allocated once here, >= 1 MiB) and work on cuda_stream (NULL: a
+ * stream of the batch's own). */
+int ul_batch_create(ul_batch** b, int precision, size_t hbm_budget_bytes, void* cuda_stream);
+
+/* ul_batch_submit — queue a job; *job_id identifies it.  UL_EINVAL for an invalid job,
+ * UL_ENOMEM if the job alone needs more memory than the whole budget. */
+int ul_batch_submit(ul_batch* b, const ul_job* job, uint64_t* job_id);
+
+/* ul_batch_step — admit queued jobs that fit, then run up to max_passes lockstep passes
+ * (with the measurements and final reductions they reach).  Work is enqueued on the
+ * batch's stream; the call blocks only when the launch queue is full.  *n_active
+ * (may be NULL) receives the number of queued plus resident jobs. */
+int ul_batch_step(ul_batch* b, int max_passes, int* n_active);
+
+/* ul_batch_poll — *state = UL_JOB_QUEUED, UL_JOB_RUNNING or UL_JOB_DONE.  When done, out
+ * (2*r_max + 2 doubles) receives the correlator (re, im) for r = 1..r_max, the plaquette
+ * and the Metropolis acceptance rate, and the job is released (a second poll of the same
+ * id is UL_EINVAL). */
+int ul_batch_poll(ul_batch* b, uint64_t job_id, double* out, int* state);
+
+/* ul_batch_stats — link updates and kernel launches issued so far, the block size the
+ * autotuner chose for the batched update kernel (128, 256 or 512 threads, timed on the
+ * first passes; results do not depend on it) and the device bytes held by jobs. */
+int ul_batch_stats(ul_batch* b, uint64_t* link_updates, uint64_t* launches, int* block_threads,
+                   size_t* bytes_in_use);
+
+/* ul_batch_free — wait for the batch's stream and release everything (NULL accepted). */
+int ul_batch_free(ul_batch* b);
+
+/* ul_batch_last_error — text of the last error on b. */
+const char* ul_batch_last_error(const ul_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,16 @@ LIB_PATH = os.path.join(_PKG, "libul.so")
 
 _lib = None
 
+class Job(ctypes.Structure):
+    """struct ul_job of include/ul.h."""
+    _fields_ = [("L", ctypes.c_int), ("Nt", ctypes.c_int), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("n_sweeps", ctypes.c_int), ("sweep_metro", ctypes.c_int), ("sweep_or", ctypes.c_int),
+                ("slab_t", ctypes.c_int), ("n_sub", ctypes.c_int), ("r_max", ctypes.c_int),
+                ("sub_metro", ctypes.c_int), ("sub_or", ctypes.c_int), ("metro_width", ctypes.c_double)]
+
+
+UL_JOB_QUEUED, UL_JOB_RUNNING, UL_JOB_DONE = 0, 1, 2
+
 # (name, restype, argtypes) of every function declared in include/ul.h
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -48,6 +58,13 @@ SIGNATURES = [
     ("ul_last_error", ctypes.c_char_p, [_P]),
     ("ul_precision", _I, [_P]),
     ("ul_plaquette_noalloc", _I, [_DP, _I, _I, _DP, _P]),
+    ("ul_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _P]),
+    ("ul_batch_submit", _I, [_P, ctypes.POINTER(Job), _U64P]),
+    ("ul_batch_step", _I, [_P, _I, ctypes.POINTER(_I)]),
+    ("ul_batch_poll", _I, [_P, _U64, _DP, ctypes.POINTER(_I)]),
+    ("ul_batch_stats", _I, [_P, _U64P, _U64P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
+    ("ul_batch_free", _I, [_P]),
+    ("ul_batch_last_error", ctypes.c_char_p, [_P]),
 ]
 
 
@@ -174,3 +191,85 @@ class Lattice:
 
     def set_stream(self, cuda_stream: int | None) -> None:
         _check(load().ul_set_stream(self._h, ctypes.c_void_p(cuda_stream or 0)), self._h)
+
+
+def make_job(L, Nt, beta, seed, n_sweeps=100, slab_t=2, n_sub=200, r_max=None, sweep_metro=1, sweep_or=3,
+             sub_metro=1, sub_or=3, metro_width=1.0) -> Job:
+    return Job(int(L), int(Nt), float(beta), int(seed), int(n_sweeps), int(sweep_metro), int(sweep_or),
+               int(slab_t), int(n_sub), int(r_max if r_max is not None else L // 2), int(sub_metro), int(sub_or),
+               float(metro_width))
+
+
+class Batch:
+    """A batch of independent lattices advanced together (include/ul.h, ul_batch_*)."""
+
+    def __init__(self, precision: int = UL_FP64, hbm_budget_bytes: int = 1 << 30, cuda_stream: int | None = None):
+        lib = load()
+        b = ctypes.c_void_p()
+        rc = lib.ul_batch_create(ctypes.byref(b), int(precision), int(hbm_budget_bytes), ctypes.c_void_p(cuda_stream or 0))
+        if rc != UL_OK:
+            raise ULError(rc, "ul_batch_create failed")
+        self._b = b
+        self.precision = precision
+        self._rmax = {}
+
+    def _check(self, rc):
+        if rc != UL_OK:
+            raise ULError(rc, load().ul_batch_last_error(self._b).decode(errors="replace"))
+
+    def submit(self, job: Job) -> int:
+        jid = ctypes.c_uint64()
+        self._check(load().ul_batch_submit(self._b, ctypes.byref(job), ctypes.byref(jid)))
+        self._rmax[jid.value] = job.r_max
+        return jid.value
+
+    def step(self, max_passes: int = 64) -> int:
+        n = ctypes.c_int()
+        self._check(load().ul_batch_step(self._b, int(max_passes), ctypes.byref(n)))
+        return n.value
+
+    def poll(self, job_id: int):
+        """None while queued/running; dict(corr, plaquette, accept) once done."""
+        r_max = self._rmax[job_id]
+        out = np.zeros(2 * r_max + 2)
+        st = ctypes.c_int()
+        self._check(load().ul_batch_poll(self._b, int(job_id), _dp(out), ctypes.byref(st)))
+        if st.value != UL_JOB_DONE:
+            return None
+        del self._rmax[job_id]
+        return {"corr": out[0:2 * r_max:2] + 1j * out[1:2 * r_max:2], "plaquette": out[2 * r_max],
+                "accept": out[2 * r_max + 1]}
+
+    def state(self, job_id: int) -> int:
+        st = ctypes.c_int()
+        out = np.zeros(2 * self._rmax[job_id] + 2)
+        self._check(load().ul_batch_poll(self._b, int(job_id), _dp(out), ctypes.byref(st)))
+        return st.value
+
+    def stats(self):
+        u, l, t, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int(), ctypes.c_size_t()
+        self._check(load().ul_batch_stats(self._b, ctypes.byref(u), ctypes.byref(l), ctypes.byref(t), ctypes.byref(m)))
+        return {"link_updates": u.value, "launches": l.value, "block_threads": t.value, "bytes_in_use": m.value}
+
+    def run_to_completion(self, job_ids, passes_per_step: int = 64):
+        results = {}
+        pending = set(job_ids)
+        while pending:
+            self.step(passes_per_step)
+            for j in list(pending):
+                r = self.poll(j)
+                if r is not None:
+                    results[j] = r
+                    pending.discard(j)
+        return results
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().ul_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

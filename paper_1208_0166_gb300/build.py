@@ -27,6 +27,7 @@ SOURCES = {
     "ul_reduce.cu": [],
     "ul_api.cu": [],
     "ul_noalloc.cu": [],
+    "ul_batch.cu": [],
 }
 
 

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ul_batch_types.h"
+
 namespace ul {
 
 struct Geo;
@@ -58,5 +60,15 @@ size_t ml_partials_doubles(const Geo& g, int r_max, int nd);
 cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int nd, const double2* asum,
                              const double2* bsum, const double* osum, double* partials, double* out_dev,
                              cudaStream_t st);
+
+// One batched class update over every lattice of the table (blocks: sum of the lattices'
+// block counts at `threads` threads per block).
+template <typename R>
+cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int threads, int mu, int parity,
+                                  cudaStream_t st);
+
+// One batched transporter measurement (correlators only) over the lattices of the table.
+template <typename R>
+cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaStream_t st);
 
 } // namespace ul

@@ -7,6 +7,7 @@
 // transporters T, insertion operator, multilevel field estimator).
 #pragma once
 #include "ul_device.cuh"
+#include "ul_batch_types.h"
 #include "ul_internal.h"
 #include "ul_math.cuh"
 
@@ -335,14 +336,12 @@ __device__ __forceinline__ Cx<R> slab_line(const Geo& g, const cs_t<R>* __restri
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-    measure_store_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int fields, int slot,
-                         double2* __restrict__ asum, Cx<R>* __restrict__ tk, R* __restrict__ ok,
-                         double* __restrict__ osum)
+__device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* __restrict__ cs, int slab_t,
+                                                   int r_max, int fields, int slot, double2* __restrict__ asum,
+                                                   Cx<R>* __restrict__ tk, R* __restrict__ ok,
+                                                   double* __restrict__ osum, int k)
 {
     const int S = g.Nt / slab_t;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + x0
-    if (k >= S * g.L3) return;
     const int s = k / g.L3;
     const int x0 = k - s * g.L3;
     const int px = x0 % g.L, pyz = x0 - px;
@@ -383,6 +382,17 @@ __global__ void __launch_bounds__(kThreads)
         o[ch] = acc[ch];
         osum[ch * SL3 + k] += static_cast<double>(acc[ch]);
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    measure_store_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int fields, int slot,
+                         double2* __restrict__ asum, Cx<R>* __restrict__ tk, R* __restrict__ ok,
+                         double* __restrict__ osum)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + x0
+    if (k >= (g.Nt / slab_t) * g.L3) return;
+    measure_store_site<R>(g, cs, slab_t, r_max, fields, slot, asum, tk, ok, osum, k);
 }
 
 // Accumulator of a complex x real product sum over the samples of one chunk.
@@ -486,6 +496,89 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Batched kernels: one launch updates class (mu, parity) of every resident lattice of a
+// batch (lattices of different shapes, couplings, seeds and schedule positions).  The
+// per-lattice parameters travel in the kernel's parameter block; block b belongs to the
+// last job whose block0 <= b.  Each link is updated by the same device function as in
+// the single-lattice kernel, so a lattice's trajectory does not depend on its batch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Geo geo_of(int L, int Nt, int V, int Vh, int L3)
+{
+    Geo g;
+    g.L = L;
+    g.Nt = Nt;
+    g.Lh = L / 2;
+    g.L3 = L3;
+    g.V = V;
+    g.Vh = Vh;
+    return g;
+}
+
+template <typename R, int MU>
+__device__ __forceinline__ bool batch_update_link(const BatchUpdateJob& J, int parity, int h)
+{
+    const Geo g = geo_of(J.L, J.Nt, J.V, J.Vh, J.L3);
+    UpdateArgs a;
+    a.parity = parity;
+    a.metro = J.metro;
+    a.slab_t = J.slab_t;
+    a.frozen_mask = J.frozen_mask;
+    a.pass = J.pass;
+    a.pass_base = nullptr;
+    a.seed = J.seed;
+    a.beta = J.beta;
+    a.width = J.width;
+    a.accepted = J.accepted;
+    R* theta = static_cast<R*>(J.theta);
+    cs_t<R>* cs = static_cast<cs_t<R>*>(J.cs);
+    switch (J.L) {
+    case 8: return update_link<R, 8, MU>(g, theta, cs, h, a);
+    case 12: return update_link<R, 12, MU>(g, theta, cs, h, a);
+    case 16: return update_link<R, 16, MU>(g, theta, cs, h, a);
+    case 20: return update_link<R, 20, MU>(g, theta, cs, h, a);
+    case 24: return update_link<R, 24, MU>(g, theta, cs, h, a);
+    case 32: return update_link<R, 32, MU>(g, theta, cs, h, a);
+    default: return update_link<R, 0, MU>(g, theta, cs, h, a);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) batched_update_kernel(const __grid_constant__ BatchUpdateTable t, int mu,
+                                                             int parity)
+{
+    int j = t.njobs - 1;
+    while (j > 0 && static_cast<int>(blockIdx.x) < t.job[j].block0) --j;
+    const BatchUpdateJob& J = t.job[j];
+    const int h = (static_cast<int>(blockIdx.x) - J.block0) * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+    bool acc = false;
+    if (h < J.Vh) {
+        switch (mu) {
+        case 0: acc = batch_update_link<R, 0>(J, parity, h); break;
+        case 1: acc = batch_update_link<R, 1>(J, parity, h); break;
+        case 2: acc = batch_update_link<R, 2>(J, parity, h); break;
+        default: acc = batch_update_link<R, 3>(J, parity, h); break;
+        }
+    }
+    if (J.metro) {
+        const unsigned mask = __ballot_sync(0xffffffffu, acc);
+        if ((threadIdx.x & 31) == 0 && mask) atomicAdd(J.accepted, static_cast<unsigned long long>(__popc(mask)));
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) batched_measure_kernel(const __grid_constant__ BatchMeasureTable t)
+{
+    int j = t.njobs - 1;
+    while (j > 0 && static_cast<int>(blockIdx.x) < t.job[j].block0) --j;
+    const BatchMeasureJob& J = t.job[j];
+    const int k = (static_cast<int>(blockIdx.x) - J.block0) * kThreads + static_cast<int>(threadIdx.x);
+    const Geo g = geo_of(J.L, J.Nt, J.V, J.Vh, J.L3);
+    if (k >= (J.Nt / J.slab_t) * J.L3) return;
+    measure_store_site<R>(g, static_cast<const cs_t<R>*>(J.cs), J.slab_t, J.r_max, 0, 0, J.asum, nullptr, nullptr,
+                          nullptr, k);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -579,7 +672,24 @@ cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int n
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int threads, int mu, int parity,
+                                  cudaStream_t st)
+{
+    batched_update_kernel<R><<<blocks, threads, 0, st>>>(t, mu, parity);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaStream_t st)
+{
+    batched_measure_kernel<R><<<blocks, kThreads, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
 #define UL_INSTANTIATE_KERNELS(R)                                                                                  \
+    template cudaError_t launch_batched_update<R>(const BatchUpdateTable&, int, int, int, int, cudaStream_t);      \
+    template cudaError_t launch_batched_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                   \
     template cudaError_t launch_hot_start<R>(const Geo&, R*, void*, uint64_t, cudaStream_t);                        \
     template cudaError_t launch_refresh_cs<R>(const Geo&, const R*, void*, cudaStream_t);                           \
     template cudaError_t launch_update_class<R>(const Geo&, R*, void*, int, int, bool, uint64_t,                    \
