@@ -285,6 +285,118 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
     return out
 
 
+def _torch_setup():
+    import torch
+
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    return torch, dist, ws, rank, local
+
+
+def run_batch(args):
+    """32 independent configurations of uneven sizes (8 each of 12^4, 16^4, 20^4, 24^4,
+    beta from {0.96, 0.98, 1.0}) advanced together by the batch engine; a step is the
+    whole batch run to completion (100 sweeps + one 200-sample level + reduction each)."""
+    torch, dist, ws, rank, local = _torch_setup()
+    from paper_1208_0166_gb300 import _lib as lib
+    from paper_1208_0166_gb300.serving import job_from
+    from paper_1208_0166_gb300.workloads import batch_jobs_uneven
+
+    prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
+    specs = batch_jobs_uneven(1000 + 100 * rank)
+    stream = torch.cuda.Stream()
+    b = lib.Batch(prec, 8 << 30, stream.cuda_stream)
+
+    def step():
+        ids = [b.submit(job_from(sp)) for sp in specs]
+        return b.run_to_completion(ids, passes_per_step=32)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    u0, l0 = b.stats()["link_updates"], b.stats()["launches"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+    e1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = b.stats()
+    updates, launches = st["link_updates"] - u0, st["launches"] - l0
+    samples = sum(sp["n_sub"] * (sp["Nt"] // sp["slab_t"]) * sp["L"] ** 3 * sp["r_max"] for sp in specs) * args.steps
+    t = ms / 1e3
+    if dist:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    b.close()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "workload_mode": "batch", "value": updates * ws / t, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
+            "config": {"workload": "batch: 32 configurations, 8 each of 12^4/16^4/20^4/24^4, beta in "
+                                   "{0.96,0.98,1.0}, 100 sweeps + slab_t=2 n_sub=200 r<=L/3, one launch per class",
+                       "jobs": len(specs), "block_threads": st["block_threads"]},
+            "correlator_samples_per_s": samples * ws / t, "gpu_launches": launches, "clocks": clk,
+            "C_r_first_job": [[z.real, z.imag] for z in res[min(res)]["corr"][:3]]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson stream of correlator jobs (L in {12,16,20,24,32}, beta ~ U[0.95,1.005],
+    r_max in [4, L/3], n_sub in [50, 400]) served by continuous batching."""
+    torch, dist, ws, rank, local = _torch_setup()
+    from paper_1208_0166_gb300 import _lib as lib
+    from paper_1208_0166_gb300.serving import Server
+    from paper_1208_0166_gb300.workloads import serving_stream
+
+    prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
+    stream = torch.cuda.Stream()
+    warm = serving_stream(4, rate_hz=1000.0, seed=99, sizes=(12,), n_sweeps=2, n_sub_range=(2, 4))
+    srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
+    srv.run(warm)
+    srv.close()
+    reqs = serving_stream(args.serve_jobs, rate_hz=args.serve_rate, seed=7 + rank)
+    srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    results, summary = srv.run(reqs)
+    clk = clocks.stop()
+    srv.close()
+    if rank != 0:
+        return 0
+    line = {"metric": "served multilevel correlator jobs/s and p50/p99 latency", "workload_mode": "serve",
+            "value": summary["jobs_per_s"], "unit": "jobs/s", "n_gpus": ws, "higher_is_better": True,
+            "p50_latency_s": summary["p50_latency_s"], "p99_latency_s": summary["p99_latency_s"],
+            "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
+            "config": {"workload": f"Poisson stream, {args.serve_jobs} jobs at {args.serve_rate} Hz, L in "
+                                   "{12,16,20,24,32}, beta~U[0.95,1.005], r_max in [4,L/3], n_sub in [50,400], "
+                                   "100 sweeps, slab_t=2, HBM budget 16 GiB",
+                       "block_threads": summary["stats"]["block_threads"]},
+            "link_updates_per_s": summary["stats"]["link_updates"] / summary["wall_s"],
+            "gpu_launches": summary["stats"]["launches"], "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def profile_step(args):
     """One step of the workload with no timing and no output (for profiler captures)."""
     import torch
@@ -400,6 +512,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                    help="single: the 24^4 configuration step (default); batch: 32 uneven lattices; "
+                         "serve: Poisson stream through the continuous-batching loop")
+    ap.add_argument("--serve-jobs", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--profile-step", action="store_true",
                     help="run one step of the workload and exit (command line for ncu captures)")
     args = ap.parse_args()
@@ -407,6 +524,14 @@ def main():
         return profile_step(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        if args.precision == "fp64" and "--precision" not in sys.argv:
+            args.precision = "fp32"
+        return run_batch(args)
+    if args.workload == "serve":
+        if "--precision" not in sys.argv:
+            args.precision = "fp32"
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -52,3 +52,33 @@ def near_ordered_angles(L: int, Nt: int, seed: int, spread: float = 0.3) -> np.n
     rng = np.random.default_rng(seed)
     V = L ** 3 * Nt
     return rng.uniform(-spread, spread, size=4 * V)
+
+
+def batch_jobs_uneven(seed_base: int = 1000):
+    """32 independent configurations: 8 each of 12^4, 16^4, 20^4, 24^4; job j has seed
+    seed_base + j and a coupling drawn from {0.96, 0.98, 1.0} by numpy's Philox keyed by
+    that seed; 100 sweeps, one level of slabs of 2 slices with 200 sub-samples, r <= L/3."""
+    jobs = []
+    for k, L in enumerate([12] * 8 + [16] * 8 + [20] * 8 + [24] * 8):
+        seed = seed_base + k
+        rng = np.random.Generator(np.random.Philox(key=seed))
+        beta = [0.96, 0.98, 1.0][int(rng.integers(0, 3))]
+        jobs.append(dict(L=L, Nt=L, beta=beta, seed=seed, n_sweeps=100, slab_t=2, n_sub=200, r_max=L // 3))
+    return jobs
+
+
+def serving_stream(n_jobs: int, rate_hz: float, seed: int = 7, sizes=(12, 16, 20, 24, 32),
+                   n_sweeps: int = 100, n_sub_range=(50, 400)):
+    """A Poisson stream of correlator jobs: arrival times (s) with rate rate_hz, L uniform
+    over sizes, beta ~ U[0.95, 1.005], r_max uniform in [4, L/3], n_sub uniform in
+    n_sub_range; job k has seed 1 + k."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_jobs))
+    out = []
+    for k in range(n_jobs):
+        L = int(rng.choice(sizes))
+        out.append((float(t[k]), dict(L=L, Nt=L, beta=float(rng.uniform(0.95, 1.005)), seed=1 + k,
+                                       n_sweeps=n_sweeps, slab_t=2,
+                                       n_sub=int(rng.integers(n_sub_range[0], n_sub_range[1] + 1)),
+                                       r_max=int(rng.integers(4, max(4, L // 3) + 1)))))
+    return out
