@@ -214,7 +214,9 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
     """Returns dict with timings for K steps of the workload at precision prec.  All work
     (the library's kernels, the L2 flush and the CUDA events) runs on one torch stream."""
     stream = torch.cuda.Stream()
-    lat = lib.Lattice(W.L, W.Nt, W.beta, 1 + rank, prec)
+    from paper_1208_0166_gb300.replicas import replica_seed
+
+    lat = lib.Lattice(W.L, W.Nt, W.beta, replica_seed(1, rank), prec)
     lat.set_stream(stream.cuda_stream)
     with torch.cuda.stream(stream):
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -339,15 +341,13 @@ def run_batch(args):
     st = b.stats()
     updates, launches = st["link_updates"] - u0, st["launches"] - l0
     samples = sum(sp["n_sub"] * (sp["Nt"] // sp["slab_t"]) * sp["L"] ** 3 * sp["r_max"] for sp in specs) * args.steps
-    t = ms / 1e3
-    if dist:
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    from paper_1208_0166_gb300.replicas import aggregate
+
+    t, total_updates = aggregate(ms / 1e3, updates, dist, "cuda")
     b.close()
     if rank != 0:
         return 0
-    line = {"metric": METRIC, "workload_mode": "batch", "value": updates * ws / t, "unit": UNIT, "n_gpus": ws,
+    line = {"metric": METRIC, "workload_mode": "batch", "value": total_updates / t, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
@@ -439,16 +439,14 @@ def run_ours(args):
     main = _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib)
     clk = clocks.stop()
 
-    def gmax(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    from paper_1208_0166_gb300.replicas import aggregate
 
-    total_s = gmax(main["total_ms"]) / 1e3
+    def gmax(x):
+        return aggregate(x, 0.0, dist, "cuda")[0]
+
+    total_s, total_updates = aggregate(main["total_ms"] / 1e3, UPDATES_PER_STEP * K, dist, "cuda")
     e2e_s = gmax(main["e2e_s"])
-    value = UPDATES_PER_STEP * K * ws / total_s
+    value = total_updates / total_s
     samples = SAMPLES_PER_STEP * K * ws / total_s
 
     compare = None
