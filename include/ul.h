@@ -145,6 +145,16 @@ int ul_free(ul_lattice* h);
  *   "sub_metro"    Metropolis passes per multilevel sub-sample (>= 0, default 1)
  *   "sub_or"       overrelaxation passes per multilevel sub-sample (>= 0, default 3)
  *   "beta"         coupling (>= 0)
+ *   "persistent"   1: each compound sweep, and each chunk of sub-samples with their
+ *                  measurements, runs as one cooperative launch whose classes are separated
+ *                  by a grid barrier; 0 (default): one launch per class, replayed from
+ *                  CUDA graphs.  Results are identical either way.
+ *   "barrier_spin_limit"  polls a block spends waiting at a grid barrier before it gives
+ *                  up (default 2^24, about a second); a wait that gives up stops the
+ *                  launch and the next blocking call returns UL_ETIMEOUT (the handle
+ *                  stays usable; the links are then in an incomplete state).
+ *   "barrier_unreachable"  1: every barrier waits for one block more than exist, so
+ *                  every wait runs into its limit (for testing the timeout path); 0 (default).
  *   "graphs"       1 (default): recurring launch sequences (a compound sweep, a chunk of
  *                  sub-samples) are captured once into CUDA graphs and replayed; 0: every
  *                  kernel is launched directly.  Results are identical either way.

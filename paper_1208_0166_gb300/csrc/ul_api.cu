@@ -48,6 +48,12 @@ struct ul_lattice {
     std::vector<Graph> graphs;
     bool use_graphs = true;
     unsigned long long* d_pass_base = nullptr;
+    // persistent cooperative sweeps with a bounded-wait grid barrier
+    bool use_persistent = false;
+    bool barrier_unreachable = false; // test switch: no barrier can complete
+    unsigned long long spin_limit = 1ull << 24;
+    unsigned int* d_bar = nullptr;    // [0] arrivals, [1] generation
+    int* d_status = nullptr;          // nonzero after a wait gave up
     cudaStream_t cap_stream = nullptr;
 
     cudaStream_t own_stream = nullptr;
@@ -100,6 +106,8 @@ void release(ul_lattice* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h, 0);
     cudaFree(h->d_pass_base);
+    cudaFree(h->d_bar);
+    cudaFree(h->d_status);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->theta);
     cudaFree(h->cs);
@@ -217,8 +225,67 @@ int run_sequence(ul_lattice* h, const std::vector<long long>& key, Body body)
     return UL_OK;
 }
 
+ul::PersistArgs persist_args(ul_lattice* h, int n_units, int n_metro, int n_or, int slab_t)
+{
+    ul::PersistArgs a{};
+    a.u.parity = 0;
+    a.u.metro = 0;
+    a.u.slab_t = slab_t;
+    a.u.frozen_mask = 0;
+    if (slab_t > 0 && h->g.Nt <= 64)
+        for (int t = 0; t < h->g.Nt; t += slab_t) a.u.frozen_mask |= 1ull << t;
+    a.u.pass = h->metro_pass;
+    a.u.pass_base = nullptr;
+    a.u.seed = h->seed;
+    a.u.beta = h->beta;
+    a.u.width = h->width;
+    a.u.beta_f = static_cast<float>(h->beta);
+    a.u.width_f = static_cast<float>(h->width);
+    a.u.accepted = h->d_accepted;
+    a.n_units = n_units;
+    a.n_metro = n_metro;
+    a.n_or = n_or;
+    a.bar = h->d_bar;
+    a.status = h->d_status;
+    a.expected = h->barrier_unreachable ? 0xffffffffu : 0u;
+    a.spin_limit = h->spin_limit;
+    return a;
+}
+
+int launch_persistent(ul_lattice* h, const ul::PersistArgs& a)
+{
+    UL_CK(h, cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), h->stream));
+    cudaError_t e = is_f64(h) ? ul::launch_persistent<double>(h->g, static_cast<double*>(h->theta), h->cs, a, 256, h->stream)
+                              : ul::launch_persistent<float>(h->g, static_cast<float*>(h->theta), h->cs, a, 256, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "persistent sweep launch");
+    h->launches += 1;
+    return UL_OK;
+}
+
+// A device-side wait that gave up leaves a nonzero status word: report it once, reset
+// the barrier, and keep the handle usable.
+int check_device_status(ul_lattice* h)
+{
+    int st = 0;
+    UL_CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    if (!st) return UL_OK;
+    UL_CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
+    UL_CK(h, cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned int), h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    return fail(h, UL_ETIMEOUT,
+                "a grid-barrier wait of a persistent sweep reached its limit; the sweep stopped early and "
+                "the link state is incomplete");
+}
+
 int compound_sweep(ul_lattice* h, int n_metro, int n_or)
 {
+    if (h->use_persistent) {
+        int rc = launch_persistent(h, persist_args(h, 1, n_metro, n_or, 0));
+        if (rc) return rc;
+        account_passes(h, n_metro, 0);
+        return UL_OK;
+    }
     const std::vector<long long> key = {kGraphSweep, n_metro, n_or, bits_of(h->beta), bits_of(h->width),
                                         static_cast<long long>(h->seed)};
     int rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* base) {
@@ -274,6 +341,11 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
     if ((e = cudaMalloc(&h->d_accepted, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "counters");
     if ((e = cudaMalloc(&h->d_scalar, 16 * sizeof(double))) != cudaSuccess) return bail(e, "scalars");
     if ((e = cudaMalloc(&h->d_pass_base, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "pass base");
+    if ((e = cudaMalloc(&h->d_bar, 2 * sizeof(unsigned int))) != cudaSuccess) return bail(e, "barrier");
+    if ((e = cudaMalloc(&h->d_status, sizeof(int))) != cudaSuccess) return bail(e, "status");
+    if ((e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned int), h->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream)) != cudaSuccess) return bail(e, "memset");
+    h->use_persistent = false; // graph replay measured faster on GB300 (see the design notes)
     if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "capture stream");
     if ((e = cudaMalloc(&h->plaq_partials, ul::plaquette_partials(h->g) * sizeof(double))) != cudaSuccess)
@@ -371,6 +443,29 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
                                             reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
                                             reinterpret_cast<long long>(tk), reinterpret_cast<long long>(ok),
                                             reinterpret_cast<long long>(osum)};
+        if (h->use_persistent) {
+            ul::PersistArgs a = persist_args(h, count, sm, so, slab_t);
+            a.measure = 1;
+            a.r_max = r_max;
+            a.fields = fields ? 1 : 0;
+            a.slot0 = 0;
+            a.asum = asum;
+            a.tk = tk;
+            a.ok = ok;
+            a.osum = osum;
+            rc = launch_persistent(h, a);
+            if (rc) return rc;
+            if (fields) {
+                cudaError_t e = is_f64(h)
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream)
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+                h->launches += 1;
+            }
+            account_passes(h, sm * count, slab_t);
+            k += count;
+            continue;
+        }
         rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* base) -> long {
             long n = 0;
             for (int j = 0; j < count; ++j) {
@@ -408,6 +503,11 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
         std::free(host);
         return cuda_fail(h, e, "ul_multilevel: result copy");
     }
+    rc = check_device_status(h);
+    if (rc) {
+        std::free(host);
+        return rc;
+    }
     std::memcpy(out_corr, host, 2ull * r_max * sizeof(double));
     if (fields) {
         std::memcpy(out_fields, host + 2 * r_max, 2ull * r_max * nd * 8 * sizeof(double));
@@ -433,6 +533,8 @@ int ul_plaquette(ul_lattice* h, double* out)
     double v = 0.0;
     UL_CK(h, cudaMemcpyAsync(&v, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     UL_CK(h, cudaStreamSynchronize(h->stream));
+    const int rc = check_device_status(h);
+    if (rc) return rc;
     *out = v;
     return UL_OK;
 }
@@ -450,6 +552,15 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
     } else if (!std::strcmp(key, "sub_or")) {
         if (!(v >= 0.0) || v != static_cast<int>(v)) return fail(h, UL_EINVAL, "sub_or must be an integer >= 0");
         h->sub_or = static_cast<int>(v);
+    } else if (!std::strcmp(key, "persistent")) {
+        if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "persistent must be 0 or 1");
+        h->use_persistent = v != 0.0;
+    } else if (!std::strcmp(key, "barrier_spin_limit")) {
+        if (!(v >= 1.0) || v > 1e15) return fail(h, UL_EINVAL, "barrier_spin_limit must be in [1, 1e15]");
+        h->spin_limit = static_cast<unsigned long long>(v);
+    } else if (!std::strcmp(key, "barrier_unreachable")) {
+        if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "barrier_unreachable must be 0 or 1");
+        h->barrier_unreachable = v != 0.0;
     } else if (!std::strcmp(key, "graphs")) {
         if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "graphs must be 0 or 1");
         h->use_graphs = v != 0.0;
@@ -476,7 +587,7 @@ int ul_get_links(ul_lattice* h, double* theta_host)
     h->launches += 1;
     UL_CK(h, cudaMemcpyAsync(theta_host, h->canon, 4ull * h->g.V * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     UL_CK(h, cudaStreamSynchronize(h->stream));
-    return UL_OK;
+    return check_device_status(h);
 }
 
 int ul_set_links(ul_lattice* h, const double* theta_host)
@@ -531,7 +642,7 @@ int ul_synchronize(ul_lattice* h)
 {
     if (!h) return fail(nullptr, UL_EINVAL, "ul_synchronize: NULL handle");
     UL_CK(h, cudaStreamSynchronize(h->stream));
-    return UL_OK;
+    return check_device_status(h);
 }
 
 int ul_set_stream(ul_lattice* h, void* cuda_stream)

@@ -1,11 +1,40 @@
-// ul_batch_types.h — parameter tables of the batched kernels (shared by the kernel
-// translation units and the batch engine).  A table travels by value in the kernel's
+// ul_batch_types.h — argument blocks of the update, persistent and batched kernels
+// (shared by the kernel translation units and the host layer).  A table travels by value in the kernel's
 // parameter block, so it is limited to kMaxBatchJobs lattices per launch.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace ul {
+
+// Arguments of one class update (uniform over a launch).
+struct UpdateArgs {
+    int parity, metro, slab_t;
+    unsigned long long frozen_mask; // bit t: spatial links on slice t frozen (Nt <= 64)
+    uint64_t pass;
+    const unsigned long long* pass_base;
+    uint64_t seed;
+    double beta, width;     // FP64 kernels
+    float beta_f, width_f;  // FP32 kernels
+    unsigned long long* accepted;
+};
+
+// Arguments of a persistent sweep launch (see persistent_kernel).
+struct PersistArgs {
+    UpdateArgs u;             // u.pass: first Metropolis pass number of this launch
+    int n_units;              // compound sweeps, or sub-samples when measure = 1
+    int n_metro, n_or;        // passes per unit
+    int measure;              // 1: measurement after each unit
+    int r_max, fields, slot0; // measurement: correlator separations, insertions, first sample slot
+    double2* asum;
+    void* tk;
+    void* ok;
+    double* osum;
+    unsigned int* bar;        // arrival counter, zero at launch
+    int* status;              // 0 = ok; set when a wait gives up
+    unsigned int expected;    // blocks that arrive at each barrier
+    unsigned long long spin_limit;
+};
 
 constexpr int kMaxBatchJobs = 48;
 

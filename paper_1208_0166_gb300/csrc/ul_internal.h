@@ -61,6 +61,10 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
                              const double2* bsum, const double* osum, double* partials, double* out_dev,
                              cudaStream_t st);
 
+// Persistent cooperative sweep kernel (256 threads per block; `threads` is ignored).
+template <typename R>
+cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st);
+
 // One batched class update over every lattice of the table (blocks: sum of the lattices'
 // block counts at `threads` threads per block).
 template <typename R>

@@ -6,6 +6,7 @@
 // and overrelaxation), Section 2.2 (multilevel: slabs with frozen spatial links,
 // transporters T, insertion operator, multilevel field estimator).
 #pragma once
+#include <algorithm>
 #include "ul_device.cuh"
 #include "ul_batch_types.h"
 #include "ul_internal.h"
@@ -89,15 +90,11 @@ __global__ void __launch_bounds__(kThreads) refresh_cs_kernel(Geo g, const R* __
 // neighbour sites are reached by adding direction strides to the lexicographic index
 // with a wrap correction, so no coordinate array is indexed at run time.
 // ---------------------------------------------------------------------------
-struct UpdateArgs {
-    int parity, metro, slab_t;
-    unsigned long long frozen_mask; // bit t: spatial links on slice t frozen (Nt <= 64)
-    uint64_t pass;
-    const unsigned long long* pass_base;
-    uint64_t seed;
-    double beta, width;
-    unsigned long long* accepted;
-};
+
+template <typename R>
+__device__ __forceinline__ R beta_of(const UpdateArgs& a) { return sizeof(R) == 8 ? static_cast<R>(a.beta) : static_cast<R>(a.beta_f); }
+template <typename R>
+__device__ __forceinline__ R width_of(const UpdateArgs& a) { return sizeof(R) == 8 ? static_cast<R>(a.width) : static_cast<R>(a.width_f); }
 
 template <int LC>
 struct Extent {
@@ -121,28 +118,38 @@ __device__ __forceinline__ int step_down(int c, int L, int Nt)
     return c == 0 ? (n - 1) * st : -st;
 }
 
-template <typename R>
-__device__ __forceinline__ Cx<R> load_link(const cs_t<R>* __restrict__ cs, int Vh, int dir, int par, int j)
+// Loads of link data.  CG = true reads through L2 only (ld.global.cg): inside a
+// persistent kernel other SMs rewrite links between classes and L1 is not coherent.
+template <typename T, bool CG>
+__device__ __forceinline__ T ld_link(const T* p)
 {
-    return link_u<R>(cs, (dir * 2 + par) * Vh + (j >> 1));
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
 }
 
-template <typename R, int MU, int NU>
+template <typename R, bool CG = false>
+__device__ __forceinline__ Cx<R> load_link(const cs_t<R>* __restrict__ cs, int Vh, int dir, int par, int j)
+{
+    const cs_t<R> v = ld_link<cs_t<R>, CG>(cs + (dir * 2 + par) * Vh + (j >> 1));
+    return Cx<R>{v.x, v.y};
+}
+
+template <typename R, int MU, int NU, bool CG>
 __device__ __forceinline__ void staple_term(Cx<R>& A, const cs_t<R>* __restrict__ cs, int Vh, int p, int i,
                                             const int c[4], int L, int Nt, int up_mu)
 {
     const int q = p ^ 1;
     const int up_nu = step_up<NU>(c[NU], L, Nt);
     const int dn_nu = step_down<NU>(c[NU], L, Nt);
-    const Cx<R> fwd = cmul(cmul(load_link<R>(cs, Vh, NU, q, i + up_mu), cconj(load_link<R>(cs, Vh, MU, q, i + up_nu))),
-                           cconj(load_link<R>(cs, Vh, NU, p, i)));
-    const Cx<R> bwd = cmul(cmul(cconj(load_link<R>(cs, Vh, NU, p, i + up_mu + dn_nu)),
-                                cconj(load_link<R>(cs, Vh, MU, q, i + dn_nu))),
-                           load_link<R>(cs, Vh, NU, q, i + dn_nu));
+    const Cx<R> fwd = cmul(cmul(load_link<R, CG>(cs, Vh, NU, q, i + up_mu), cconj(load_link<R, CG>(cs, Vh, MU, q, i + up_nu))),
+                           cconj(load_link<R, CG>(cs, Vh, NU, p, i)));
+    const Cx<R> bwd = cmul(cmul(cconj(load_link<R, CG>(cs, Vh, NU, p, i + up_mu + dn_nu)),
+                                cconj(load_link<R, CG>(cs, Vh, MU, q, i + dn_nu))),
+                           load_link<R, CG>(cs, Vh, NU, q, i + dn_nu));
     A = cadd(A, cadd(fwd, bwd));
 }
 
-template <typename R, int LC, int MU>
+template <typename R, int LC, int MU, bool CG = false>
 __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int h,
                                             const UpdateArgs& a)
 {
@@ -166,12 +173,12 @@ __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta,
     const int c[4] = {t, x, y, z};
     const int up_mu = step_up<MU>(c[MU], L, Nt);
     Cx<R> A{R(0), R(0)};
-    if (MU != 0) staple_term<R, MU, (MU == 0 ? 1 : 0)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
-    if (MU != 1) staple_term<R, MU, (MU == 1 ? 2 : 1)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
-    if (MU != 2) staple_term<R, MU, (MU == 2 ? 3 : 2)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
-    if (MU != 3) staple_term<R, MU, (MU == 3 ? 0 : 3)>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    if (MU != 0) staple_term<R, MU, (MU == 0 ? 1 : 0), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    if (MU != 1) staple_term<R, MU, (MU == 1 ? 2 : 1), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    if (MU != 2) staple_term<R, MU, (MU == 2 ? 3 : 2), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
+    if (MU != 3) staple_term<R, MU, (MU == 3 ? 0 : 3), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
     const int off = (MU * 2 + p) * Vh + h;
-    const R th = theta[off];
+    const R th = ld_link<R, CG>(theta + off);
     if (a.metro) {
         uint64_t pass = a.pass;
         if (a.pass_base) pass += *a.pass_base;
@@ -179,9 +186,9 @@ __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta,
         const Philox4 w = philox4x64_10(link_id, pass, 0, 0, a.seed, kStreamMetropolis);
         const R u1 = P::uniform(w.w[0]);
         const R u2 = P::uniform(w.w[1]);
-        const R width = static_cast<R>(a.width), beta = static_cast<R>(a.beta);
+        const R width = width_of<R>(a), beta = beta_of<R>(a);
         const R prop = P::wrap(th + width * (R(2) * u1 - R(1)));
-        const cs_t<R> old = cs[off];
+        const cs_t<R> old = ld_link<cs_t<R>, CG>(cs + off);
         const R s_old = -beta * (old.x * A.re - old.y * A.im);
         R sn, cn;
         P::sincos(prop, &sn, &cn);
@@ -327,15 +334,23 @@ __device__ __constant__ static const int kPlaneNu[4] = {1, 2, 3, 3};
 //   tk[((slot*S + s)*R + r-1)*L3 + x0] = T,   ok[((slot*S + s)*L3 + x0)*8 + ch] = O.
 // The per-sample products are formed in the link precision R (FP64 or FP32); every
 // accumulator is FP64.
-template <typename R>
+template <typename R, bool CG = false>
+__device__ __forceinline__ Cx<R> link_at(const cs_t<R>* __restrict__ cs, int off)
+{
+    const cs_t<R> v = ld_link<cs_t<R>, CG>(cs + off);
+    return Cx<R>{v.x, v.y};
+}
+
+template <typename R, bool CG = false>
 __device__ __forceinline__ Cx<R> slab_line(const Geo& g, const cs_t<R>* __restrict__ cs, int x, int t0, int slab_t)
 {
-    Cx<R> w = link_u<R>(cs, link_offset(g, 0, site_from_lex(g, x + g.L3 * t0)));
-    for (int t = t0 + 1; t < t0 + slab_t; ++t) w = cmul(w, link_u<R>(cs, link_offset(g, 0, site_from_lex(g, x + g.L3 * t))));
+    Cx<R> w = link_at<R, CG>(cs, link_offset(g, 0, site_from_lex(g, x + g.L3 * t0)));
+    for (int t = t0 + 1; t < t0 + slab_t; ++t)
+        w = cmul_rn(w, link_at<R, CG>(cs, link_offset(g, 0, site_from_lex(g, x + g.L3 * t))));
     return w;
 }
 
-template <typename R>
+template <typename R, bool CG = false>
 __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* __restrict__ cs, int slab_t,
                                                    int r_max, int fields, int slot, double2* __restrict__ asum,
                                                    Cx<R>* __restrict__ tk, R* __restrict__ ok,
@@ -346,12 +361,12 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
     const int x0 = k - s * g.L3;
     const int px = x0 % g.L, pyz = x0 - px;
     const int t0 = s * slab_t;
-    const Cx<R> w0 = cconj(slab_line<R>(g, cs, x0, t0, slab_t));
+    const Cx<R> w0 = cconj(slab_line<R, CG>(g, cs, x0, t0, slab_t));
     for (int r = 1; r <= r_max; ++r) {
         const int x1 = (px + r) % g.L + pyz;
-        const Cx<R> T = cmul(w0, slab_line<R>(g, cs, x1, t0, slab_t));
+        const Cx<R> T = cmul_rn(w0, slab_line<R, CG>(g, cs, x1, t0, slab_t));
         const long ai = static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0;
-        double2 av = asum[ai];
+        double2 av = ld_link<double2, CG>(asum + ai);
         av.x += static_cast<double>(T.re);
         av.y += static_cast<double>(T.im);
         asum[ai] = av;
@@ -368,9 +383,10 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
             const int mu = kPlaneMu[c], nu = kPlaneNu[c];
             const Site xpm = site_step(g, x, mu, +1);
             const Site xpn = site_step(g, x, nu, +1);
-            const Cx<R> P = cmul(cmul(cmul(link_u<R>(cs, link_offset(g, mu, x)), link_u<R>(cs, link_offset(g, nu, xpm))),
-                                      cconj(link_u<R>(cs, link_offset(g, mu, xpn)))),
-                                 cconj(link_u<R>(cs, link_offset(g, nu, x))));
+            const Cx<R> P = cmul_rn(cmul_rn(cmul_rn(link_at<R, CG>(cs, link_offset(g, mu, x)),
+                                                    link_at<R, CG>(cs, link_offset(g, nu, xpm))),
+                                            cconj(link_at<R, CG>(cs, link_offset(g, mu, xpn)))),
+                                    cconj(link_at<R, CG>(cs, link_offset(g, nu, x))));
             acc[2 * c] += P.im;
             acc[2 * c + 1] += P.re;
         }
@@ -380,7 +396,7 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
         o[ch] = acc[ch];
-        osum[ch * SL3 + k] += static_cast<double>(acc[ch]);
+        osum[ch * SL3 + k] = ld_link<double, CG>(osum + ch * SL3 + k) + static_cast<double>(acc[ch]);
     }
 }
 
@@ -496,6 +512,93 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Persistent sweep kernel: one cooperative launch runs n_units units, each n_metro
+// Metropolis + n_or overrelaxation passes (8 classes each) and, with `measure`, one
+// measurement; classes are separated by a grid-wide barrier.  Every link is updated by
+// the same device function as in the one-class-per-launch kernel (loads through L2),
+// so the trajectory is the same bit for bit.
+//
+// The barrier is one arrival counter in device memory, zeroed before the launch.  Every
+// wait is bounded: after spin_limit polls a waiting block writes a nonzero status word
+// and the kernel returns; the host reports UL_ETIMEOUT at its next synchronising call.
+// ---------------------------------------------------------------------------
+
+// Barrier number `epoch` (1, 2, ...) of a launch completes when the arrival counter, which
+// is zero at launch and only grows, reaches epoch * expected.
+__device__ __forceinline__ bool grid_barrier(const PersistArgs& a, unsigned int& epoch)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        epoch += 1;
+        const unsigned int target = epoch * a.expected;
+        __threadfence();
+        atomicAdd(a.bar, 1u);
+        volatile unsigned int* vcount = a.bar;
+        unsigned long long polls = 0;
+        while (*vcount < target) {
+            if (++polls > a.spin_limit) {
+                atomicExch(a.status, 1);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        if (ok && *reinterpret_cast<volatile int*>(a.status) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename R, int LC>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) persistent_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs,
+                                                         PersistArgs a)
+{
+    if (*reinterpret_cast<volatile int*>(a.status) != 0) return;
+    const int stride = static_cast<int>(gridDim.x * blockDim.x);
+    const int tid = static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+    unsigned int epoch = 0;
+    UpdateArgs u = a.u;
+    for (int unit = 0; unit < a.n_units; ++unit) {
+        for (int k = 0; k < a.n_metro + a.n_or; ++k) {
+            u.metro = k < a.n_metro ? 1 : 0;
+            for (int mu = 0; mu < 4; ++mu)
+                for (int par = 0; par < 2; ++par) {
+                    u.parity = par;
+                    int accepted = 0;
+                    for (int h = tid; h < g.Vh; h += stride) {
+                        bool acc;
+                        switch (mu) {
+                        case 0: acc = update_link<R, LC, 0, true>(g, theta, cs, h, u); break;
+                        case 1: acc = update_link<R, LC, 1, true>(g, theta, cs, h, u); break;
+                        case 2: acc = update_link<R, LC, 2, true>(g, theta, cs, h, u); break;
+                        default: acc = update_link<R, LC, 3, true>(g, theta, cs, h, u); break;
+                        }
+                        accepted += acc ? 1 : 0;
+                    }
+                    if (u.metro) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) accepted += __shfl_xor_sync(0xffffffffu, accepted, o);
+                        if ((threadIdx.x & 31) == 0 && accepted)
+                            atomicAdd(u.accepted, static_cast<unsigned long long>(accepted));
+                    }
+                    if (!grid_barrier(a, epoch)) return;
+                }
+            if (u.metro) u.pass += 1;
+        }
+        if (a.measure) {
+            const int SL3 = (g.Nt / u.slab_t) * g.L3;
+            for (int q = tid; q < SL3; q += stride)
+                measure_store_site<R, true>(g, cs, u.slab_t, a.r_max, a.fields, a.slot0 + unit, a.asum,
+                                            static_cast<Cx<R>*>(a.tk), static_cast<R*>(a.ok), a.osum, q);
+            if (!grid_barrier(a, epoch)) return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Batched kernels: one launch updates class (mu, parity) of every resident lattice of a
 // batch (lattices of different shapes, couplings, seeds and schedule positions).  The
 // per-lattice parameters travel in the kernel's parameter block; block b belongs to the
@@ -528,6 +631,8 @@ __device__ __forceinline__ bool batch_update_link(const BatchUpdateJob& J, int p
     a.seed = J.seed;
     a.beta = J.beta;
     a.width = J.width;
+    a.beta_f = static_cast<float>(J.beta);
+    a.width_f = static_cast<float>(J.width);
     a.accepted = J.accepted;
     R* theta = static_cast<R*>(J.theta);
     cs_t<R>* cs = static_cast<cs_t<R>*>(J.cs);
@@ -612,6 +717,8 @@ cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int pa
     a.seed = seed;
     a.beta = beta;
     a.width = width;
+    a.beta_f = static_cast<float>(beta);
+    a.width_f = static_cast<float>(width);
     a.accepted = accepted;
     cs_t<R>* c = static_cast<cs_t<R>*>(cs);
     const dim3 grid(blocks_for(g.Vh));
@@ -687,7 +794,52 @@ cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaS
     return cudaGetLastError();
 }
 
+template <typename R, int LC>
+cudaError_t launch_persistent_lc(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st)
+{
+    static int blocks_per_sm = 0;
+    static int n_sm = 0;
+    auto fn = persistent_kernel<R, LC>;
+    threads = 256;
+    if (!blocks_per_sm) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, threads, 0);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const int work = in.measure ? std::max(g.Vh, (g.Nt / in.u.slab_t) * g.L3) : g.Vh;
+    int grid = blocks_per_sm * n_sm;
+    grid = std::min(grid, (work + threads - 1) / threads);
+    grid = std::max(grid, 1);
+    PersistArgs a = in;
+    a.expected = in.expected == 0 ? static_cast<unsigned int>(grid)
+                 : (in.expected == 0xffffffffu ? static_cast<unsigned int>(grid) + 1u : in.expected);
+    Geo gg = g;
+    cs_t<R>* c = static_cast<cs_t<R>*>(cs);
+    void* args[] = {static_cast<void*>(&gg), static_cast<void*>(&theta), static_cast<void*>(&c), static_cast<void*>(&a)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(fn), dim3(grid), dim3(threads), args, 0, st);
+}
+
+// in.expected == 0: the barrier waits for the whole grid; 0xffffffff: for one block more
+// than the grid, so every wait runs into its limit (exercises the timeout path).
+template <typename R>
+cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st)
+{
+    switch (g.L) {
+    case 8: return launch_persistent_lc<R, 8>(g, theta, cs, in, threads, st);
+    case 12: return launch_persistent_lc<R, 12>(g, theta, cs, in, threads, st);
+    case 16: return launch_persistent_lc<R, 16>(g, theta, cs, in, threads, st);
+    case 20: return launch_persistent_lc<R, 20>(g, theta, cs, in, threads, st);
+    case 24: return launch_persistent_lc<R, 24>(g, theta, cs, in, threads, st);
+    case 32: return launch_persistent_lc<R, 32>(g, theta, cs, in, threads, st);
+    default: return launch_persistent_lc<R, 0>(g, theta, cs, in, threads, st);
+    }
+}
+
 #define UL_INSTANTIATE_KERNELS(R)                                                                                  \
+    template cudaError_t launch_persistent<R>(const Geo&, R*, void*, const PersistArgs&, int, cudaStream_t);       \
     template cudaError_t launch_batched_update<R>(const BatchUpdateTable&, int, int, int, int, cudaStream_t);      \
     template cudaError_t launch_batched_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                   \
     template cudaError_t launch_hot_start<R>(const Geo&, R*, void*, uint64_t, cudaStream_t);                        \

@@ -220,6 +220,19 @@ __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b)
 {
     return Cx<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
+// Complex product with every operation rounded separately (no fused multiply-add in any
+// compilation context): measurement products use it so that they do not depend on how a
+// kernel inlines them.
+__device__ __forceinline__ Cx<float> cmul_rn(Cx<float> a, Cx<float> b)
+{
+    return Cx<float>{__fsub_rn(__fmul_rn(a.re, b.re), __fmul_rn(a.im, b.im)),
+                     __fadd_rn(__fmul_rn(a.re, b.im), __fmul_rn(a.im, b.re))};
+}
+__device__ __forceinline__ Cx<double> cmul_rn(Cx<double> a, Cx<double> b)
+{
+    return Cx<double>{__dsub_rn(__dmul_rn(a.re, b.re), __dmul_rn(a.im, b.im)),
+                      __dadd_rn(__dmul_rn(a.re, b.im), __dmul_rn(a.im, b.re))};
+}
 template <typename T>
 __device__ __forceinline__ Cx<T> cconj(Cx<T> a)
 {

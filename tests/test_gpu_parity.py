@@ -283,3 +283,52 @@ def test_graph_replay_equals_direct_launches(prec):
     for key in ("corr", "fields", "vac"):
         assert np.array_equal(a[3][key], b[3][key])
     assert np.array_equal(a[4], b[4]) and a[5] == b[5]
+
+
+@pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
+def test_persistent_sweeps_equal_per_class_launches(prec):
+    """One cooperative launch per compound sweep / chunk of sub-samples (grid barriers between
+    classes) gives the same trajectory and observables bit for bit."""
+    L, Nt = 8, 8
+    out = []
+    for persistent in (1, 0):
+        g = _lib.Lattice(L, Nt, 1.0, 41, prec)
+        g.set_option("persistent", persistent)
+        g.set_option("insertion_chunk_mb", 1)
+        for _ in range(3):
+            g.sweep(1, 3)
+        r1 = g.multilevel_fields(2, 4, 3, 2)
+        r2 = g.multilevel(1, 3, 2)
+        out.append((g.get_links(), g.stats(), r1, r2, g.plaquette()))
+    a, b = out
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+    for key in ("corr", "fields", "vac"):
+        assert np.array_equal(a[2][key], b[2][key])
+    assert np.array_equal(a[3], b[3]) and a[4] == b[4]
+
+
+def test_persistent_barrier_timeout_is_reported_and_recoverable():
+    """A barrier that cannot complete (one block more than the grid) makes every wait reach
+    its limit; the next blocking call reports UL_ETIMEOUT and the handle keeps working."""
+    L, Nt = 8, 8
+    th = random_angles(L, Nt, 5)
+    ref = _lib.Lattice(L, Nt, 1.0, 9, _lib.UL_FP32_ACC64)
+    ref.set_option("persistent", 0)
+    ref.set_links(th)
+    ref.sweep(1, 3)
+    want = ref.get_links()
+    g = _lib.Lattice(L, Nt, 1.0, 9, _lib.UL_FP32_ACC64)
+    g.set_option("persistent", 1)
+    g.set_option("barrier_spin_limit", 2000)
+    g.set_option("barrier_unreachable", 1)
+    g.set_links(th)
+    g.sweep(1, 3)
+    with pytest.raises(_lib.ULError) as e:
+        g.synchronize()
+    assert e.value.code == _lib.UL_ETIMEOUT
+    g.set_option("barrier_unreachable", 0)
+    g.set_option("barrier_spin_limit", 1 << 24)
+    g.set_links(th)
+    g.set_state(9, 0)
+    g.sweep(1, 3)
+    assert np.array_equal(g.get_links(), want)
