@@ -145,6 +145,11 @@ int ul_free(ul_lattice* h);
  *   "sub_metro"    Metropolis passes per multilevel sub-sample (>= 0, default 1)
  *   "sub_or"       overrelaxation passes per multilevel sub-sample (>= 0, default 3)
  *   "beta"         coupling (>= 0)
+ *   "multihit"     1: ul_multilevel* form the correlator at r >= 2 from the analytic
+ *                  multihit values of the temporal links, (I1(beta|A|)/I0(beta|A|)) conj(A)/|A|
+ *                  with A the staple (Section 2.2: multihit for the potential); r = 1, whose
+ *                  two lines share plaquettes, and the field insertions keep the links
+ *                  themselves.  0 (default): links themselves everywhere.
  *   "persistent"   1: each compound sweep, and each chunk of sub-samples with their
  *                  measurements, runs as one cooperative launch whose classes are separated
  *                  by a grid barrier; 0 (default): one launch per class, replayed from

@@ -78,7 +78,10 @@ def _load():
     lib.ulo_polyakov_correlator.argtypes = [i, i, dp, i, dp]
     lib.ulo_field_correlator.argtypes = [i, i, dp, i, i, dp]
     lib.ulo_field_correlator_one.argtypes = [i, i, dp, i, i, i, dp, dp]
-    lib.ulo_multilevel.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, dp, dp, dp, dp]
+    lib.ulo_multilevel.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, dp, dp, dp, dp, i]
+    lib.ulo_bessel_ratio.argtypes = [d]
+    lib.ulo_bessel_ratio.restype = d
+    lib.ulo_multihit_link.argtypes = [i, i, d, dp, l, dp, dp]
     lib.ulo_multilevel.restype = i
     lib.ulo_gauge_transform.argtypes = [i, i, u64, dp]
     _lib = lib
@@ -187,11 +190,17 @@ class Lattice:
                                          ctypes.byref(re), ctypes.byref(im))
         return complex(re.value, im.value)
 
+    def multihit_link(self, i: int) -> complex:
+        re, im = ctypes.c_double(), ctypes.c_double()
+        _load().ulo_multihit_link(self.L, self.Nt, self.beta, _dp(self.theta), int(i), ctypes.byref(re),
+                                  ctypes.byref(im))
+        return complex(re.value, im.value)
+
     def gauge_transform(self, seed: int) -> None:
         _load().ulo_gauge_transform(self.L, self.Nt, int(seed), _dp(self.theta))
 
     def multilevel(self, slab_t: int, n_sub: int, r_max: int, d_max: int = -1,
-                   sub_metro: int = 1, sub_or: int = 3, record_samples: bool = False):
+                   sub_metro: int = 1, sub_or: int = 3, record_samples: bool = False, multihit: bool = False):
         """One-level multilevel estimator; returns dict(corr, fields, vac[, samples_T])."""
         S = self.Nt // slab_t
         corr = np.empty(2 * r_max, dtype=np.float64)
@@ -202,7 +211,8 @@ class Lattice:
         rc = _load().ulo_multilevel(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
                                     ctypes.byref(self.metro_pass), int(slab_t), int(n_sub), int(sub_metro),
                                     int(sub_or), int(r_max), int(max(d_max, 0)), _dp(corr),
-                                    _dp_or_null(fields), _dp_or_null(vac), _dp_or_null(samples))
+                                    _dp_or_null(fields), _dp_or_null(vac), _dp_or_null(samples),
+                                    1 if multihit else 0)
         if rc != 0:
             raise ValueError("invalid multilevel arguments")
         out = {"corr": _cplx(corr.reshape(-1, 2))}
@@ -212,6 +222,10 @@ class Lattice:
         if samples is not None:
             out["samples_T"] = _cplx(samples.reshape(n_sub, S, self.L ** 3, r_max, 2))
         return out
+
+
+def bessel_ratio(x: float) -> float:
+    return _load().ulo_bessel_ratio(float(x))
 
 
 def metropolis_link(theta, a: complex, beta, width, u1, u2):

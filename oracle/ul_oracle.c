@@ -571,25 +571,77 @@ void ulo_field_correlator_one(int L, int Nt, const double* theta, int r, int d, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Analytic multihit (Section 2.2: temporal links replaced by their average  */
+/* over the link's own Boltzmann weight with all other links fixed)          */
+/* ------------------------------------------------------------------------ */
+
+/* I1(x)/I0(x) for x >= 0 from the power series
+ *   I0(x) = sum_k (x^2/4)^k / (k!)^2,   I1(x) = (x/2) sum_k (x^2/4)^k / (k! (k+1)!),
+ * summed until the terms stop changing the sums; for x > 600 (beyond any coupling used
+ * here) the asymptotic series 1 - 1/(2x) - 1/(8x^2) - 1/(8x^3). */
+double ulo_bessel_ratio(double x)
+{
+    if (x <= 0.0) return 0.0;
+    if (x > 600.0) return 1.0 - 1.0 / (2.0 * x) - 1.0 / (8.0 * x * x) - 1.0 / (8.0 * x * x * x);
+    const double q = 0.25 * x * x;
+    double t0 = 1.0, s0 = 1.0;       /* I0 terms and sum */
+    double t1 = 0.5 * x, s1 = t1;    /* I1 terms and sum */
+    for (int k = 1; k < 2000; k++) {
+        t0 *= q / ((double)k * (double)k);
+        t1 *= q / ((double)k * (double)(k + 1));
+        double n0 = s0 + t0, n1 = s1 + t1;
+        if (n0 == s0 && n1 == s1) break;
+        s0 = n0;
+        s1 = n1;
+    }
+    return s1 / s0;
+}
+
+/* Multihit link: the mean of e^{i theta} under exp(beta Re(e^{i theta} A)) with A the
+ * staple of the temporal link at site i: (I1(beta |A|) / I0(beta |A|)) A* / |A|. */
+static cplx multihit_link(const lat_t* g, const double* theta, double beta, long i)
+{
+    cplx A = staple(g, theta, 0, i);
+    double a = sqrt(A.re * A.re + A.im * A.im);
+    if (a == 0.0) return cmk(0.0, 0.0);
+    double f = ulo_bessel_ratio(beta * a) / a;
+    return cmk(f * A.re, -f * A.im);
+}
+
+void ulo_multihit_link(int L, int Nt, double beta, const double* theta, long i, double* re, double* im)
+{
+    lat_t g = mk(L, Nt);
+    cplx u = multihit_link(&g, theta, beta, i);
+    *re = u.re;
+    *im = u.im;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One-level multilevel estimator (Section 2.2)                              */
 /* ------------------------------------------------------------------------ */
 
 /* T^(tau)(s, x0, r) = prod over the slab's slices t of U*_0(x0,t) U_0(x0 + r xhat, t):
  * the product of the two-link transporters T(x0,t,r) of the slab. */
-static cplx slab_transporter(const lat_t* g, const double* theta, int slab_t, int s, long x0, int r)
+static cplx slab_transporter(const lat_t* g, const double* theta, int slab_t, int s, long x0, int r,
+                             int multihit, double beta)
 {
     cplx T = cmk(1.0, 0.0);
     long x1 = spatial_shift(g, x0, r, 0);
-    for (int t = s * slab_t; t < (s + 1) * slab_t; t++)
-        T = cmul(T, cmul(cconj(link(g, theta, 0, spatial_to_site(g, x0, t))),
-                         link(g, theta, 0, spatial_to_site(g, x1, t))));
+    /* Multihit only where the two temporal links share no plaquette (r >= 2). */
+    int mh = multihit && r >= 2;
+    for (int t = s * slab_t; t < (s + 1) * slab_t; t++) {
+        long i0 = spatial_to_site(g, x0, t), i1 = spatial_to_site(g, x1, t);
+        cplx a = mh ? multihit_link(g, theta, beta, i0) : link(g, theta, 0, i0);
+        cplx b = mh ? multihit_link(g, theta, beta, i1) : link(g, theta, 0, i1);
+        T = cmul(T, cmul(cconj(a), b));
+    }
     return T;
 }
 
 int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
                    uint64_t* metro_pass, int slab_t, int n_sub, int sub_metro, int sub_or,
                    int r_max, int d_max, double* corr, double* fields, double* vac,
-                   double* samples_T)
+                   double* samples_T, int multihit)
 {
     if (slab_t < 1 || Nt % slab_t != 0 || n_sub < 1 || r_max < 1 || r_max > L / 2 ||
         (fields && (d_max < 0 || d_max >= L)))
@@ -609,7 +661,8 @@ int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, doub
         for (int s = 0; s < S; s++)
             for (long x0 = 0; x0 < L3; x0++)
                 for (int r = 1; r <= r_max; r++) {
-                    cplx T = slab_transporter(&g, theta, slab_t, s, x0, r);
+                    cplx T = slab_transporter(&g, theta, slab_t, s, x0, r, multihit, beta);
+                    cplx Tplain = multihit ? slab_transporter(&g, theta, slab_t, s, x0, r, 0, beta) : T;
                     long a = ((long)s * L3 + x0) * r_max + (r - 1);
                     Asum[a] = cadd(Asum[a], T);
                     if (samples_T) {
@@ -626,7 +679,7 @@ int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, doub
                             for (int t = s * slab_t; t < (s + 1) * slab_t; t++)
                                 O += channel_value(&g, theta, ch, spatial_to_site(&g, y, t));
                             long b = (a * nd + d) * 8 + ch;
-                            Bsum[b] = cadd(Bsum[b], cscale(T, O));
+                            Bsum[b] = cadd(Bsum[b], cscale(Tplain, O));
                         }
                     }
                 }

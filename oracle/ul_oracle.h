@@ -97,11 +97,21 @@ void ulo_field_correlator_one(int L, int Nt, const double* theta, int r, int d, 
  * passes with slab-boundary spatial links frozen, followed by a measurement.
  * samples_T: NULL, or n_sub*S*L^3*r_max*2 doubles recording every T^(tau) sample,
  * layout [k][s][x0][r-1][re,im] (lets tests enumerate the product by brute force).
+ * multihit: nonzero to use, for the correlator at r >= 2, the multihit links of the
+ * temporal direction (ulo_multihit_link); insertions always use the links themselves.
  */
 int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
                    uint64_t* metro_pass, int slab_t, int n_sub, int sub_metro, int sub_or,
                    int r_max, int d_max, double* corr, double* fields, double* vac,
-                   double* samples_T);
+                   double* samples_T, int multihit);
+
+/* I1(x)/I0(x), x >= 0 (power series; asymptotic series beyond x = 600). */
+double ulo_bessel_ratio(double x);
+
+/* Analytic multihit value of the temporal link at site i: its average over its own
+ * Boltzmann weight exp(beta Re(U A)) with the staple A fixed,
+ * (I1(beta|A|) / I0(beta|A|)) A* / |A| (Section 2.2, multihit for the potential). */
+void ulo_multihit_link(int L, int Nt, double beta, const double* theta, long i, double* re, double* im);
 
 /* Random gauge transformation theta_mu(x) += lambda(x) - lambda(x + mu),
  * lambda(x) = -pi + 2 pi u53(Philox(key=(seed,2), ctr=(i,0,0,0)) word 0); result wrapped. */

@@ -23,6 +23,7 @@ struct ul_lattice {
     int sub_metro = 1;
     int sub_or = 3;
     int chunk_mb = 4096; // bound on the per-sample T/O buffers of the insertion contraction
+    bool multihit = false; // correlator at r >= 2 from multihit temporal links
     uint64_t proposed = 0;
     uint64_t launches = 0; // kernels launched on behalf of this handle
 
@@ -413,7 +414,8 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
     const size_t off_o = off_b + al(n_b * sizeof(double2));
     const size_t off_t = off_o + al(n_o * sizeof(double));
     const size_t off_k = off_t + al(fields ? n_a * 2 * rs * chunk : 0);
-    const size_t off_p = off_k + al(fields ? 8ull * S * g.L3 * rs * chunk : 0);
+    const size_t off_u = off_k + al(fields ? 8ull * S * g.L3 * rs * chunk : 0);
+    const size_t off_p = off_u + al(h->multihit ? static_cast<size_t>(g.V) * 2 * rs : 0);
     const size_t off_out = off_p + al(n_p * sizeof(double));
     const size_t bytes = off_out + al(n_out * sizeof(double));
     int rc = ensure_ml(h, bytes);
@@ -424,6 +426,7 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
     double* osum = reinterpret_cast<double*>(base + off_o);
     void* tk = base + off_t;
     void* ok = base + off_k;
+    void* ubar = h->multihit ? static_cast<void*>(base + off_u) : nullptr;
     double* partials = reinterpret_cast<double*>(base + off_p);
     double* dout = reinterpret_cast<double*>(base + off_out);
     UL_CK(h, cudaMemsetAsync(asum, 0, n_a * sizeof(double2), h->stream));
@@ -442,7 +445,7 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
                                             bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
                                             reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
                                             reinterpret_cast<long long>(tk), reinterpret_cast<long long>(ok),
-                                            reinterpret_cast<long long>(osum)};
+                                            reinterpret_cast<long long>(osum), reinterpret_cast<long long>(ubar)};
         if (h->use_persistent) {
             ul::PersistArgs a = persist_args(h, count, sm, so, slab_t);
             a.measure = 1;
@@ -453,6 +456,7 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
             a.tk = tk;
             a.ok = ok;
             a.osum = osum;
+            a.ubar = ubar;
             rc = launch_persistent(h, a);
             if (rc) return rc;
             if (fields) {
@@ -472,9 +476,16 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
                 const long m = enqueue_passes(h, st, sm, so, slab_t, first + static_cast<uint64_t>(j) * sm, base);
                 if (m < 0) return m;
                 n += m;
-                cudaError_t e = is_f64(h)
-                    ? ul::launch_measure_store<double>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, st)
-                    : ul::launch_measure_store<float>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, st);
+                cudaError_t e;
+                if (ubar) {
+                    e = is_f64(h) ? ul::launch_multihit<double>(g, h->cs, h->beta, ubar, st)
+                                  : ul::launch_multihit<float>(g, h->cs, h->beta, ubar, st);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "multihit launch");
+                    ++n;
+                }
+                e = is_f64(h)
+                    ? ul::launch_measure_store<double>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st)
+                    : ul::launch_measure_store<float>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st);
                 if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
                 ++n;
             }
@@ -552,6 +563,9 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
     } else if (!std::strcmp(key, "sub_or")) {
         if (!(v >= 0.0) || v != static_cast<int>(v)) return fail(h, UL_EINVAL, "sub_or must be an integer >= 0");
         h->sub_or = static_cast<int>(v);
+    } else if (!std::strcmp(key, "multihit")) {
+        if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "multihit must be 0 or 1");
+        h->multihit = v != 0.0;
     } else if (!std::strcmp(key, "persistent")) {
         if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "persistent must be 0 or 1");
         h->use_persistent = v != 0.0;

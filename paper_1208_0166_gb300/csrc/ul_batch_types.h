@@ -30,6 +30,7 @@ struct PersistArgs {
     void* tk;
     void* ok;
     double* osum;
+    void* ubar;               // multihit temporal links (null: correlator from the links themselves)
     unsigned int* bar;        // arrival counter, zero at launch
     int* status;              // 0 = ok; set when a wait gives up
     unsigned int expected;    // blocks that arrive at each barrier

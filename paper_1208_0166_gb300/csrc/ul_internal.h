@@ -46,7 +46,11 @@ cudaError_t launch_plaquette(const Geo& g, const void* cs, double* partials, dou
 // channel sums O stored in sample slot `slot` of tk / ok (precision R) and O added to osum.
 template <typename R>
 cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r_max, bool fields, int slot,
-                                 double2* asum, void* tk, void* ok, double* osum, cudaStream_t st);
+                                 double2* asum, void* tk, void* ok, double* osum, const void* ubar, cudaStream_t st);
+
+// Multihit temporal links ubar[i] (lexicographic site i, complex in precision R).
+template <typename R>
+cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* ubar, cudaStream_t st);
 
 // bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] += sum over the first `count` stored samples of
 // T(s,x0,r) O(s, x0 + floor(r/2) xhat + d yhat, ch).

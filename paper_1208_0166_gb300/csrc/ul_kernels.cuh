@@ -350,11 +350,28 @@ __device__ __forceinline__ Cx<R> slab_line(const Geo& g, const cs_t<R>* __restri
     return w;
 }
 
+// Product over the slab's slices of the multihit temporal links ubar[x + L3 t].
+template <typename R, bool CG = false>
+__device__ __forceinline__ Cx<R> slab_line_mh(const Geo& g, const Cx<R>* __restrict__ ubar, int x, int t0, int slab_t)
+{
+    const cs_t<R>* u = reinterpret_cast<const cs_t<R>*>(ubar);
+    cs_t<R> v = ld_link<cs_t<R>, CG>(u + x + g.L3 * t0);
+    Cx<R> w{v.x, v.y};
+    for (int t = t0 + 1; t < t0 + slab_t; ++t) {
+        v = ld_link<cs_t<R>, CG>(u + x + g.L3 * t);
+        w = cmul_rn(w, Cx<R>{v.x, v.y});
+    }
+    return w;
+}
+
+// ubar (may be null): multihit temporal links by lexicographic site; when set, the
+// correlator at r >= 2 uses them (the insertion samples keep the links themselves).
 template <typename R, bool CG = false>
 __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* __restrict__ cs, int slab_t,
                                                    int r_max, int fields, int slot, double2* __restrict__ asum,
                                                    Cx<R>* __restrict__ tk, R* __restrict__ ok,
-                                                   double* __restrict__ osum, int k)
+                                                   double* __restrict__ osum, int k,
+                                                   const Cx<R>* __restrict__ ubar = nullptr)
 {
     const int S = g.Nt / slab_t;
     const int s = k / g.L3;
@@ -362,13 +379,15 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
     const int px = x0 % g.L, pyz = x0 - px;
     const int t0 = s * slab_t;
     const Cx<R> w0 = cconj(slab_line<R, CG>(g, cs, x0, t0, slab_t));
+    const Cx<R> w0m = ubar ? cconj(slab_line_mh<R, CG>(g, ubar, x0, t0, slab_t)) : w0;
     for (int r = 1; r <= r_max; ++r) {
         const int x1 = (px + r) % g.L + pyz;
         const Cx<R> T = cmul_rn(w0, slab_line<R, CG>(g, cs, x1, t0, slab_t));
+        const Cx<R> Tc = (ubar && r >= 2) ? cmul_rn(w0m, slab_line_mh<R, CG>(g, ubar, x1, t0, slab_t)) : T;
         const long ai = static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0;
         double2 av = ld_link<double2, CG>(asum + ai);
-        av.x += static_cast<double>(T.re);
-        av.y += static_cast<double>(T.im);
+        av.x += static_cast<double>(Tc.re);
+        av.y += static_cast<double>(Tc.im);
         asum[ai] = av;
         if (fields) tk[(static_cast<long>(slot * S + s) * r_max + (r - 1)) * g.L3 + x0] = T;
     }
@@ -404,11 +423,55 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads)
     measure_store_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int fields, int slot,
                          double2* __restrict__ asum, Cx<R>* __restrict__ tk, R* __restrict__ ok,
-                         double* __restrict__ osum)
+                         double* __restrict__ osum, const Cx<R>* __restrict__ ubar)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + x0
     if (k >= (g.Nt / slab_t) * g.L3) return;
-    measure_store_site<R>(g, cs, slab_t, r_max, fields, slot, asum, tk, ok, osum, k);
+    measure_store_site<R>(g, cs, slab_t, r_max, fields, slot, asum, tk, ok, osum, k, ubar);
+}
+
+// ---------------------------------------------------------------------------
+// Analytic multihit (Section 2.2): the temporal link at lexicographic site i replaced by
+// its mean over its own Boltzmann weight exp(beta Re(U A)) with the staple A fixed,
+//   ubar = (I1(beta |A|) / I0(beta |A|)) A* / |A|   (0 when A = 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double bessel_ratio_i1_i0(double x)
+{
+    if (x <= 0.0) return 0.0;
+    if (x > 600.0) return 1.0 - 1.0 / (2.0 * x) - 1.0 / (8.0 * x * x) - 1.0 / (8.0 * x * x * x);
+    return cyl_bessel_i1(x) / cyl_bessel_i0(x);
+}
+
+template <typename R, int LC, bool CG = false>
+__device__ __forceinline__ void multihit_site(const Geo& g, const cs_t<R>* __restrict__ cs, double beta,
+                                              Cx<R>* __restrict__ ubar, int i)
+{
+    const Extent<LC> e(g);
+    const int L = e.L, Nt = e.Nt;
+    const int x = i % L;
+    const int rest = i / L;
+    const int y = rest % L;
+    const int z = (rest / L) % L;
+    const int t = rest / (L * L);
+    const int c[4] = {t, x, y, z};
+    const int p = (x + y + z + t) & 1;
+    const int up_mu = step_up<0>(t, L, Nt);
+    Cx<R> A{R(0), R(0)};
+    staple_term<R, 0, 1, CG>(A, cs, g.Vh, p, i, c, L, Nt, up_mu);
+    staple_term<R, 0, 2, CG>(A, cs, g.Vh, p, i, c, L, Nt, up_mu);
+    staple_term<R, 0, 3, CG>(A, cs, g.Vh, p, i, c, L, Nt, up_mu);
+    const double are = static_cast<double>(A.re), aim = static_cast<double>(A.im);
+    const double a = sqrt(are * are + aim * aim);
+    const double f = a > 0.0 ? bessel_ratio_i1_i0(beta * a) / a : 0.0;
+    ubar[i] = Cx<R>{static_cast<R>(f * are), static_cast<R>(-f * aim)};
+}
+
+template <typename R, int LC>
+__global__ void __launch_bounds__(kThreads) multihit_kernel(Geo g, const cs_t<R>* __restrict__ cs, double beta,
+                                                            Cx<R>* __restrict__ ubar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < g.V) multihit_site<R, LC>(g, cs, beta, ubar, i);
 }
 
 // Accumulator of a complex x real product sum over the samples of one chunk.
@@ -589,10 +652,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) persistent_kernel
             if (u.metro) u.pass += 1;
         }
         if (a.measure) {
+            Cx<R>* ubar = static_cast<Cx<R>*>(a.ubar);
+            if (ubar) {
+                for (int q = tid; q < g.V; q += stride) multihit_site<R, LC, true>(g, cs, u.beta, ubar, q);
+                if (!grid_barrier(a, epoch)) return;
+            }
             const int SL3 = (g.Nt / u.slab_t) * g.L3;
             for (int q = tid; q < SL3; q += stride)
                 measure_store_site<R, true>(g, cs, u.slab_t, a.r_max, a.fields, a.slot0 + unit, a.asum,
-                                            static_cast<Cx<R>*>(a.tk), static_cast<R*>(a.ok), a.osum, q);
+                                            static_cast<Cx<R>*>(a.tk), static_cast<R*>(a.ok), a.osum, q, ubar);
             if (!grid_barrier(a, epoch)) return;
         }
     }
@@ -759,12 +827,30 @@ cudaError_t launch_plaquette(const Geo& g, const void* cs, double* partials, dou
 
 template <typename R>
 cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r_max, bool fields, int slot,
-                                 double2* asum, void* tk, void* ok, double* osum, cudaStream_t st)
+                                 double2* asum, void* tk, void* ok, double* osum, const void* ubar, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
     measure_store_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
         g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, fields ? 1 : 0, slot, asum, static_cast<Cx<R>*>(tk),
-        static_cast<R*>(ok), osum);
+        static_cast<R*>(ok), osum, static_cast<const Cx<R>*>(ubar));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* ubar, cudaStream_t st)
+{
+    const cs_t<R>* c = static_cast<const cs_t<R>*>(cs);
+    Cx<R>* u = static_cast<Cx<R>*>(ubar);
+    const int nb = blocks_for(g.V);
+    switch (g.L) {
+    case 8: multihit_kernel<R, 8><<<nb, kThreads, 0, st>>>(g, c, beta, u); break;
+    case 12: multihit_kernel<R, 12><<<nb, kThreads, 0, st>>>(g, c, beta, u); break;
+    case 16: multihit_kernel<R, 16><<<nb, kThreads, 0, st>>>(g, c, beta, u); break;
+    case 20: multihit_kernel<R, 20><<<nb, kThreads, 0, st>>>(g, c, beta, u); break;
+    case 24: multihit_kernel<R, 24><<<nb, kThreads, 0, st>>>(g, c, beta, u); break;
+    case 32: multihit_kernel<R, 32><<<nb, kThreads, 0, st>>>(g, c, beta, u); break;
+    default: multihit_kernel<R, 0><<<nb, kThreads, 0, st>>>(g, c, beta, u); break;
+    }
     return cudaGetLastError();
 }
 
@@ -851,7 +937,8 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
     template cudaError_t launch_from_canonical<R>(const Geo&, const double*, R*, void*, cudaStream_t);              \
     template cudaError_t launch_plaquette<R>(const Geo&, const void*, double*, double*, cudaStream_t);               \
     template cudaError_t launch_measure_store<R>(const Geo&, const void*, int, int, bool, int, double2*, void*,     \
-                                                 void*, double*, cudaStream_t);                                     \
+                                                 void*, double*, const void*, cudaStream_t);                        \
+    template cudaError_t launch_multihit<R>(const Geo&, const void*, double, void*, cudaStream_t);                 \
     template cudaError_t launch_insertion_contract<R>(const Geo&, int, int, int, int, const void*, const void*,     \
                                                       double2*, cudaStream_t);
 

@@ -332,3 +332,41 @@ def test_persistent_barrier_timeout_is_reported_and_recoverable():
     g.set_state(9, 0)
     g.sweep(1, 3)
     assert np.array_equal(g.get_links(), want)
+
+
+@pytest.mark.parametrize("mode", ["graphs", "direct", "persistent"])
+def test_multihit_multilevel_matches_oracle(mode):
+    """Correlator at r >= 2 from multihit temporal links (Section 2.2), insertions from the
+    links themselves; every launch mode against the oracle."""
+    L, Nt = 6, 4
+    g = _lib.Lattice(L, Nt, 1.0, 23)
+    c = O.Lattice(L, Nt, 1.0, 23)
+    g.set_option("multihit", 1)
+    g.set_option("graphs", 1 if mode == "graphs" else 0)
+    g.set_option("persistent", 1 if mode == "persistent" else 0)
+    g.sweep(1, 3)
+    c.sweep(1, 3)
+    gr = g.multilevel_fields(2, 3, 3, 2)
+    cr = c.multilevel(2, 3, 3, d_max=2, multihit=True)
+    assert np.max(np.abs(gr["corr"] - cr["corr"])) < OBS_TOL
+    assert np.max(np.abs(gr["fields"] - cr["fields"])) < OBS_TOL
+    assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
+    plain = O.Lattice(L, Nt, 1.0, 23)
+    plain.sweep(1, 3)
+    pr = plain.multilevel(2, 3, 3)
+    assert abs(gr["corr"][0] - pr["corr"][0]) < OBS_TOL       # r = 1 keeps the links
+    assert np.max(np.abs(gr["corr"][1:] - pr["corr"][1:])) > 1e-9
+
+
+def test_multihit_fp32_close_to_fp64():
+    L, Nt = 8, 8
+    th = random_angles(L, Nt, 9)
+    res = {}
+    for prec in (_lib.UL_FP64, _lib.UL_FP32_ACC64):
+        g = _lib.Lattice(L, Nt, 1.0, 3, prec)
+        g.set_links(th)
+        g.set_option("multihit", 1)
+        g.set_option("sub_metro", 0)
+        g.set_option("sub_or", 0)
+        res[prec] = g.multilevel(2, 2, 4)
+    assert np.max(np.abs(res[_lib.UL_FP64] - res[_lib.UL_FP32_ACC64])) < 1e-6
