@@ -79,6 +79,8 @@ def _load():
     lib.ulo_field_correlator.argtypes = [i, i, dp, i, i, dp]
     lib.ulo_field_correlator_one.argtypes = [i, i, dp, i, i, i, dp, dp]
     lib.ulo_multilevel.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, dp, dp, dp, dp, i]
+    lib.ulo_multilevel2.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, i, dp, i]
+    lib.ulo_multilevel2.restype = i
     lib.ulo_bessel_ratio.argtypes = [d]
     lib.ulo_bessel_ratio.restype = d
     lib.ulo_multihit_link.argtypes = [i, i, d, dp, l, dp, dp]
@@ -189,6 +191,17 @@ class Lattice:
         _load().ulo_field_correlator_one(self.L, self.Nt, _dp(self.theta), int(r), int(d), int(ch),
                                          ctypes.byref(re), ctypes.byref(im))
         return complex(re.value, im.value)
+
+    def multilevel2(self, tau1: int, n1: int, tau2: int, n2: int, r_max: int, sub_metro: int = 1,
+                    sub_or: int = 3, multihit: bool = False) -> np.ndarray:
+        """Two-level multilevel correlator."""
+        corr = np.empty(2 * r_max, dtype=np.float64)
+        rc = _load().ulo_multilevel2(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+                                     ctypes.byref(self.metro_pass), int(tau1), int(n1), int(tau2), int(n2),
+                                     int(sub_metro), int(sub_or), int(r_max), _dp(corr), 1 if multihit else 0)
+        if rc != 0:
+            raise ValueError("invalid two-level arguments")
+        return _cplx(corr.reshape(-1, 2))
 
     def multihit_link(self, i: int) -> complex:
         re, im = ctypes.c_double(), ctypes.c_double()

@@ -731,3 +731,62 @@ int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, doub
     free(Bsum);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Two-level multilevel estimator of the correlator (Section 2.2: two       */
+/* nested levels of layers with frozen spatial links)                        */
+/* ------------------------------------------------------------------------ */
+
+int ulo_multilevel2(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
+                    uint64_t* metro_pass, int tau1, int n1, int tau2, int n2, int sub_metro, int sub_or,
+                    int r_max, double* corr, int multihit)
+{
+    if (tau1 < 1 || tau2 < 1 || Nt % tau1 != 0 || tau1 % tau2 != 0 || n1 < 1 || n2 < 1 || r_max < 1 ||
+        r_max > L / 2)
+        return -1;
+    lat_t g = mk(L, Nt);
+    long L3 = (long)L * L * L;
+    int S1 = Nt / tau1, S2 = Nt / tau2, m = tau1 / tau2;
+    cplx* A1 = (cplx*)calloc((size_t)S1 * L3 * r_max, sizeof(cplx));
+    cplx* A2 = (cplx*)calloc((size_t)S2 * L3 * r_max, sizeof(cplx));
+    for (int k1 = 0; k1 < n1; k1++) {
+        /* level 1: update with the spatial links on t = 0 mod tau1 frozen */
+        ulo_sweep(L, Nt, beta, seed, width, theta, metro_pass, sub_metro, sub_or, tau1);
+        memset(A2, 0, sizeof(cplx) * (size_t)S2 * L3 * r_max);
+        for (int k2 = 0; k2 < n2; k2++) {
+            /* level 2: also the spatial links on t = 0 mod tau2 frozen */
+            ulo_sweep(L, Nt, beta, seed, width, theta, metro_pass, sub_metro, sub_or, tau2);
+            for (int s = 0; s < S2; s++)
+                for (long x0 = 0; x0 < L3; x0++)
+                    for (int r = 1; r <= r_max; r++) {
+                        long a = ((long)s * L3 + x0) * r_max + (r - 1);
+                        A2[a] = cadd(A2[a], slab_transporter(&g, theta, tau2, s, x0, r, multihit, beta));
+                    }
+        }
+        /* one level-1 sample per level-1 slab: product of its level-2 slab means */
+        for (int s1 = 0; s1 < S1; s1++)
+            for (long x0 = 0; x0 < L3; x0++)
+                for (int r = 1; r <= r_max; r++) {
+                    cplx prod = cmk(1.0, 0.0);
+                    for (int j = 0; j < m; j++)
+                        prod = cmul(prod, cdivr(A2[((long)(s1 * m + j) * L3 + x0) * r_max + (r - 1)], (double)n2));
+                    long a = ((long)s1 * L3 + x0) * r_max + (r - 1);
+                    A1[a] = cadd(A1[a], prod);
+                }
+    }
+    for (int r = 1; r <= r_max; r++) {
+        cplx sum = cmk(0.0, 0.0);
+        for (long x0 = 0; x0 < L3; x0++) {
+            cplx prod = cmk(1.0, 0.0);
+            for (int s1 = 0; s1 < S1; s1++)
+                prod = cmul(prod, cdivr(A1[((long)s1 * L3 + x0) * r_max + (r - 1)], (double)n1));
+            sum = cadd(sum, prod);
+        }
+        sum = cdivr(sum, (double)L3);
+        corr[2 * (r - 1)] = sum.re;
+        corr[2 * (r - 1) + 1] = sum.im;
+    }
+    free(A1);
+    free(A2);
+    return 0;
+}

@@ -105,6 +105,20 @@ int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, doub
                    int r_max, int d_max, double* corr, double* fields, double* vac,
                    double* samples_T, int multihit);
 
+/*
+ * Two-level multilevel estimator of the correlator (Section 2.2, the bracketed products
+ * of the field estimator read as level-1 averages of products of level-2 averages):
+ *   n1 times: sub_metro + sub_or passes with spatial links on t = 0 mod tau1 frozen, then
+ *             n2 times: the same passes with t = 0 mod tau2 also frozen and a measurement
+ *             of T^(tau2) per level-2 slab; one level-1 sample per level-1 slab is the
+ *             product of the level-2 means of the tau1/tau2 slabs inside it;
+ *   corr[r] = (1/L^3) sum_x0 prod_{level-1 slabs} (mean of the level-1 samples).
+ * tau2 divides tau1, tau1 divides Nt.  multihit as in ulo_multilevel.
+ */
+int ulo_multilevel2(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
+                    uint64_t* metro_pass, int tau1, int n1, int tau2, int n2, int sub_metro, int sub_or,
+                    int r_max, double* corr, int multihit);
+
 /* I1(x)/I0(x), x >= 0 (power series; asymptotic series beyond x = 600). */
 double ulo_bessel_ratio(double x);
 

@@ -583,3 +583,53 @@ def test_multihit_reduces_the_spread_of_the_correlator():
         mh.append(lat.copy().multilevel(4, 1, 2, sub_metro=0, sub_or=0, multihit=True)["corr"][1].real)
         lat.sweep(1, 2)
     assert np.std(mh) < np.std(plain)
+
+
+# --------------------------------------------------------------------------
+# Two-level multilevel (Section 2.2)
+# --------------------------------------------------------------------------
+
+def test_two_level_reduces_to_one_level():
+    """tau1 = Nt with one level-1 sample: one level-1 update of the lattice with the t = 0
+    spatial links frozen, then exactly the one-level estimator with slabs of tau2."""
+    L, Nt = 4, 8
+    th = random_angles(L, Nt, 141)
+    a = O.Lattice(L, Nt, 1.0, 3, theta=th).multilevel2(Nt, 1, 2, 3, 2, sub_metro=1, sub_or=3)
+    b = O.Lattice(L, Nt, 1.0, 3, theta=th)
+    b.sweep(1, 3, slab_t=Nt)
+    ref = b.multilevel(2, 3, 2, sub_metro=1, sub_or=3)["corr"]
+    assert np.max(np.abs(a - ref)) < 1e-14
+
+
+def test_two_level_without_updates_is_the_direct_correlator():
+    L, Nt = 4, 8
+    lat = O.Lattice(L, Nt, 1.0, 1, theta=random_angles(L, Nt, 142))
+    c = lat.copy().multilevel2(4, 2, 2, 3, 2, sub_metro=0, sub_or=0)
+    assert np.max(np.abs(c - lat.polyakov_correlator(2))) < 1e-14
+    gt = lat.copy()
+    gt.gauge_transform(8)
+    assert np.max(np.abs(gt.multilevel2(4, 2, 2, 3, 2, sub_metro=0, sub_or=0) - c)) < 1e-13
+
+
+def test_two_level_product_structure_by_enumeration():
+    """One level-1 sample: the estimator is (1/L^3) sum_x0 prod over level-2 slabs of the
+    level-2 means, i.e. the average over all choices of one level-2 sample per slab."""
+    L, Nt, tau2, n2 = 2, 4, 1, 2
+    lat = O.Lattice(L, Nt, 1.0, 6, theta=random_angles(L, Nt, 143))
+    start = lat.copy()
+    c = lat.multilevel2(Nt, 1, tau2, n2, 1, sub_metro=0, sub_or=0)
+    # with no updates every level-2 sample is the same: compare with the direct correlator,
+    # then with updates record the level-2 samples by replay and enumerate
+    assert abs(c[0] - start.polyakov_correlator(1)[0]) < 1e-14
+    lat = start.copy()
+    c = lat.multilevel2(Nt, 1, tau2, n2, 1, sub_metro=1, sub_or=1)
+    rep = start.copy()
+    rep.sweep(1, 1, slab_t=Nt)
+    samples = rep.multilevel(tau2, n2, 1, sub_metro=1, sub_or=1, record_samples=True)["samples_T"]
+    S2, L3 = Nt // tau2, L ** 3
+    total = 0.0
+    import itertools as it
+    for combo in it.product(range(n2), repeat=S2):
+        for x0 in range(L3):
+            total += np.prod([samples[combo[s], s, x0, 0] for s in range(S2)])
+    assert abs(c[0] - total / (n2 ** S2 * L3)) < 1e-14
