@@ -109,6 +109,19 @@ int ul_multilevel(ul_lattice* h, int slab_t, int n_sub, int r_max, double* out);
 int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max,
                          double* out_corr, double* out_fields, double* out_vac);
 
+/*
+ * ul_multilevel2 — two-level multilevel correlator (Section 2.2: the paper's two-level
+ * scheme, its field estimator grouping pairs of thickness-2 slabs into level-1 factors).
+ * n1 times: "sub_metro" + "sub_or" passes with the spatial links on t = 0 mod tau1 frozen,
+ * then n2 sub-samples of the same passes with t = 0 mod tau2 also frozen, each followed by
+ * a measurement of T (thickness tau2) per level-2 slab; one level-1 sample per level-1 slab
+ * is the product of the n2-sample means of the tau1/tau2 level-2 slabs inside it.
+ * out (2*r_max doubles): (re, im) of (1/L^3) sum_x0 prod_{level-1 slabs} <level-1 sample>.
+ * tau2 divides tau1, tau1 divides Nt, n1, n2 >= 1, 1 <= r_max <= L/2 (and <= 128).
+ * Option "multihit" applies as for ul_multilevel.
+ */
+int ul_multilevel2(ul_lattice* h, int tau1, int n1, int tau2, int n2, int r_max, double* out);
+
 /* ul_plaquette — *out = <Re U_p> = (1/6V) sum_x sum_{mu<nu} Re U_mu nu(x) (Section 2),
  * accumulated in FP64 in a fixed order (bitwise reproducible). */
 int ul_plaquette(ul_lattice* h, double* out);

@@ -44,6 +44,7 @@ SIGNATURES = [
     ("ul_sweep", _I, [_P, _I, _I]),
     ("ul_multilevel", _I, [_P, _I, _I, _I, _DP]),
     ("ul_multilevel_fields", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
+    ("ul_multilevel2", _I, [_P, _I, _I, _I, _I, _I, _DP]),
     ("ul_plaquette", _I, [_P, _DP]),
     ("ul_free", _I, [_P]),
     ("ul_set_option", _I, [_P, ctypes.c_char_p, _D]),
@@ -137,6 +138,12 @@ class Lattice:
     def multilevel(self, slab_t: int, n_sub: int, r_max: int) -> np.ndarray:
         out = np.zeros(2 * r_max)
         _check(load().ul_multilevel(self._h, int(slab_t), int(n_sub), int(r_max), _dp(out)), self._h)
+        return out[0::2] + 1j * out[1::2]
+
+    def multilevel2(self, tau1: int, n1: int, tau2: int, n2: int, r_max: int) -> np.ndarray:
+        out = np.zeros(2 * r_max)
+        _check(load().ul_multilevel2(self._h, int(tau1), int(n1), int(tau2), int(n2), int(r_max), _dp(out)),
+               self._h)
         return out[0::2] + 1j * out[1::2]
 
     def multilevel_fields(self, slab_t: int, n_sub: int, r_max: int, d_max: int):

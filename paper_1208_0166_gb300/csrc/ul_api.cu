@@ -89,7 +89,7 @@ size_t real_size(const ul_lattice* h) { return h->precision == UL_FP64 ? sizeof(
 
 bool is_f64(const ul_lattice* h) { return h->precision == UL_FP64; }
 
-enum : long long { kGraphSweep = 1, kGraphChunk = 2 };
+enum : long long { kGraphSweep = 1, kGraphChunk = 2, kGraphLevel2 = 3 };
 
 void drop_graphs(ul_lattice* h, long long kind)
 {
@@ -126,6 +126,7 @@ int ensure_ml(ul_lattice* h, size_t bytes)
     if (bytes <= h->ml_bytes) return UL_OK;
     UL_CK(h, cudaStreamSynchronize(h->stream));
     drop_graphs(h, kGraphChunk); // they reference the old buffer
+    drop_graphs(h, kGraphLevel2);
     cudaFree(h->ml_buf);
     h->ml_buf = nullptr;
     h->ml_bytes = 0;
@@ -531,6 +532,110 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
 int ul_multilevel(ul_lattice* h, int slab_t, int n_sub, int r_max, double* out)
 {
     return ul_multilevel_fields(h, slab_t, n_sub, r_max, -1, out, nullptr, nullptr);
+}
+
+int ul_multilevel2(ul_lattice* h, int tau1, int n1, int tau2, int n2, int r_max, double* out)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_multilevel2: NULL handle");
+    const ul::Geo& g = h->g;
+    if (tau1 < 1 || tau2 < 1 || g.Nt % tau1 != 0 || tau1 % tau2 != 0)
+        return fail(h, UL_EINVAL, "ul_multilevel2: tau2 must divide tau1 and tau1 must divide Nt");
+    if (g.Nt / tau2 > ul::kMaxSlabs) return fail(h, UL_EINVAL, "ul_multilevel2: more than 256 level-2 slabs");
+    if (n1 < 1 || n2 < 1) return fail(h, UL_EINVAL, "ul_multilevel2: n1 and n2 must be >= 1");
+    if (r_max < 1 || r_max > g.L / 2 || r_max > 128)
+        return fail(h, UL_EINVAL, "ul_multilevel2: r_max must be in [1, min(L/2, 128)]");
+    if (!out) return fail(h, UL_EINVAL, "ul_multilevel2: output pointer is NULL");
+    const int S1 = g.Nt / tau1, S2 = g.Nt / tau2;
+    const size_t rs = real_size(h);
+    auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+    const size_t n_a1 = static_cast<size_t>(S1) * r_max * g.L3, n_a2 = static_cast<size_t>(S2) * r_max * g.L3;
+    const size_t n_p = ul::ml_partials_doubles(g, r_max, 0);
+    const size_t off_2 = al(n_a1 * sizeof(double2));
+    const size_t off_u = off_2 + al(n_a2 * sizeof(double2));
+    const size_t off_p = off_u + al(h->multihit ? static_cast<size_t>(g.V) * 2 * rs : 0);
+    const size_t off_out = off_p + al(n_p * sizeof(double));
+    int rc = ensure_ml(h, off_out + al((2ull * r_max + 8) * sizeof(double)));
+    if (rc) return rc;
+    char* base = static_cast<char*>(h->ml_buf);
+    double2* asum1 = reinterpret_cast<double2*>(base);
+    double2* asum2 = reinterpret_cast<double2*>(base + off_2);
+    void* ubar = h->multihit ? static_cast<void*>(base + off_u) : nullptr;
+    double* partials = reinterpret_cast<double*>(base + off_p);
+    double* dout = reinterpret_cast<double*>(base + off_out);
+    UL_CK(h, cudaMemsetAsync(asum1, 0, n_a1 * sizeof(double2), h->stream));
+    const int sm = h->sub_metro, so = h->sub_or;
+    const long long kb = bits_of(h->beta), kw = bits_of(h->width), ks = static_cast<long long>(h->seed);
+
+    // level-2 samples of one level-1 iteration: passes with tau2 frozen, measurement into asum2
+    auto level2_chunk = [&](int count) -> int {
+        if (h->use_persistent) {
+            ul::PersistArgs a = persist_args(h, count, sm, so, tau2);
+            a.measure = 1;
+            a.r_max = r_max;
+            a.asum = asum2;
+            a.ubar = ubar;
+            return launch_persistent(h, a);
+        }
+        const std::vector<long long> key = {kGraphLevel2, 2, tau2, sm, so, r_max, count, kb, kw, ks,
+                                            reinterpret_cast<long long>(asum2), reinterpret_cast<long long>(ubar)};
+        return run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* pb) -> long {
+            long n = 0;
+            for (int j = 0; j < count; ++j) {
+                const long q = enqueue_passes(h, st, sm, so, tau2, first + static_cast<uint64_t>(j) * sm, pb);
+                if (q < 0) return q;
+                n += q;
+                cudaError_t e;
+                if (ubar) {
+                    e = is_f64(h) ? ul::launch_multihit<double>(g, h->cs, h->beta, ubar, st)
+                                  : ul::launch_multihit<float>(g, h->cs, h->beta, ubar, st);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "multihit launch");
+                    ++n;
+                }
+                e = is_f64(h) ? ul::launch_measure_store<double>(g, h->cs, tau2, r_max, false, 0, asum2, nullptr, nullptr,
+                                                                 nullptr, ubar, st)
+                              : ul::launch_measure_store<float>(g, h->cs, tau2, r_max, false, 0, asum2, nullptr, nullptr,
+                                                                nullptr, ubar, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
+                ++n;
+            }
+            return n;
+        });
+    };
+
+    for (int k1 = 0; k1 < n1; ++k1) {
+        // level-1 update: passes with tau1 frozen
+        if (h->use_persistent) {
+            rc = launch_persistent(h, persist_args(h, 1, sm, so, tau1));
+        } else {
+            const std::vector<long long> key = {kGraphLevel2, 1, tau1, sm, so, kb, kw, ks};
+            rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* pb) {
+                return enqueue_passes(h, st, sm, so, tau1, first, pb);
+            });
+        }
+        if (rc) return rc;
+        account_passes(h, sm, tau1);
+        UL_CK(h, cudaMemsetAsync(asum2, 0, n_a2 * sizeof(double2), h->stream));
+        for (int k2 = 0; k2 < n2;) {
+            const int count = std::min(64, n2 - k2);
+            rc = level2_chunk(count);
+            if (rc) return rc;
+            account_passes(h, sm * count, tau2);
+            k2 += count;
+        }
+        cudaError_t e = ul::launch_fold_level2(g, tau1, tau2, r_max, n2, asum2, asum1, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "level-2 fold launch");
+        h->launches += 1;
+    }
+    cudaError_t e = ul::launch_ml_reduce(g, tau1, n1, r_max, 0, asum1, nullptr, nullptr, partials, dout, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
+    h->launches += 2;
+    double host[2 * 128];
+    UL_CK(h, cudaMemcpyAsync(host, dout, 2ull * r_max * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    rc = check_device_status(h);
+    if (rc) return rc;
+    std::memcpy(out, host, 2ull * r_max * sizeof(double));
+    return UL_OK;
 }
 
 int ul_plaquette(ul_lattice* h, double* out)

@@ -65,6 +65,11 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
                              const double2* bsum, const double* osum, double* partials, double* out_dev,
                              cudaStream_t st);
 
+// Two-level multilevel: add the level-1 samples (products of the level-2 means inside each
+// level-1 slab) of the level-2 accumulator asum2 to asum1.
+cudaError_t launch_fold_level2(const Geo& g, int tau1, int tau2, int r_max, int n2, const double2* asum2,
+                               double2* asum1, cudaStream_t st);
+
 // Persistent cooperative sweep kernel (256 threads per block; `threads` is ignored).
 template <typename R>
 cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st);

@@ -116,6 +116,30 @@ __global__ void __launch_bounds__(kT) ml_vacuum_kernel(int SL3, const double* __
 
 __global__ void set_u64_kernel(unsigned long long* p, unsigned long long v) { *p = v; }
 
+// Two-level multilevel: one level-1 sample per (level-1 slab s1, r, x0) is the product of
+// the level-2 means of the m level-2 slabs inside s1, added to the level-1 accumulator.
+//   asum1[(s1*R + r)*L3 + x0] += prod_{j<m} asum2[((s1*m + j)*R + r)*L3 + x0] / n2
+__global__ void __launch_bounds__(kT) fold_level2_kernel(int L3, int S1, int m, int r_max, int n2,
+                                                         const double2* __restrict__ asum2,
+                                                         double2* __restrict__ asum1)
+{
+    const long k = static_cast<long>(blockIdx.x) * kT + threadIdx.x;
+    const long total = static_cast<long>(S1) * r_max * L3;
+    if (k >= total) return;
+    const int x0 = static_cast<int>(k % L3);
+    const long sr = k / L3;
+    const int r = static_cast<int>(sr % r_max);
+    const int s1 = static_cast<int>(sr / r_max);
+    const double n = static_cast<double>(n2);
+    Cx<double> prod{1.0, 0.0};
+    for (int j = 0; j < m; ++j)
+        prod = cmul(prod, mean_of(asum2[(static_cast<long>(s1 * m + j) * r_max + r) * L3 + x0], n));
+    double2 a = asum1[k];
+    a.x += prod.re;
+    a.y += prod.im;
+    asum1[k] = a;
+}
+
 } // namespace
 
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st)
@@ -148,5 +172,14 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
 }
 
 int plaquette_partials(const Geo& g) { return (g.V + kT - 1) / kT; }
+
+cudaError_t launch_fold_level2(const Geo& g, int tau1, int tau2, int r_max, int n2, const double2* asum2,
+                               double2* asum1, cudaStream_t st)
+{
+    const int S1 = g.Nt / tau1, m = tau1 / tau2;
+    const long total = static_cast<long>(S1) * r_max * g.L3;
+    fold_level2_kernel<<<static_cast<int>((total + kT - 1) / kT), kT, 0, st>>>(g.L3, S1, m, r_max, n2, asum2, asum1);
+    return cudaGetLastError();
+}
 
 } // namespace ul

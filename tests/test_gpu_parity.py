@@ -370,3 +370,31 @@ def test_multihit_fp32_close_to_fp64():
         g.set_option("sub_or", 0)
         res[prec] = g.multilevel(2, 2, 4)
     assert np.max(np.abs(res[_lib.UL_FP64] - res[_lib.UL_FP32_ACC64])) < 1e-6
+
+
+@pytest.mark.parametrize("mode,multihit", [("graphs", 0), ("direct", 1), ("persistent", 0), ("graphs", 1)])
+def test_two_level_multilevel_matches_oracle(mode, multihit):
+    """Two-level scheme (level-1 slabs of 4, level-2 slabs of 2) against the oracle."""
+    L, Nt = 6, 8
+    g = _lib.Lattice(L, Nt, 1.0, 51)
+    c = O.Lattice(L, Nt, 1.0, 51)
+    g.set_option("graphs", 1 if mode == "graphs" else 0)
+    g.set_option("persistent", 1 if mode == "persistent" else 0)
+    g.set_option("multihit", multihit)
+    g.sweep(1, 3)
+    c.sweep(1, 3)
+    gr = g.multilevel2(4, 3, 2, 70, 3)     # 70 level-2 samples: two graph chunks
+    cr = c.multilevel2(4, 3, 2, 70, 3, multihit=bool(multihit))
+    assert np.max(np.abs(gr - cr)) < OBS_TOL
+    assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
+    assert g.get_state()[1] == c.metro_pass.value
+
+
+def test_two_level_full_size_sampled():
+    """24^4 with level-1 slabs of 4 and level-2 slabs of 2 (few samples) against the oracle."""
+    L = 24
+    g = _lib.Lattice(L, L, 1.0, 2)
+    c = O.Lattice(L, L, 1.0, 2)
+    gr = g.multilevel2(4, 1, 2, 2, 8)
+    cr = c.multilevel2(4, 1, 2, 2, 8)
+    assert np.max(np.abs(gr - cr)) < OBS_TOL
