@@ -165,13 +165,16 @@ long enqueue_passes(ul_lattice* h, cudaStream_t st, int n_metro, int n_or, int s
         const uint64_t pass = first_pass + (metro ? static_cast<uint64_t>(k) : 0);
         for (int mu = 0; mu < 4; ++mu)
             for (int par = 0; par < 2; ++par) {
+                int launched = 0;
                 cudaError_t e = is_f64(h)
                     ? ul::launch_update_class<double>(h->g, static_cast<double*>(h->theta), h->cs, mu, par, metro, pass,
-                                                      pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st)
+                                                      pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st,
+                                                      &launched)
                     : ul::launch_update_class<float>(h->g, static_cast<float*>(h->theta), h->cs, mu, par, metro, pass,
-                                                     pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st);
+                                                     pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st,
+                                                     &launched);
                 if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
-                ++n;
+                n += launched;
             }
     }
     return n;

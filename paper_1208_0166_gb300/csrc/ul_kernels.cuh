@@ -210,13 +210,30 @@ __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta,
     return false;
 }
 
+// Threads per block of the one-class-per-launch update kernel: small blocks spread the
+// ~1.1 links per thread slot of a 24^4 class evenly over the SMs.
+constexpr int kUpdateThreads = 128;
+
+// With compact_tau > 1 and mu != 0 the grid covers only the unfrozen time slices (those
+// with t % compact_tau != 0): thread q maps to the q-th link of those slices.
 template <typename R, int LC>
-__global__ void __launch_bounds__(kThreads)
-    update_class_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int mu, UpdateArgs a)
+__global__ void __launch_bounds__(kUpdateThreads, 10)
+    update_class_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int mu, UpdateArgs a, int compact_tau)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = h < g.Vh;
+    if (compact_tau > 1 && mu != 0) {
+        const int L = LC ? LC : g.L;
+        const int hs = (L * L * L) / 2; // links of one parity on one time slice
+        const int per = compact_tau - 1; // unfrozen slices per slab
+        const int q = h;
+        valid = q < (g.Nt / compact_tau) * per * hs;
+        const int slice = q / hs;
+        const int t = (slice / per) * compact_tau + 1 + slice % per;
+        h = t * hs + (q - slice * hs);
+    }
     bool acc = false;
-    if (h < g.Vh) {
+    if (valid) {
         switch (mu) {
         case 0: acc = update_link<R, LC, 0>(g, theta, cs, h, a); break;
         case 1: acc = update_link<R, LC, 1>(g, theta, cs, h, a); break;
@@ -771,7 +788,7 @@ cudaError_t launch_refresh_cs(const Geo& g, const R* theta, void* cs, cudaStream
 template <typename R>
 cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int parity, bool metro, uint64_t pass,
                                 const unsigned long long* pass_base, uint64_t seed, double beta, double width,
-                                int slab_t, unsigned long long* accepted, cudaStream_t st)
+                                int slab_t, unsigned long long* accepted, cudaStream_t st, int* launched)
 {
     UpdateArgs a;
     a.parity = parity;
@@ -789,15 +806,21 @@ cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int pa
     a.width_f = static_cast<float>(width);
     a.accepted = accepted;
     cs_t<R>* c = static_cast<cs_t<R>*>(cs);
-    const dim3 grid(blocks_for(g.Vh));
+    const int compact = (slab_t > 1 && mu != 0) ? slab_t : 0;
+    const long work = compact ? static_cast<long>(g.Nt / slab_t) * (slab_t - 1) * (g.L3 / 2) : g.Vh;
+    *launched = 0;
+    if (work == 0) return cudaSuccess; // slab_t == 1: every spatial link is frozen
+    *launched = 1;
+    const dim3 grid(static_cast<unsigned>((work + kUpdateThreads - 1) / kUpdateThreads));
+    const int T = kUpdateThreads;
     switch (g.L) {
-    case 8: update_class_kernel<R, 8><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
-    case 12: update_class_kernel<R, 12><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
-    case 16: update_class_kernel<R, 16><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
-    case 20: update_class_kernel<R, 20><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
-    case 24: update_class_kernel<R, 24><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
-    case 32: update_class_kernel<R, 32><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
-    default: update_class_kernel<R, 0><<<grid, kThreads, 0, st>>>(g, theta, c, mu, a); break;
+    case 8: update_class_kernel<R, 8><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
+    case 12: update_class_kernel<R, 12><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
+    case 16: update_class_kernel<R, 16><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
+    case 20: update_class_kernel<R, 20><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
+    case 24: update_class_kernel<R, 24><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
+    case 32: update_class_kernel<R, 32><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
+    default: update_class_kernel<R, 0><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
     }
     return cudaGetLastError();
 }
@@ -932,7 +955,7 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
     template cudaError_t launch_refresh_cs<R>(const Geo&, const R*, void*, cudaStream_t);                           \
     template cudaError_t launch_update_class<R>(const Geo&, R*, void*, int, int, bool, uint64_t,                    \
                                                 const unsigned long long*, uint64_t, double, double, int,          \
-                                                unsigned long long*, cudaStream_t);                                \
+                                                unsigned long long*, cudaStream_t, int*);                          \
     template cudaError_t launch_to_canonical<R>(const Geo&, const R*, double*, cudaStream_t);                       \
     template cudaError_t launch_from_canonical<R>(const Geo&, const double*, R*, void*, cudaStream_t);              \
     template cudaError_t launch_plaquette<R>(const Geo&, const void*, double*, double*, cudaStream_t);               \
