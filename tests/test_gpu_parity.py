@@ -398,3 +398,22 @@ def test_two_level_full_size_sampled():
     gr = g.multilevel2(4, 1, 2, 2, 8)
     cr = c.multilevel2(4, 1, 2, 2, 8)
     assert np.max(np.abs(gr - cr)) < OBS_TOL
+
+
+def test_fp32_observables_agree_with_fp64_over_seeds():
+    """16 independent chains per precision (8^4, beta = 1, 20 sweeps, one level of 4 slabs,
+    20 sub-samples): the mean correlators agree within 3 combined standard errors."""
+    L, Nt, seeds = 8, 8, range(1, 17)
+    res = {}
+    for prec in (_lib.UL_FP64, _lib.UL_FP32_ACC64):
+        cs = []
+        for s in seeds:
+            g = _lib.Lattice(L, Nt, 1.0, s, prec)
+            g.sweep(20, 60)
+            cs.append(g.multilevel(2, 20, 2).real)
+            g.close()
+        cs = np.array(cs)
+        res[prec] = (cs.mean(axis=0), cs.std(axis=0, ddof=1) / math.sqrt(len(cs)))
+    (m64, e64), (m32, e32) = res[_lib.UL_FP64], res[_lib.UL_FP32_ACC64]
+    print("C(r) FP64", m64, "+-", e64, " FP32", m32, "+-", e32)
+    assert np.all(np.abs(m64 - m32) < 3 * np.hypot(e64, e32) + 1e-12)
