@@ -48,12 +48,16 @@ INSERTION_SAMPLES_PER_STEP = SAMPLES_PER_STEP * (W.d_max + 1) * 8
 H2D_BYTES = 4 * V * 8                                       # canonical FP64 link angles
 D2H_BYTES = (2 * W.r_max + 2 * W.r_max * (W.d_max + 1) * 8 + 8) * 8 + 8  # results + plaquette
 
-# Algorithmic FP64 floating-point operations per link update of the update kernel
-# (FMA counted as 2): staple 12 complex products + sums; Metropolis adds the proposal,
-# one sincos, exp and the wrap; overrelaxation adds atan2, the wrap and one sincos.
+# Algorithmic floating-point operations per link update of the update kernel, counted on
+# the operation sequence (FMA = 2; add, multiply, division, rint, floor, ldexp = 1):
+#   staple: 12 complex products (6 each) + 12 adds = 84
+#   sincos 42, exp 33, atan2 30, wrap 5
+#   Metropolis: staple + uniforms 2 + proposal 4 + wrap + 2 local actions 8 + sincos
+#               + dS 1 + exp = 179
+#   overrelaxation: staple + atan2 + reflection 2 + wrap + sincos = 163
 FLOP_STAPLE = 12 * 6 + 12
-FLOP_METRO = FLOP_STAPLE + 58 + 40 + 30 + 14
-FLOP_OR = FLOP_STAPLE + 60 + 14 + 40
+FLOP_METRO = FLOP_STAPLE + 2 + 4 + 5 + 8 + 42 + 1 + 33
+FLOP_OR = FLOP_STAPLE + 30 + 2 + 5 + 42
 
 # Peaks.  HBM from MEASURED_PEAKS.json; ALU peaks derived from unit counts and the
 # maximum SM clock: FP64 4 flop/clk/SM (nominal 1.25 TFLOP/s), FP32 256 flop/clk/SM.
