@@ -157,7 +157,9 @@ double ulo_atan2(double y, double x)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Complex numbers as (re, im) pairs; every product is (ac - bd, ad + bc).   */
+/* Complex numbers as (re, im) pairs.  A product (a + ib)(c + id) is formed  */
+/* as re = fma(a, c, -(b d)), im = fma(a, d, b c): each component is one     */
+/* fused multiply-add of one exact product and one rounded product.          */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -171,7 +173,7 @@ static cplx cmk(double re, double im)
     z.im = im;
     return z;
 }
-static cplx cmul(cplx a, cplx b) { return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+static cplx cmul(cplx a, cplx b) { return cmk(fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)); }
 static cplx cconj(cplx a) { return cmk(a.re, -a.im); }
 static cplx cadd(cplx a, cplx b) { return cmk(a.re + b.re, a.im + b.im); }
 static cplx cscale(cplx a, double s) { return cmk(a.re * s, a.im * s); }

@@ -203,7 +203,7 @@ struct Prec<float> {
 };
 
 // ---------------------------------------------------------------------------
-// Complex helpers: (a.re b.re - a.im b.im, a.re b.im + a.im b.re)
+// Complex helpers (FP32 products may be contracted by the compiler; FP64 products below)
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Cx {
@@ -219,6 +219,14 @@ template <typename T>
 __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b)
 {
     return Cx<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// FP64 complex product: each component one fused multiply-add of an exact and a rounded
+// product, re = fma(a.re, b.re, -(a.im b.im)), im = fma(a.re, b.im, a.im b.re) (four FP64
+// instructions; the FP64 oracle forms its products the same way).
+template <>
+__device__ __forceinline__ Cx<double> cmul<double>(Cx<double> a, Cx<double> b)
+{
+    return Cx<double>{fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)};
 }
 // Complex product with every operation rounded separately (no fused multiply-add in any
 // compilation context): measurement products use it so that they do not depend on how a
