@@ -23,12 +23,14 @@ cudaError_t launch_refresh_cs(const Geo& g, const R* theta, void* cs, cudaStream
 // One sub-sweep of class (mu, parity).  slab_t > 0 freezes spatial links on slices
 // t % slab_t == 0.  metro selects Metropolis (else overrelaxation).  The Metropolis pass
 // number is pass + *pass_base (pass_base may be null).  *launched is 0 when the class has
-// no updatable link (a spatial class with slab_t == 1) and nothing was launched.
+// no updatable link (a spatial class with slab_t == 1) and nothing was launched.  pdl:
+// launch with programmatic stream serialization (the kernel may be scheduled while the
+// previous kernel of the stream runs; it reads no link before that kernel completed).
 template <typename R>
 cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int parity, bool metro,
                                 uint64_t pass, const unsigned long long* pass_base, uint64_t seed, double beta,
                                 double width, int slab_t, unsigned long long* accepted, cudaStream_t st,
-                                int* launched);
+                                int* launched, bool pdl);
 
 // *p = v (one thread); sets the pass base read by graph-replayed update kernels.
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);

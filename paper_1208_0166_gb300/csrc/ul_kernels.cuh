@@ -232,6 +232,12 @@ __global__ void __launch_bounds__(kUpdateThreads, 10)
         const int t = (slice / per) * compact_tau + 1 + slice % per;
         h = t * hs + (q - slice * hs);
     }
+    // Programmatic dependent launch: once every block of this grid has started, the next
+    // class kernel of the stream may be scheduled; no link is read before the previous
+    // kernel of the stream has completed and its writes are visible.  (Both instructions
+    // are no-ops for a kernel launched without the programmatic-serialization attribute.)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     bool acc = false;
     if (valid) {
         switch (mu) {
@@ -788,7 +794,7 @@ cudaError_t launch_refresh_cs(const Geo& g, const R* theta, void* cs, cudaStream
 template <typename R>
 cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int parity, bool metro, uint64_t pass,
                                 const unsigned long long* pass_base, uint64_t seed, double beta, double width,
-                                int slab_t, unsigned long long* accepted, cudaStream_t st, int* launched)
+                                int slab_t, unsigned long long* accepted, cudaStream_t st, int* launched, bool pdl)
 {
     UpdateArgs a;
     a.parity = parity;
@@ -811,18 +817,25 @@ cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int pa
     *launched = 0;
     if (work == 0) return cudaSuccess; // slab_t == 1: every spatial link is frozen
     *launched = 1;
-    const dim3 grid(static_cast<unsigned>((work + kUpdateThreads - 1) / kUpdateThreads));
-    const int T = kUpdateThreads;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(static_cast<unsigned>((work + kUpdateThreads - 1) / kUpdateThreads));
+    cfg.blockDim = dim3(kUpdateThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     switch (g.L) {
-    case 8: update_class_kernel<R, 8><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
-    case 12: update_class_kernel<R, 12><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
-    case 16: update_class_kernel<R, 16><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
-    case 20: update_class_kernel<R, 20><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
-    case 24: update_class_kernel<R, 24><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
-    case 32: update_class_kernel<R, 32><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
-    default: update_class_kernel<R, 0><<<grid, T, 0, st>>>(g, theta, c, mu, a, compact); break;
+    case 8: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 8>, g, theta, c, mu, a, compact);
+    case 12: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 12>, g, theta, c, mu, a, compact);
+    case 16: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 16>, g, theta, c, mu, a, compact);
+    case 20: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 20>, g, theta, c, mu, a, compact);
+    case 24: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 24>, g, theta, c, mu, a, compact);
+    case 32: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 32>, g, theta, c, mu, a, compact);
+    default: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 0>, g, theta, c, mu, a, compact);
     }
-    return cudaGetLastError();
 }
 
 template <typename R>
@@ -955,7 +968,7 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
     template cudaError_t launch_refresh_cs<R>(const Geo&, const R*, void*, cudaStream_t);                           \
     template cudaError_t launch_update_class<R>(const Geo&, R*, void*, int, int, bool, uint64_t,                    \
                                                 const unsigned long long*, uint64_t, double, double, int,          \
-                                                unsigned long long*, cudaStream_t, int*);                          \
+                                                unsigned long long*, cudaStream_t, int*, bool);                    \
     template cudaError_t launch_to_canonical<R>(const Geo&, const R*, double*, cudaStream_t);                       \
     template cudaError_t launch_from_canonical<R>(const Geo&, const double*, R*, void*, cudaStream_t);              \
     template cudaError_t launch_plaquette<R>(const Geo&, const void*, double*, double*, cudaStream_t);               \
