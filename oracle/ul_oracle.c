@@ -11,7 +11,7 @@
  *   Section 2 (Wilson action):     beta S = beta sum_x sum_{mu<nu} [1 - Re U_mu nu(x)],
  *                                  U_mu nu(x) = U_mu(x) U_nu(x+mu) U*_mu(x+nu) U*_nu(x)
  *   Section 2.1 (Configurations):  Metropolis + overrelaxation updates
- *   Section 2.2 (Multilevel):      layers with fixed spatial links, partial updates;
+ *   Section 2.2 (Multilevel):      time layers whose spatial boundary links are held fixed, updates of the rest;
  *                                  V(r) = -(1/Nt) ln <P*(0) P(r)>;
  *                                  insertion operator O(x0,x,t,r) = U*_0(x0,t) U_0(x0+r,t) O(x,t);
  *                                  TO^(2) = T(t) O(t+1) + O(t) T(t+1);
