@@ -126,7 +126,7 @@ Layout layout_of(const Job& j, size_t rs)
 }
 
 // Block sizes tried by the batched update kernel's autotuner, and the choice per precision.
-const int kTuneCandidates[3] = {128, 256, 512};
+const int kTuneCandidates[3] = {64, 96, 128};
 int g_tuned_threads[2] = {0, 0};
 
 } // namespace
@@ -141,7 +141,7 @@ struct ul_batch {
     std::vector<Job*> resident; // running or reducing
     std::map<uint64_t, Job*> jobs;
     uint64_t next_id = 1;
-    int threads = 256;
+    int threads = 128;
     // autotuning: timed passes per candidate, then the fastest block size
     struct Sample {
         int threads;
@@ -281,7 +281,7 @@ void collect_tuning(ul_batch* b)
     for (auto& s : b->tune)
         if (cudaEventQuery(s.b) != cudaSuccess) return;
     float best = 1e30f;
-    int pick = 256;
+    int pick = 128;
     for (int c : kTuneCandidates) {
         float sum = 0.f;
         int n = 0;
@@ -311,7 +311,10 @@ void collect_tuning(ul_batch* b)
 int one_pass(ul_batch* b, bool* did_work)
 {
     *did_work = false;
+    // Two tables per pass: temporal classes (every link) and spatial classes (for a masked
+    // job only the unfrozen slices); they differ only in the block offsets.
     ul::BatchUpdateTable t{};
+    ul::BatchUpdateTable ts{};
     ul::BatchMeasureTable m{};
     std::vector<Job*> in_pass;
     for (Job* j : b->resident)
@@ -326,7 +329,7 @@ int one_pass(ul_batch* b, bool* did_work)
         threads = kTuneCandidates[b->tune.size() % 3];
         timing = true;
     }
-    int blocks = 0;
+    int blocks = 0, blocks_s = 0;
     std::vector<bool> measure(in_pass.size(), false);
     for (size_t q = 0; q < in_pass.size(); ++q) {
         Job* j = in_pass[q];
@@ -354,6 +357,12 @@ int one_pass(ul_batch* b, bool* did_work)
         u.beta = j->spec.beta;
         u.width = j->spec.metro_width;
         blocks += (j->g.Vh + threads - 1) / threads;
+        ts.job[ts.njobs] = u;
+        ts.job[ts.njobs].block0 = blocks_s;
+        ts.njobs += 1;
+        const long spatial_work = slab_t > 1 ? static_cast<long>(j->g.Nt / slab_t) * (slab_t - 1) * (j->g.L3 / 2)
+                                             : (slab_t == 1 ? 0L : static_cast<long>(j->g.Vh));
+        blocks_s += static_cast<int>((spatial_work + threads - 1) / threads);
         b->link_updates += updatable(*j, slab_t);
         if (metro) {
             j->metro_pass += 1;
@@ -368,14 +377,18 @@ int one_pass(ul_batch* b, bool* did_work)
         UB_CK(b, cudaEventCreate(&smp.b));
         UB_CK(b, cudaEventRecord(smp.a, b->stream));
     }
+    const bool pdl = b->precision == UL_FP32_ACC64;
     for (int mu = 0; mu < 4; ++mu)
         for (int par = 0; par < 2; ++par) {
+            const ul::BatchUpdateTable& tab = mu == 0 ? t : ts;
+            const int nb = mu == 0 ? blocks : blocks_s;
+            if (nb == 0) continue; // every spatial link of every job is frozen (slab_t == 1)
             cudaError_t e = b->precision == UL_FP64
-                ? ul::launch_batched_update<double>(t, blocks, threads, mu, par, b->stream)
-                : ul::launch_batched_update<float>(t, blocks, threads, mu, par, b->stream);
+                ? ul::launch_batched_update<double>(tab, nb, threads, mu, par, b->stream, pdl)
+                : ul::launch_batched_update<float>(tab, nb, threads, mu, par, b->stream, pdl);
             if (e != cudaSuccess) return bcuda(b, e, "batched update launch");
+            b->launches += 1;
         }
-    b->launches += 8;
     if (timing) {
         UB_CK(b, cudaEventRecord(smp.b, b->stream));
         b->tune.push_back(smp);

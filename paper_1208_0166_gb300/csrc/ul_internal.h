@@ -79,10 +79,11 @@ template <typename R>
 cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st);
 
 // One batched class update over every lattice of the table (blocks: sum of the lattices'
-// block counts at `threads` threads per block).
+// block counts at `threads` <= 128 threads per block; a masked spatial class counts only the
+// unfrozen slices).  pdl: programmatic dependent launch.
 template <typename R>
 cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int threads, int mu, int parity,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool pdl);
 
 // One batched transporter measurement (correlators only) over the lattices of the table.
 template <typename R>

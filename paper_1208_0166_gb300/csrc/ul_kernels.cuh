@@ -738,16 +738,36 @@ __device__ __forceinline__ bool batch_update_link(const BatchUpdateJob& J, int p
     }
 }
 
+// Block b belongs to the last job whose block0 <= b.  For a masked spatial class (slab_t > 1,
+// mu != 0) a job's blocks cover only its unfrozen time slices (see update_class_kernel).
+// Minimum resident 128-thread blocks per SM.  The batched form reads its extents at run time
+// and needs more registers than the compile-time-extent class kernel: the FP64 form fits 6
+// blocks (80 registers) without spills, the FP32 form 12 (40 registers).
+template <typename R> struct BatchMinBlocks { static constexpr int value = 6; };
+template <> struct BatchMinBlocks<float> { static constexpr int value = 12; };
+
 template <typename R>
-__global__ void __launch_bounds__(512) batched_update_kernel(const __grid_constant__ BatchUpdateTable t, int mu,
-                                                             int parity)
+__global__ void __launch_bounds__(128, BatchMinBlocks<R>::value) batched_update_kernel(const __grid_constant__ BatchUpdateTable t, int mu,
+                                                                 int parity)
 {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int j = t.njobs - 1;
     while (j > 0 && static_cast<int>(blockIdx.x) < t.job[j].block0) --j;
     const BatchUpdateJob& J = t.job[j];
-    const int h = (static_cast<int>(blockIdx.x) - J.block0) * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+    int h = (static_cast<int>(blockIdx.x) - J.block0) * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+    bool valid = h < J.Vh;
+    if (J.slab_t > 1 && mu != 0) {
+        const int hs = J.L3 / 2;           // links of one parity on one time slice
+        const int per = J.slab_t - 1;      // unfrozen slices per slab
+        const int q = h;
+        valid = q < (J.Nt / J.slab_t) * per * hs;
+        const int slice = q / hs;
+        const int tt = (slice / per) * J.slab_t + 1 + slice % per;
+        h = tt * hs + (q - slice * hs);
+    }
     bool acc = false;
-    if (h < J.Vh) {
+    if (valid) {
         switch (mu) {
         case 0: acc = batch_update_link<R, 0>(J, parity, h); break;
         case 1: acc = batch_update_link<R, 1>(J, parity, h); break;
@@ -903,10 +923,19 @@ cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int n
 
 template <typename R>
 cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int threads, int mu, int parity,
-                                  cudaStream_t st)
+                                  cudaStream_t st, bool pdl)
 {
-    batched_update_kernel<R><<<blocks, threads, 0, st>>>(t, mu, parity);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batched_update_kernel<R>, t, mu, parity);
 }
 
 template <typename R>
@@ -962,7 +991,7 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
 
 #define UL_INSTANTIATE_KERNELS(R)                                                                                  \
     template cudaError_t launch_persistent<R>(const Geo&, R*, void*, const PersistArgs&, int, cudaStream_t);       \
-    template cudaError_t launch_batched_update<R>(const BatchUpdateTable&, int, int, int, int, cudaStream_t);      \
+    template cudaError_t launch_batched_update<R>(const BatchUpdateTable&, int, int, int, int, cudaStream_t, bool); \
     template cudaError_t launch_batched_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                   \
     template cudaError_t launch_hot_start<R>(const Geo&, R*, void*, uint64_t, cudaStream_t);                        \
     template cudaError_t launch_refresh_cs<R>(const Geo&, const R*, void*, cudaStream_t);                           \
