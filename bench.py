@@ -158,8 +158,22 @@ def _dist():
     return ws, rank, local
 
 
+def _options(args):
+    out = {}
+    for kv in args.option:
+        k, _, v = kv.partition("=")
+        out[k.strip()] = float(v)
+    return out
+
+
+def _apply_options(lat, args):
+    for k, v in _options(args).items():
+        lat.set_option(k, v)
+
+
 def _config(args):
-    return {"workload": W.name + f" beta={W.beta} 100 sweeps (1 Metropolis + 3 OR) per configuration",
+    extra = {"options": _options(args)} if args.option else {}
+    return {**extra, "workload": W.name + f" beta={W.beta} 100 sweeps (1 Metropolis + 3 OR) per configuration",
             "lattice": f"{W.L}^3x{W.Nt}", "beta": W.beta, "slab_t": SLAB_T, "slabs": S, "n_sub": W.n_sub,
             "sweeps_per_config": W.therm_sweeps, "r_max": W.r_max, "d_max": W.d_max,
             "insertions": "E_x,E_y,E_z,B_x (Im and Re) on the mid-plane", "precision": args.precision,
@@ -223,6 +237,7 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
     from paper_1208_0166_gb300.replicas import replica_seed
 
     lat = lib.Lattice(W.L, W.Nt, W.beta, replica_seed(1, rank), prec)
+    _apply_options(lat, args)
     lat.set_stream(stream.cuda_stream)
     with torch.cuda.stream(stream):
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -412,6 +427,7 @@ def profile_step(args):
 
     prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
     lat = lib.Lattice(W.L, W.Nt, W.beta, 1, prec)
+    _apply_options(lat, args)
     for _ in range(W.therm_sweeps):
         lat.sweep(W.sweep_metro, W.sweep_or)
     lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
@@ -521,6 +537,8 @@ def main():
                          "serve: Poisson stream through the continuous-batching loop")
     ap.add_argument("--serve-jobs", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
+                    help="library run option set on the lattice (ul_set_option), e.g. slab_resident=1")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one step of the workload and exit (command line for ncu captures)")
     args = ap.parse_args()

@@ -180,6 +180,17 @@ int ul_free(ul_lattice* h);
  *   "graphs"       1 (default): recurring launch sequences (a compound sweep, a chunk of
  *                  sub-samples) are captured once into CUDA graphs and replayed; 0: every
  *                  kernel is launched directly.  Results are identical either way.
+ *   "slab_resident"  1: ul_multilevel / ul_multilevel_fields run each chunk of sub-samples
+ *                  as one launch in which a thread-block cluster owns one time slab: its
+ *                  links are held in the shared memory of the cluster's CTAs (Section 2.2:
+ *                  with the slab boundaries frozen a slab's updates read only its own links)
+ *                  and classes are separated by cluster barriers.  Used where the slab fits
+ *                  and neither "multihit" nor "persistent" is set; elsewhere, and with 0,
+ *                  one launch per class.  Default 1 for UL_FP32_ACC64, 0 for UL_FP64.
+ *                  Results are identical either way.
+ *   "slab_cluster" CTAs per slab in the slab-resident form (a divisor of L, at most 16;
+ *                  0, the default: the most CTAs up to 8 that keep every slab resident).
+ *                  A size whose slab share does not fit falls back to one launch per class.
  *   "insertion_chunk_mb"  bound (MiB, default 4096) on the buffers that hold the per-sample
  *                  transporters and channel sums between insertion contractions; fewer
  *                  MiB means more, smaller contractions (results change only by rounding)

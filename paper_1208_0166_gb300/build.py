@@ -23,7 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 SOURCES = {
     "ul_kernels_f64.cu": ["-fmad=false"],
-    "ul_kernels_f32.cu": [],
+    "ul_kernels_f32.cu": ["-fmad=false"],
     "ul_reduce.cu": [],
     "ul_api.cu": [],
     "ul_noalloc.cu": [],

@@ -53,6 +53,9 @@ struct ul_lattice {
     // persistent cooperative sweeps with a bounded-wait grid barrier
     bool use_persistent = false;
     bool barrier_unreachable = false; // test switch: no barrier can complete
+    // slab-resident sub-samples (one thread-block cluster per slab, links in shared memory)
+    int slab_mode = 0;    // 0: off, 1: on where the slab fits
+    int slab_cluster = 0; // CTAs per slab (0: chosen by slab_plan)
     unsigned long long spin_limit = 1ull << 24;
     unsigned int* d_bar = nullptr;    // [0] arrivals, [1] generation
     int* d_status = nullptr;          // nonzero after a wait gave up
@@ -355,6 +358,9 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
     // programmatic dependent launch: measured faster for FP32 classes (4.94 -> 4.60 us at 24^4)
     // and slower for FP64 classes (51.8 -> 56.5 us), so on by default for FP32 only
     h->use_pdl = precision == UL_FP32_ACC64;
+    // slab-resident sub-samples: measured faster for FP32 at 24^4 (step 57.4 -> 49.8 ms); the
+    // FP64 form is bound by the FP64 pipe and a cluster form leaves a third of the SMs idle
+    h->slab_mode = precision == UL_FP32_ACC64 ? 1 : 0;
     if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "capture stream");
     if ((e = cudaMalloc(&h->plaq_partials, ul::plaquette_partials(h->g) * sizeof(double))) != cudaSuccess)
@@ -443,12 +449,52 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
         UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
     }
 
+    // Slab-resident form: one cluster launch per chunk of sub-samples, where the slab fits
+    // into the shared memory of a cluster (multihit values are formed by their own kernel,
+    // so that mode keeps the per-class launches).
+    int slab_cl = 0, slab_threads = 0;
+    if (h->slab_mode && !ubar && !h->use_persistent) {
+        cudaError_t e = is_f64(h) ? ul::slab_plan<double>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads)
+                                  : ul::slab_plan<float>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads);
+        if (e != cudaSuccess) return cuda_fail(h, e, "slab plan");
+    }
+
     // Sub-samples in chunks; each chunk (passes + measurement per sample, then the insertion
     // contraction of the chunk) is one launch sequence, replayed as a graph.
-    const int seq = fields ? chunk : std::min(n_sub, 64);
+    const int seq = fields ? chunk : (slab_cl ? n_sub : std::min(n_sub, 64));
     for (int k = 0; k < n_sub;) {
         const int count = std::min(seq, n_sub - k);
         const int sm = h->sub_metro, so = h->sub_or;
+        if (slab_cl) {
+            ul::SlabArgs a{};
+            a.u = persist_args(h, count, sm, so, slab_t).u;
+            a.n_units = count;
+            a.n_metro = sm;
+            a.n_or = so;
+            a.cluster = slab_cl;
+            a.nz = g.L / slab_cl;
+            a.r_max = r_max;
+            a.fields = fields ? 1 : 0;
+            a.slot0 = 0;
+            a.asum = asum;
+            a.tk = tk;
+            a.ok = ok;
+            a.osum = osum;
+            cudaError_t e = is_f64(h)
+                ? ul::launch_slab<double>(g, static_cast<double*>(h->theta), h->cs, a, slab_threads, h->stream)
+                : ul::launch_slab<float>(g, static_cast<float*>(h->theta), h->cs, a, slab_threads, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "slab-resident launch");
+            h->launches += 1;
+            if (fields) {
+                e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream)
+                              : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+                h->launches += 1;
+            }
+            account_passes(h, sm * count, slab_t);
+            k += count;
+            continue;
+        }
         const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
                                             bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
                                             reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
@@ -694,6 +740,13 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
     } else if (!std::strcmp(key, "graphs")) {
         if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "graphs must be 0 or 1");
         h->use_graphs = v != 0.0;
+    } else if (!std::strcmp(key, "slab_resident")) {
+        if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "slab_resident must be 0 or 1");
+        h->slab_mode = static_cast<int>(v);
+    } else if (!std::strcmp(key, "slab_cluster")) {
+        if (!(v >= 0.0) || v > 16.0 || v != static_cast<int>(v))
+            return fail(h, UL_EINVAL, "slab_cluster must be an integer in [0, 16]");
+        h->slab_cluster = static_cast<int>(v);
     } else if (!std::strcmp(key, "insertion_chunk_mb")) {
         if (!(v >= 1.0) || v > 1e6 || v != static_cast<int>(v))
             return fail(h, UL_EINVAL, "insertion_chunk_mb must be an integer in [1, 1e6]");

@@ -37,6 +37,19 @@ struct PersistArgs {
     unsigned long long spin_limit;
 };
 
+// Arguments of a slab-resident sub-sample launch (see slab_kernel).
+struct SlabArgs {
+    UpdateArgs u;             // u.pass: first Metropolis pass; u.slab_t: slab thickness
+    int n_units;              // sub-samples (each: passes, then one measurement)
+    int n_metro, n_or;        // passes per sub-sample
+    int cluster, nz;          // CTAs per slab (one cluster), z planes per CTA
+    int r_max, fields, slot0; // measurement as in PersistArgs
+    double2* asum;
+    void* tk;
+    void* ok;
+    double* osum;
+};
+
 constexpr int kMaxBatchJobs = 48;
 
 struct BatchUpdateJob {

@@ -78,6 +78,15 @@ cudaError_t launch_fold_level2(const Geo& g, int tau1, int tau2, int r_max, int 
 template <typename R>
 cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st);
 
+// Slab-resident sub-samples (one thread-block cluster per slab, links in shared memory).
+// slab_plan sets *cluster to the CTAs per slab (0: the slab does not fit, or the cluster
+// shape cannot launch) and *threads to the block size; force_cluster > 0 asks for that
+// cluster size only.
+template <typename R>
+cudaError_t slab_plan(const Geo& g, int tau, int force_cluster, int* cluster, int* threads);
+template <typename R>
+cudaError_t launch_slab(const Geo& g, R* theta, void* cs, const SlabArgs& a, int threads, cudaStream_t st);
+
 // One batched class update over every lattice of the table (blocks: sum of the lattices'
 // block counts at `threads` <= 128 threads per block; a masked spatial class counts only the
 // unfrozen slices).  pdl: programmatic dependent launch.

@@ -7,6 +7,7 @@
 // transporters T, insertion operator, multilevel field estimator).
 #pragma once
 #include <algorithm>
+#include <cooperative_groups.h>
 #include "ul_device.cuh"
 #include "ul_batch_types.h"
 #include "ul_internal.h"
@@ -134,6 +135,22 @@ __device__ __forceinline__ Cx<R> load_link(const cs_t<R>* __restrict__ cs, int V
     return Cx<R>{v.x, v.y};
 }
 
+// One plane's contribution to the staple sum, from its six links:
+//   A += U_nu(x+mu) U*_mu(x+nu) U*_nu(x) + U*_nu(x+mu-nu) U*_mu(x-nu) U_nu(x-nu),
+// the forward and the backward staple formed by staple_fwd and staple_bwd and added as
+// A + (fwd + bwd).  Every update kernel (one class per launch, persistent, batched,
+// slab-resident) uses these functions, so a link's new value does not depend on the kernel.
+template <typename R>
+__device__ __forceinline__ Cx<R> staple_fwd(Cx<R> nu_up_mu, Cx<R> mu_up_nu, Cx<R> nu_here)
+{
+    return cmul(cmul(nu_up_mu, cconj(mu_up_nu)), cconj(nu_here));
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> staple_bwd(Cx<R> nu_diag, Cx<R> mu_dn_nu, Cx<R> nu_dn_nu)
+{
+    return cmul(cmul(cconj(nu_diag), cconj(mu_dn_nu)), nu_dn_nu);
+}
+
 template <typename R, int MU, int NU, bool CG>
 __device__ __forceinline__ void staple_term(Cx<R>& A, const cs_t<R>* __restrict__ cs, int Vh, int p, int i,
                                             const int c[4], int L, int Nt, int up_mu)
@@ -141,19 +158,56 @@ __device__ __forceinline__ void staple_term(Cx<R>& A, const cs_t<R>* __restrict_
     const int q = p ^ 1;
     const int up_nu = step_up<NU>(c[NU], L, Nt);
     const int dn_nu = step_down<NU>(c[NU], L, Nt);
-    const Cx<R> fwd = cmul(cmul(load_link<R, CG>(cs, Vh, NU, q, i + up_mu), cconj(load_link<R, CG>(cs, Vh, MU, q, i + up_nu))),
-                           cconj(load_link<R, CG>(cs, Vh, NU, p, i)));
-    const Cx<R> bwd = cmul(cmul(cconj(load_link<R, CG>(cs, Vh, NU, p, i + up_mu + dn_nu)),
-                                cconj(load_link<R, CG>(cs, Vh, MU, q, i + dn_nu))),
-                           load_link<R, CG>(cs, Vh, NU, q, i + dn_nu));
+    const Cx<R> fwd = staple_fwd(load_link<R, CG>(cs, Vh, NU, q, i + up_mu), load_link<R, CG>(cs, Vh, MU, q, i + up_nu),
+                                 load_link<R, CG>(cs, Vh, NU, p, i));
+    const Cx<R> bwd = staple_bwd(load_link<R, CG>(cs, Vh, NU, p, i + up_mu + dn_nu),
+                                 load_link<R, CG>(cs, Vh, MU, q, i + dn_nu), load_link<R, CG>(cs, Vh, NU, q, i + dn_nu));
     A = cadd(A, cadd(fwd, bwd));
+}
+
+// Metropolis decision for a link with angle th, phase old() = (cos th, sin th) (read after
+// the proposal is formed, which keeps it out of registers during the generator) and staple
+// sum A; the two uniforms come from Philox(counter (link_id, pass, 0, 0), key (seed, 1)).
+// On acceptance returns true with the new angle and phase in nth, ncs.
+template <typename R, class OldPhase>
+__device__ __forceinline__ bool metropolis_new(R th, OldPhase old_phase, Cx<R> A, uint64_t link_id, uint64_t pass,
+                                               uint64_t seed, R width, R beta, R& nth, cs_t<R>& ncs)
+{
+    using P = Prec<R>;
+    const Philox4 w = philox4x64_10(link_id, pass, 0, 0, seed, kStreamMetropolis);
+    const R u1 = P::uniform(w.w[0]);
+    const R u2 = P::uniform(w.w[1]);
+    const R prop = P::wrap(th + width * (R(2) * u1 - R(1)));
+    const cs_t<R> old = old_phase();
+    const R s_old = -beta * (old.x * A.re - old.y * A.im);
+    R sn, cn;
+    P::sincos(prop, &sn, &cn);
+    const R s_new = -beta * (cn * A.re - sn * A.im);
+    const R dS = s_new - s_old;
+    if (u2 < P::exp(-dS)) {
+        nth = prop;
+        ncs = cs_t<R>{cn, sn};
+        return true;
+    }
+    return false;
+}
+
+// Overrelaxation: the reflection th' = wrap(-2 arg(A) - th) with its phase.
+template <typename R>
+__device__ __forceinline__ void overrelax_new(R th, Cx<R> A, R& nth, cs_t<R>& ncs)
+{
+    using P = Prec<R>;
+    const R alpha = P::atan2(A.im, A.re);
+    nth = P::wrap(R(-2) * alpha - th);
+    R sn, cn;
+    P::sincos(nth, &sn, &cn);
+    ncs = cs_t<R>{cn, sn};
 }
 
 template <typename R, int LC, int MU, bool CG = false>
 __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int h,
                                             const UpdateArgs& a)
 {
-    using P = Prec<R>;
     const Extent<LC> e(g);
     const int L = e.L, Nt = e.Nt, Lh = L / 2, Vh = g.Vh;
     const int p = a.parity;
@@ -179,34 +233,22 @@ __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta,
     if (MU != 3) staple_term<R, MU, (MU == 3 ? 0 : 3), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
     const int off = (MU * 2 + p) * Vh + h;
     const R th = ld_link<R, CG>(theta + off);
+    R nth;
+    cs_t<R> ncs;
     if (a.metro) {
         uint64_t pass = a.pass;
         if (a.pass_base) pass += *a.pass_base;
         const uint64_t link_id = static_cast<uint64_t>(MU) * g.V + static_cast<uint64_t>(i);
-        const Philox4 w = philox4x64_10(link_id, pass, 0, 0, a.seed, kStreamMetropolis);
-        const R u1 = P::uniform(w.w[0]);
-        const R u2 = P::uniform(w.w[1]);
-        const R width = width_of<R>(a), beta = beta_of<R>(a);
-        const R prop = P::wrap(th + width * (R(2) * u1 - R(1)));
-        const cs_t<R> old = ld_link<cs_t<R>, CG>(cs + off);
-        const R s_old = -beta * (old.x * A.re - old.y * A.im);
-        R sn, cn;
-        P::sincos(prop, &sn, &cn);
-        const R s_new = -beta * (cn * A.re - sn * A.im);
-        const R dS = s_new - s_old;
-        if (u2 < P::exp(-dS)) {
-            theta[off] = prop;
-            cs[off] = cs_t<R>{cn, sn};
-            return true;
-        }
-        return false;
+        if (!metropolis_new<R>(th, [&] { return ld_link<cs_t<R>, CG>(cs + off); }, A, link_id, pass, a.seed,
+                               width_of<R>(a), beta_of<R>(a), nth, ncs))
+            return false;
+        theta[off] = nth;
+        cs[off] = ncs;
+        return true;
     }
-    const R alpha = P::atan2(A.im, A.re);
-    const R nth = P::wrap(R(-2) * alpha - th);
-    R sn, cn;
-    P::sincos(nth, &sn, &cn);
+    overrelax_new<R>(th, A, nth, ncs);
     theta[off] = nth;
-    cs[off] = cs_t<R>{cn, sn};
+    cs[off] = ncs;
     return false;
 }
 
@@ -990,6 +1032,8 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
 }
 
 #define UL_INSTANTIATE_KERNELS(R)                                                                                  \
+    template cudaError_t slab_plan<R>(const Geo&, int, int, int*, int*);                                           \
+    template cudaError_t launch_slab<R>(const Geo&, R*, void*, const SlabArgs&, int, cudaStream_t);               \
     template cudaError_t launch_persistent<R>(const Geo&, R*, void*, const PersistArgs&, int, cudaStream_t);       \
     template cudaError_t launch_batched_update<R>(const BatchUpdateTable&, int, int, int, int, cudaStream_t, bool); \
     template cudaError_t launch_batched_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                   \
@@ -1008,3 +1052,5 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
                                                       double2*, cudaStream_t);
 
 } // namespace ul
+
+#include "ul_slab.cuh"

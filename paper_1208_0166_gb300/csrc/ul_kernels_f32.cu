@@ -1,5 +1,6 @@
-// FP32 instantiation of the lattice kernels (links and updates in FP32; measurement
-// products and accumulators in FP64).
+// FP32 instantiation of the lattice kernels (links, updates and per-sample products in FP32;
+// accumulators in FP64).  Compiled with -fmad=false like the FP64 unit: every fused
+// multiply-add is written out, so each kernel evaluates a link update the same way.
 #include "ul_kernels.cuh"
 
 namespace ul {

@@ -15,7 +15,9 @@
 // Every fused multiply-add is an explicit fma(); the FP64 translation unit is compiled
 // with -fmad=false so no other multiply-add is fused.  All results are within 1 ulp.
 //
-// FP32 path: CUDA's single-precision sincosf/expf/atan2f; FMA contraction allowed.
+// FP32 path: CUDA's single-precision sincosf/expf/atan2f.  The FP32 translation unit is
+// also compiled with -fmad=false and its complex products are fused explicitly, so a link's
+// new value does not depend on the kernel that computes it.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -227,6 +229,12 @@ template <>
 __device__ __forceinline__ Cx<double> cmul<double>(Cx<double> a, Cx<double> b)
 {
     return Cx<double>{fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)};
+}
+// FP32 complex product, fused the same way (two FFMA and two FMUL).
+template <>
+__device__ __forceinline__ Cx<float> cmul<float>(Cx<float> a, Cx<float> b)
+{
+    return Cx<float>{__fmaf_rn(a.re, b.re, -__fmul_rn(a.im, b.im)), __fmaf_rn(a.re, b.im, __fmul_rn(a.im, b.re))};
 }
 // Complex products with a fixed rounding sequence in every compilation context (FP32: every
 // operation rounded separately; FP64: one explicit fused multiply-add per component), used
