@@ -86,6 +86,9 @@ def _load():
     lib.ulo_multihit_link.argtypes = [i, i, d, dp, l, dp, dp]
     lib.ulo_multilevel.restype = i
     lib.ulo_gauge_transform.argtypes = [i, i, u64, dp]
+    lib.ulo_multilevel_sym.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, dp, dp, dp]
+    lib.ulo_multilevel_sym.restype = i
+    lib.ulo_symmetry_transform.argtypes = [i, i, dp, ip, ip, dp]
     _lib = lib
     return lib
 
@@ -235,6 +238,30 @@ class Lattice:
         if samples is not None:
             out["samples_T"] = _cplx(samples.reshape(n_sub, S, self.L ** 3, r_max, 2))
         return out
+
+
+    def multilevel_sym(self, slab_t: int, n_sub: int, r_max: int, d_max: int, sub_metro: int = 1,
+                       sub_or: int = 3):
+        """Symmetrised one-level estimator (mean over the 24 frames); dict(corr, fields, vac)."""
+        corr = np.empty(2 * r_max, dtype=np.float64)
+        fields = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64)
+        vac = np.empty(N_CHANNELS, dtype=np.float64)
+        rc = _load().ulo_multilevel_sym(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+                                        ctypes.byref(self.metro_pass), int(slab_t), int(n_sub), int(sub_metro),
+                                        int(sub_or), int(r_max), int(d_max), _dp(corr), _dp(fields), _dp(vac))
+        if rc != 0:
+            raise ValueError("invalid multilevel arguments")
+        return {"corr": _cplx(corr.reshape(-1, 2)),
+                "fields": _cplx(fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)), "vac": vac}
+
+    def transformed(self, axis_of, sign_of) -> "Lattice":
+        """Image under the spatial signed permutation e_i -> sign_of[i] e_{axis_of[i]}, i = 1..3
+        (sequences of length 3 for x, y, z)."""
+        ax = (ctypes.c_int * 4)(0, *[int(v) for v in axis_of])
+        sg = (ctypes.c_int * 4)(1, *[int(v) for v in sign_of])
+        out = np.empty_like(self.theta)
+        _load().ulo_symmetry_transform(self.L, self.Nt, _dp(self.theta), ax, sg, _dp(out))
+        return Lattice(self.L, self.Nt, self.beta, self.seed, self.width, out, self.metro_pass.value)
 
 
 def bessel_ratio(x: float) -> float:

@@ -735,6 +735,227 @@ int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Symmetrised insertions: the one-level estimator averaged over the 24      */
+/* lattice symmetries that keep the time axis and send the separation        */
+/* direction to a positive spatial axis                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Link in a signed direction: U_{+mu}(x) = U_mu(x); U_{-mu}(x) = U*_mu(x - mu), the link
+ * from x to x - mu traversed backwards. */
+static cplx signed_link(const lat_t* g, const double* theta, int mu, int sgn, long i)
+{
+    if (sgn > 0) return link(g, theta, mu, i);
+    int c[4];
+    coords(g, i, c);
+    return cconj(link(g, theta, mu, shifted(g, c, mu, -1, mu, 0)));
+}
+
+/* Oriented plaquette at site i spanned by the signed directions (s1 e_mu, s2 e_nu):
+ * U_{s1 mu}(x) U_{s2 nu}(x + s1 mu) U*_{s1 mu}(x + s2 nu) U*_{s2 nu}(x). */
+static cplx signed_plaquette(const lat_t* g, const double* theta, int mu, int s1, int nu, int s2, long i)
+{
+    int c[4];
+    coords(g, i, c);
+    long x_mu = shifted(g, c, mu, s1, mu, 0);
+    long x_nu = shifted(g, c, nu, s2, nu, 0);
+    return cmul(cmul(cmul(signed_link(g, theta, mu, s1, i), signed_link(g, theta, nu, s2, x_mu)),
+                     cconj(signed_link(g, theta, mu, s1, x_nu))),
+                cconj(signed_link(g, theta, nu, s2, i)));
+}
+
+/* Spatial site x0 moved by n steps along spatial axis a (1 = x, 2 = y, 3 = z). */
+static long spatial_step(const lat_t* g, long x0, int a, int n)
+{
+    int c[4];
+    coords(g, x0, c);
+    return shifted(g, c, a, n, a, 0);
+}
+
+/* A frame: separation axis +e_a, insertion offset direction sb e_b, third direction sc e_c
+ * ((a, b, c) a permutation of (1, 2, 3)).  Its four channel planes, in the order of the
+ * unsymmetrised channels (0,x) (0,y) (0,z) (y,z), are (0, +a), (0, sb b), (0, sc c),
+ * (sb b, sc c). */
+typedef struct {
+    int a, b, c, sb, sc;
+} frame_t;
+
+static int frames24(frame_t* f)
+{
+    int n = 0;
+    for (int a = 1; a <= 3; a++) {
+        int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
+        int pairs[2][2] = {{o1, o2}, {o2, o1}};
+        for (int p = 0; p < 2; p++)
+            for (int sb = 1; sb >= -1; sb -= 2)
+                for (int sc = 1; sc >= -1; sc -= 2) {
+                    f[n].a = a;
+                    f[n].b = pairs[p][0];
+                    f[n].c = pairs[p][1];
+                    f[n].sb = sb;
+                    f[n].sc = sc;
+                    n++;
+                }
+    }
+    return n;
+}
+
+/* Channel ch = 2 plane + part (part 0 Im, 1 Re) of frame f at site i. */
+static double frame_channel(const lat_t* g, const double* theta, const frame_t* f, int ch, long i)
+{
+    int plane = ch / 2, part = ch % 2;
+    cplx P;
+    switch (plane) {
+    case 0: P = signed_plaquette(g, theta, 0, 1, f->a, 1, i); break;
+    case 1: P = signed_plaquette(g, theta, 0, 1, f->b, f->sb, i); break;
+    case 2: P = signed_plaquette(g, theta, 0, 1, f->c, f->sc, i); break;
+    default: P = signed_plaquette(g, theta, f->b, f->sb, f->c, f->sc, i); break;
+    }
+    return part == 0 ? P.im : P.re;
+}
+
+int ulo_multilevel_sym(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
+                       uint64_t* metro_pass, int slab_t, int n_sub, int sub_metro, int sub_or,
+                       int r_max, int d_max, double* corr, double* fields, double* vac)
+{
+    if (slab_t < 1 || Nt % slab_t != 0 || n_sub < 1 || r_max < 1 || r_max > L / 2 || d_max < 0 || d_max >= L)
+        return -1;
+    lat_t g = mk(L, Nt);
+    long L3 = (long)L * L * L;
+    int S = Nt / slab_t, nd = d_max + 1;
+    frame_t fr[24];
+    int nf = frames24(fr);
+    long nA = (long)S * L3 * r_max;
+    /* Asum per separation axis, Bsum per frame, Osum per frame and channel */
+    cplx* Asum = (cplx*)calloc((size_t)(3 * nA), sizeof(cplx));
+    cplx* Bsum = (cplx*)calloc((size_t)(nf * nA * nd * 8), sizeof(cplx));
+    double* Osum = (double*)calloc((size_t)(nf * 8), sizeof(double));
+    if (!Asum || !Bsum || !Osum) {
+        free(Asum);
+        free(Bsum);
+        free(Osum);
+        return -2;
+    }
+
+    for (int k = 0; k < n_sub; k++) {
+        ulo_sweep(L, Nt, beta, seed, width, theta, metro_pass, sub_metro, sub_or, slab_t);
+        for (int s = 0; s < S; s++)
+            for (long x0 = 0; x0 < L3; x0++)
+                for (int r = 1; r <= r_max; r++)
+                    for (int a = 1; a <= 3; a++) {
+                        /* T^(tau) along +e_a: product over the slab of U*_0(x0,t) U_0(x0 + r e_a, t) */
+                        long x1 = spatial_step(&g, x0, a, r);
+                        cplx T = cmk(1.0, 0.0);
+                        for (int t = s * slab_t; t < (s + 1) * slab_t; t++)
+                            T = cmul(T, cmul(cconj(link(&g, theta, 0, spatial_to_site(&g, x0, t))),
+                                             link(&g, theta, 0, spatial_to_site(&g, x1, t))));
+                        long ia = (long)(a - 1) * nA + ((long)s * L3 + x0) * r_max + (r - 1);
+                        Asum[ia] = cadd(Asum[ia], T);
+                        for (int f = 0; f < nf; f++) {
+                            if (fr[f].a != a) continue;
+                            for (int d = 0; d < nd; d++) {
+                                long y = spatial_step(&g, spatial_step(&g, x0, a, r / 2), fr[f].b, fr[f].sb * d);
+                                for (int ch = 0; ch < 8; ch++) {
+                                    double O = 0.0;
+                                    for (int t = s * slab_t; t < (s + 1) * slab_t; t++)
+                                        O += frame_channel(&g, theta, &fr[f], ch, spatial_to_site(&g, y, t));
+                                    long ib = (((long)f * nA + ((long)s * L3 + x0) * r_max + (r - 1)) * nd + d) * 8 + ch;
+                                    Bsum[ib] = cadd(Bsum[ib], cscale(T, O));
+                                }
+                            }
+                        }
+                    }
+        for (int f = 0; f < nf; f++)
+            for (int ch = 0; ch < 8; ch++)
+                for (long i = 0; i < g.V; i++) Osum[f * 8 + ch] += frame_channel(&g, theta, &fr[f], ch, i);
+    }
+
+    /* Per frame: the one-level products and reductions of ulo_multilevel; then the mean over
+     * the frames. */
+    for (int r = 1; r <= r_max; r++) {
+        cplx sum = cmk(0.0, 0.0);
+        for (int f = 0; f < nf; f++) {
+            long base = (long)(fr[f].a - 1) * nA;
+            cplx sf = cmk(0.0, 0.0);
+            for (long x0 = 0; x0 < L3; x0++) {
+                cplx prod = cmk(1.0, 0.0);
+                for (int s = 0; s < S; s++)
+                    prod = cmul(prod, cdivr(Asum[base + ((long)s * L3 + x0) * r_max + (r - 1)], (double)n_sub));
+                sf = cadd(sf, prod);
+            }
+            sum = cadd(sum, cdivr(sf, (double)L3));
+        }
+        sum = cdivr(sum, (double)nf);
+        corr[2 * (r - 1)] = sum.re;
+        corr[2 * (r - 1) + 1] = sum.im;
+    }
+    for (int r = 1; r <= r_max; r++)
+        for (int d = 0; d < nd; d++)
+            for (int ch = 0; ch < 8; ch++) {
+                cplx sum = cmk(0.0, 0.0);
+                for (int f = 0; f < nf; f++) {
+                    long base = (long)(fr[f].a - 1) * nA;
+                    cplx sf = cmk(0.0, 0.0);
+                    for (long x0 = 0; x0 < L3; x0++)
+                        for (int s = 0; s < S; s++) {
+                            long ia = ((long)s * L3 + x0) * r_max + (r - 1);
+                            cplx term = cdivr(Bsum[(((long)f * nA + ia) * nd + d) * 8 + ch], (double)n_sub);
+                            for (int s2 = 0; s2 < S; s2++) {
+                                if (s2 == s) continue;
+                                term = cmul(term, cdivr(Asum[base + ((long)s2 * L3 + x0) * r_max + (r - 1)],
+                                                        (double)n_sub));
+                            }
+                            sf = cadd(sf, term);
+                        }
+                    sum = cadd(sum, cdivr(sf, (double)g.V));
+                }
+                sum = cdivr(sum, (double)nf);
+                long o = (((long)(r - 1) * nd + d) * 8 + ch) * 2;
+                fields[o] = sum.re;
+                fields[o + 1] = sum.im;
+            }
+    if (vac)
+        for (int ch = 0; ch < 8; ch++) {
+            double v = 0.0;
+            for (int f = 0; f < nf; f++) v += Osum[f * 8 + ch] / ((double)n_sub * (double)g.V);
+            vac[ch] = v / (double)nf;
+        }
+    free(Asum);
+    free(Bsum);
+    free(Osum);
+    return 0;
+}
+
+/* Image of a configuration under the lattice symmetry g that keeps t and maps the spatial
+ * unit vector e_i to sign_of[i] e_{axis_of[i]} (i = 1, 2, 3; a signed permutation), sites
+ * x -> g x with coordinates taken mod L.  The image U' satisfies U'_{g v}(g x) = U_v(x) for
+ * every signed direction v, so a positive link of U' is a link of U or the conjugate of the
+ * link one step back. */
+void ulo_symmetry_transform(int L, int Nt, const double* theta, const int axis_of[4], const int sign_of[4],
+                            double* out)
+{
+    lat_t g = mk(L, Nt);
+    for (long ip = 0; ip < g.V; ip++) {
+        int cp[4];
+        coords(&g, ip, cp);
+        /* x = g^-1 x': x_i = sign_i x'_{axis_i} */
+        int c[4];
+        c[0] = cp[0];
+        for (int i = 1; i <= 3; i++) c[i] = sign_of[i] * cp[axis_of[i]];
+        long i0 = index_of(&g, c);
+        out[ip] = theta[i0]; /* time links */
+        for (int mp = 1; mp <= 3; mp++) {
+            int i = 1;
+            while (axis_of[i] != mp) i++;
+            /* g^-1 e_{mp} = sign_i e_i */
+            double th;
+            if (sign_of[i] > 0) th = theta[(long)i * g.V + i0];
+            else th = ulo_wrap(-theta[(long)i * g.V + shifted(&g, c, i, -1, i, 0)]);
+            out[(long)mp * g.V + ip] = th;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Two-level multilevel estimator of the correlator (Section 2.2: two       */
 /* nested levels of layers with frozen spatial links)                        */
 /* ------------------------------------------------------------------------ */

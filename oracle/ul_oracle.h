@@ -119,6 +119,23 @@ int ulo_multilevel2(int L, int Nt, double beta, uint64_t seed, double width, dou
                     uint64_t* metro_pass, int tau1, int n1, int tau2, int n2, int sub_metro, int sub_or,
                     int r_max, double* corr, int multihit);
 
+/*
+ * Symmetrised one-level estimator: ulo_multilevel's correlator, field insertions and
+ * vacuum terms (channels (0,x) (0,y) (0,z) (y,z), Im and Re) averaged over the 24 frames
+ * (separation axis +e_a, insertion offset direction sb e_b, third axis sc e_c): the lattice
+ * symmetries that keep the time axis and the orientation of the source pair.  Plaquettes
+ * in negative directions are oriented products of signed links U_{-mu}(x) = U*_mu(x - mu).
+ * Same arguments as ulo_multilevel (fields and vac required, d_max >= 0).  0 on success.
+ */
+int ulo_multilevel_sym(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
+                       uint64_t* metro_pass, int slab_t, int n_sub, int sub_metro, int sub_or,
+                       int r_max, int d_max, double* corr, double* fields, double* vac);
+
+/* Image of the configuration under the spatial signed permutation e_i -> sign_of[i] e_{axis_of[i]}
+ * (entries 1..3 used): out_{g v}(g x) = theta_v(x), angles of negative links negated. */
+void ulo_symmetry_transform(int L, int Nt, const double* theta, const int axis_of[4], const int sign_of[4],
+                            double* out);
+
 /* I1(x)/I0(x), x >= 0 (power series; asymptotic series beyond x = 600). */
 double ulo_bessel_ratio(double x);
 
