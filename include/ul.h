@@ -110,6 +110,24 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
                          double* out_corr, double* out_fields, double* out_vac);
 
 /*
+ * ul_multilevel_fields_sym — ul_multilevel_fields averaged over the 24 frames of the source
+ * pair: the estimator of Section 2.2, which the paper evaluates in one frame, evaluated in
+ * every frame to which a lattice symmetry keeping the time axis and the orientation of the
+ * pair maps that one: separation axis +e_a,
+ * a = x, y, z; insertion plaquette at x0 + floor(r/2) e_a + d sb e_b; channel planes
+ * (0, +a) "E parallel", (0, sb b) "E along the offset", (0, sc c) "E across", (sb b, sc c)
+ * "B parallel", Im and Re, where (a, b, c) is a permutation of the spatial axes and sb, sc
+ * = +-1.  A plaquette in negative directions is the oriented product of links traversed
+ * backwards, U_{-mu}(x) = U*_mu(x - mu).  The correlator is the mean of the three axes.
+ * Outputs and their layouts as in ul_multilevel_fields (out_fields required, out_vac may be
+ * NULL).  Runs one launch per class; options "slab_resident" and "persistent" do not apply;
+ * "multihit" must be 0 (UL_EINVAL otherwise).  Extra device memory: three transporter and
+ * insertion accumulators and 12 (instead of 8) channel sums per site.
+ */
+int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max,
+                             double* out_corr, double* out_fields, double* out_vac);
+
+/*
  * ul_multilevel2 — two-level multilevel correlator (Section 2.2: the paper's two-level
  * scheme, its field estimator grouping pairs of thickness-2 slabs into level-1 factors).
  * n1 times: "sub_metro" + "sub_or" passes with the spatial links on t = 0 mod tau1 frozen,

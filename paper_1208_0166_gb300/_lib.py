@@ -44,6 +44,7 @@ SIGNATURES = [
     ("ul_sweep", _I, [_P, _I, _I]),
     ("ul_multilevel", _I, [_P, _I, _I, _I, _DP]),
     ("ul_multilevel_fields", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
+    ("ul_multilevel_fields_sym", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
     ("ul_multilevel2", _I, [_P, _I, _I, _I, _I, _I, _DP]),
     ("ul_plaquette", _I, [_P, _DP]),
     ("ul_free", _I, [_P]),
@@ -152,6 +153,16 @@ class Lattice:
         vac = np.zeros(N_CHANNELS)
         _check(load().ul_multilevel_fields(self._h, int(slab_t), int(n_sub), int(r_max), int(d_max), _dp(corr),
                                            _dp(fields), _dp(vac)), self._h)
+        f = fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)
+        return {"corr": corr[0::2] + 1j * corr[1::2], "fields": f[..., 0] + 1j * f[..., 1], "vac": vac}
+
+    def multilevel_fields_sym(self, slab_t: int, n_sub: int, r_max: int, d_max: int):
+        """ul_multilevel_fields averaged over the 24 frames of the source pair."""
+        corr = np.zeros(2 * r_max)
+        fields = np.zeros(2 * r_max * (d_max + 1) * N_CHANNELS)
+        vac = np.zeros(N_CHANNELS)
+        _check(load().ul_multilevel_fields_sym(self._h, int(slab_t), int(n_sub), int(r_max), int(d_max),
+                                               _dp(corr), _dp(fields), _dp(vac)), self._h)
         f = fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)
         return {"corr": corr[0::2] + 1j * corr[1::2], "fields": f[..., 0] + 1j * f[..., 1], "vac": vac}
 

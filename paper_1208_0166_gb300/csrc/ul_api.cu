@@ -93,7 +93,7 @@ size_t real_size(const ul_lattice* h) { return h->precision == UL_FP64 ? sizeof(
 
 bool is_f64(const ul_lattice* h) { return h->precision == UL_FP64; }
 
-enum : long long { kGraphSweep = 1, kGraphChunk = 2, kGraphLevel2 = 3 };
+enum : long long { kGraphSweep = 1, kGraphChunk = 2, kGraphLevel2 = 3, kGraphSym = 4 };
 
 void drop_graphs(ul_lattice* h, long long kind)
 {
@@ -131,6 +131,7 @@ int ensure_ml(ul_lattice* h, size_t bytes)
     UL_CK(h, cudaStreamSynchronize(h->stream));
     drop_graphs(h, kGraphChunk); // they reference the old buffer
     drop_graphs(h, kGraphLevel2);
+    drop_graphs(h, kGraphSym);
     cudaFree(h->ml_buf);
     h->ml_buf = nullptr;
     h->ml_bytes = 0;
@@ -579,6 +580,136 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
         if (out_vac) std::memcpy(out_vac, host + 2 * r_max + 2 * r_max * nd * 8, 8 * sizeof(double));
     }
     std::free(host);
+    return UL_OK;
+}
+
+int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max, double* out_corr,
+                             double* out_fields, double* out_vac)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_multilevel_fields_sym: NULL handle");
+    const ul::Geo& g = h->g;
+    if (slab_t < 1 || g.Nt % slab_t != 0) return fail(h, UL_EINVAL, "ul_multilevel_fields_sym: slab_t must divide Nt");
+    if (g.Nt / slab_t > ul::kMaxSlabs) return fail(h, UL_EINVAL, "ul_multilevel_fields_sym: more than 256 slabs");
+    if (n_sub < 1) return fail(h, UL_EINVAL, "ul_multilevel_fields_sym: n_sub must be >= 1");
+    if (r_max < 1 || r_max > g.L / 2) return fail(h, UL_EINVAL, "ul_multilevel_fields_sym: r_max must be in [1, L/2]");
+    if (d_max < 0 || d_max >= g.L) return fail(h, UL_EINVAL, "ul_multilevel_fields_sym: d_max must be in [0, L)");
+    if (!out_corr || !out_fields) return fail(h, UL_EINVAL, "ul_multilevel_fields_sym: output pointer is NULL");
+    if (h->multihit) return fail(h, UL_EINVAL, "ul_multilevel_fields_sym: not available with the multihit option");
+    const int nd = d_max + 1;
+    const int S = g.Nt / slab_t;
+
+    // Scratch: asum3 | bsum3 | osum12 | tk3 | ok12 | partials | out3 (three axes) | vac12
+    const size_t rs = real_size(h);
+    const size_t n_a = static_cast<size_t>(S) * r_max * g.L3;
+    const size_t n_b = n_a * nd * 8;
+    const size_t n_o = 12ull * S * g.L3;
+    const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
+    const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
+    const size_t per_sample = (3 * n_a * 2 + 12ull * S * g.L3) * rs;
+    const size_t cap = static_cast<size_t>(h->chunk_mb) << 20;
+    const int chunk = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(n_sub), cap / per_sample)));
+    auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+    const size_t off_b = al(3 * n_a * sizeof(double2));
+    const size_t off_o = off_b + al(3 * n_b * sizeof(double2));
+    const size_t off_t = off_o + al(n_o * sizeof(double));
+    const size_t off_k = off_t + al(3 * n_a * 2 * rs * chunk);
+    const size_t off_p = off_k + al(12ull * S * g.L3 * rs * chunk);
+    const size_t off_out = off_p + al(n_p * sizeof(double));
+    const size_t bytes = off_out + al((3 * n_out + 12) * sizeof(double));
+    int rc = ensure_ml(h, bytes);
+    if (rc) return rc;
+    char* base = static_cast<char*>(h->ml_buf);
+    double2* asum3 = reinterpret_cast<double2*>(base);
+    double2* bsum3 = reinterpret_cast<double2*>(base + off_b);
+    double* osum12 = reinterpret_cast<double*>(base + off_o);
+    void* tk3 = base + off_t;
+    void* ok12 = base + off_k;
+    double* partials = reinterpret_cast<double*>(base + off_p);
+    double* dout = reinterpret_cast<double*>(base + off_out);
+    UL_CK(h, cudaMemsetAsync(asum3, 0, 3 * n_a * sizeof(double2), h->stream));
+    UL_CK(h, cudaMemsetAsync(bsum3, 0, 3 * n_b * sizeof(double2), h->stream));
+    UL_CK(h, cudaMemsetAsync(osum12, 0, n_o * sizeof(double), h->stream));
+
+    for (int k = 0; k < n_sub;) {
+        const int count = std::min(chunk, n_sub - k);
+        const int sm = h->sub_metro, so = h->sub_or;
+        const std::vector<long long> key = {kGraphSym, slab_t, sm, so, r_max, nd, count,
+                                            bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
+                                            reinterpret_cast<long long>(asum3), reinterpret_cast<long long>(bsum3),
+                                            reinterpret_cast<long long>(osum12), reinterpret_cast<long long>(tk3),
+                                            reinterpret_cast<long long>(ok12)};
+        rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* pb) -> long {
+            long n = 0;
+            for (int j = 0; j < count; ++j) {
+                const long m = enqueue_passes(h, st, sm, so, slab_t, first + static_cast<uint64_t>(j) * sm, pb);
+                if (m < 0) return m;
+                n += m;
+                cudaError_t e = is_f64(h)
+                    ? ul::launch_measure_sym<double>(g, h->cs, slab_t, r_max, j, asum3, tk3, ok12, osum12, st)
+                    : ul::launch_measure_sym<float>(g, h->cs, slab_t, r_max, j, asum3, tk3, ok12, osum12, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "symmetrised measurement launch");
+                ++n;
+            }
+            cudaError_t e = is_f64(h)
+                ? ul::launch_insertion_contract_sym<double>(g, slab_t, r_max, nd, count, tk3, ok12, bsum3, st)
+                : ul::launch_insertion_contract_sym<float>(g, slab_t, r_max, nd, count, tk3, ok12, bsum3, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "symmetrised contraction launch");
+            return n + 1;
+        });
+        if (rc) return rc;
+        account_passes(h, sm * count, slab_t);
+        k += count;
+    }
+    for (int a = 0; a < 3; ++a) {
+        cudaError_t e = ul::launch_ml_reduce(g, slab_t, n_sub, r_max, nd, asum3 + a * n_a, bsum3 + a * n_b, nullptr,
+                                             partials, dout + a * n_out, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
+        h->launches += 2;
+    }
+    cudaError_t e = ul::launch_ml_vacuum(static_cast<int>(S * g.L3), osum12, 12,
+                                         static_cast<double>(n_sub) * static_cast<double>(g.V), dout + 3 * n_out,
+                                         h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "vacuum launch");
+    h->launches += 1;
+    std::vector<double> host(3 * n_out + 12);
+    UL_CK(h, cudaMemcpyAsync(host.data(), dout, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    rc = check_device_status(h);
+    if (rc) return rc;
+    // correlator: mean over the three axes; fields: the sum over the 24 frames (each axis
+    // accumulated its 8 frames) divided by 24
+    for (int i = 0; i < 2 * r_max; ++i) out_corr[i] = (host[i] + host[n_out + i] + host[2 * n_out + i]) / 3.0;
+    const size_t nf = 2ull * r_max * nd * 8;
+    for (size_t i = 0; i < nf; ++i)
+        out_fields[i] = (host[2 * r_max + i] + host[n_out + 2 * r_max + i] + host[2 * n_out + 2 * r_max + i]) / 24.0;
+    if (out_vac) {
+        // vacuum term of each frame channel from the per-plane means (a shifted corner does not
+        // change a mean over all sites): channel planes (0,a), (0,b), (0,c), (b,c) with the Im
+        // part signed by the frame
+        const double* v = host.data() + 3 * n_out; // [plane p][Im, Re], p = (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
+        auto plane = [](int mu, int nu) { return mu == 0 ? nu - 1 : (mu == 1 ? (nu == 2 ? 3 : 4) : 5); };
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int a = 1; a <= 3; ++a) {
+            const int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
+            for (int pr = 0; pr < 2; ++pr) {
+                const int b = pr == 0 ? o1 : o2, c = pr == 0 ? o2 : o1;
+                for (int sb = 1; sb >= -1; sb -= 2)
+                    for (int sc = 1; sc >= -1; sc -= 2) {
+                        const int pbc = plane(std::min(b, c), std::max(b, c));
+                        const double ori = b < c ? 1.0 : -1.0;
+                        acc[0] += v[2 * (a - 1)];
+                        acc[1] += v[2 * (a - 1) + 1];
+                        acc[2] += sb * v[2 * (b - 1)];
+                        acc[3] += v[2 * (b - 1) + 1];
+                        acc[4] += sc * v[2 * (c - 1)];
+                        acc[5] += v[2 * (c - 1) + 1];
+                        acc[6] += sb * sc * ori * v[2 * pbc];
+                        acc[7] += v[2 * pbc + 1];
+                    }
+            }
+        }
+        for (int ch = 0; ch < 8; ++ch) out_vac[ch] = acc[ch] / 24.0;
+    }
     return UL_OK;
 }
 

@@ -52,6 +52,16 @@ template <typename R>
 cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r_max, bool fields, int slot,
                                  double2* asum, void* tk, void* ok, double* osum, const void* ubar, cudaStream_t st);
 
+// Symmetrised measurement after one sub-sample (transporters along the three axes into
+// asum3 / tk3, the six plaquette planes per site into ok12 / osum12) and the symmetrised
+// contraction of the first `count` stored samples into bsum3 (see ul_sym.cuh for layouts).
+template <typename R>
+cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_max, int slot, double2* asum3,
+                               void* tk3, void* ok12, double* osum12, cudaStream_t st);
+template <typename R>
+cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
+                                          const void* ok12, double2* bsum3, cudaStream_t st);
+
 // Multihit temporal links ubar[i] (lexicographic site i, complex in precision R).
 template <typename R>
 cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* ubar, cudaStream_t st);
@@ -65,6 +75,8 @@ cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int n
 // Cross-slab products, x0 reduction and normalisation.  out_dev receives
 // 2*r_max doubles (correlator) followed by 2*r_max*nd*8 doubles (fields) and 8 (vacuum).
 size_t ml_partials_doubles(const Geo& g, int r_max, int nd);
+// out[ch] = sum of osum[ch*SL3 .. ch*SL3 + SL3) / nV for ch < nch.
+cudaError_t launch_ml_vacuum(int SL3, const double* osum, int nch, double nV, double* out, cudaStream_t st);
 cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int nd, const double2* asum,
                              const double2* bsum, const double* osum, double* partials, double* out_dev,
                              cudaStream_t st);

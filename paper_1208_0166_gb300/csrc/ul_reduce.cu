@@ -173,6 +173,12 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
     return cudaGetLastError();
 }
 
+cudaError_t launch_ml_vacuum(int SL3, const double* osum, int nch, double nV, double* out, cudaStream_t st)
+{
+    ml_vacuum_kernel<<<nch, kT, 0, st>>>(SL3, osum, nV, out);
+    return cudaGetLastError();
+}
+
 int plaquette_partials(const Geo& g) { return (g.V + kT - 1) / kT; }
 
 cudaError_t launch_fold_level2(const Geo& g, int tau1, int tau2, int r_max, int n2, const double2* asum2,

@@ -1,0 +1,204 @@
+// ul_sym.cuh — symmetrised insertion measurement and contraction (Section 2.2), included
+// by ul_kernels.cuh.
+//
+// The one-level estimator is averaged over the 24 frames of the source pair: separation
+// axis +e_a (a = 1, 2, 3), insertion offset direction sb e_b and third direction sc e_c
+// ((a, b, c) a permutation of the spatial axes, sb, sc = +-1), i.e. over the lattice
+// symmetries that keep the time axis and the orientation of the pair.  The channels of a
+// frame are the planes (0, +a), (0, sb b), (0, sc c), (sb b, sc c) at y = x0 + floor(r/2) e_a
+// + d sb e_b.  A plaquette in negative directions is the conjugate of a stored plaquette at
+// a shifted corner:
+//   P_{mu,-nu}(x) = P*_{mu nu}(x - nu),  P_{-mu,nu}(x) = P*_{mu nu}(x - mu),
+//   P_{-mu,-nu}(x) = P_{mu nu}(x - mu - nu),  P_{nu mu}(x) = P*_{mu nu}(x),
+// so the measurement stores the six planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) once per site
+// and the contraction forms every frame's channels from them.
+#pragma once
+
+namespace ul {
+
+__device__ __constant__ static const int kSymPlaneMu[6] = {0, 0, 0, 1, 1, 2};
+__device__ __constant__ static const int kSymPlaneNu[6] = {1, 2, 3, 2, 3, 3};
+
+// Spatial lexicographic index of x0 moved by n (any sign) along spatial axis a.
+__device__ __forceinline__ int sym_shift(int L, int x0, int a, int n)
+{
+    int c[3] = {x0 % L, (x0 / L) % L, x0 / (L * L)};
+    int v = (c[a - 1] + n) % L;
+    c[a - 1] = v < 0 ? v + L : v;
+    return c[0] + L * (c[1] + L * c[2]);
+}
+
+// Measurement after one sub-sample, thread per (s, x0):
+//   T_a(s, x0, r) = W*(s, x0) W(s, x0 + r e_a)  (W the slab line),
+//   asum3[(a-1) nA + (s R + r-1) L3 + x0] += T,  tk3[(((slot*3 + a-1) S + s) R + r-1) L3 + x0] = T,
+//   O(s, x0, 2p + part) = sum_{t in slab} {Im, Re} P_p(x0, t)  (the six planes p),
+//   ok12[(slot SL3 + s L3 + x0) 12 + ch] = O,  osum12[ch SL3 + s L3 + x0] += O.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    measure_sym_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int slot,
+                       double2* __restrict__ asum3, Cx<R>* __restrict__ tk3, R* __restrict__ ok12,
+                       double* __restrict__ osum12)
+{
+    const int S = g.Nt / slab_t;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + x0
+    if (k >= S * g.L3) return;
+    const int s = k / g.L3;
+    const int x0 = k - s * g.L3;
+    const int t0 = s * slab_t;
+    const long nA = static_cast<long>(S) * r_max * g.L3;
+    const Cx<R> w0 = cconj(slab_line<R>(g, cs, x0, t0, slab_t));
+    for (int a = 1; a <= 3; ++a)
+        for (int r = 1; r <= r_max; ++r) {
+            const Cx<R> T = cmul_rn(w0, slab_line<R>(g, cs, sym_shift(g.L, x0, a, r), t0, slab_t));
+            const long ai = (a - 1) * nA + static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0;
+            double2 av = asum3[ai];
+            av.x += static_cast<double>(T.re);
+            av.y += static_cast<double>(T.im);
+            asum3[ai] = av;
+            tk3[((static_cast<long>(slot * 3 + a - 1) * S + s) * r_max + (r - 1)) * g.L3 + x0] = T;
+        }
+    R acc[12];
+#pragma unroll
+    for (int ch = 0; ch < 12; ++ch) acc[ch] = R(0);
+    for (int t = t0; t < t0 + slab_t; ++t) {
+        const Site x = site_from_lex(g, x0 + g.L3 * t);
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            const int mu = kSymPlaneMu[p], nu = kSymPlaneNu[p];
+            const Cx<R> P = cmul_rn(cmul_rn(cmul_rn(link_at<R>(cs, link_offset(g, mu, x)),
+                                                    link_at<R>(cs, link_offset(g, nu, site_step(g, x, mu, +1)))),
+                                            cconj(link_at<R>(cs, link_offset(g, mu, site_step(g, x, nu, +1))))),
+                                    cconj(link_at<R>(cs, link_offset(g, nu, x))));
+            acc[2 * p] += P.im;
+            acc[2 * p + 1] += P.re;
+        }
+    }
+    const long SL3 = static_cast<long>(S) * g.L3;
+    R* o = ok12 + (static_cast<long>(slot) * SL3 + k) * 12;
+#pragma unroll
+    for (int ch = 0; ch < 12; ++ch) {
+        o[ch] = acc[ch];
+        osum12[ch * SL3 + k] += static_cast<double>(acc[ch]);
+    }
+}
+
+// Index of the stored plane (mu, nu), mu < nu.
+__device__ __forceinline__ int sym_plane(int mu, int nu)
+{
+    return mu == 0 ? nu - 1 : (mu == 1 ? (nu == 2 ? 3 : 4) : 5);
+}
+
+// Symmetrised contraction over the `count` stored samples, thread per (a, s, r, d, x0), x0
+// fastest: with m = x0 + floor(r/2) e_a and the 8 frames (b, c, sb, sc) of axis a,
+//   bsum3[(a-1) nB + (((s R + r-1) nd + d) 8 + ch) L3 + x0]
+//       += sum_k T_a,k(s, x0, r) sum_frames channel_ch of the frame at m + d sb e_b,
+// the frames taken in the order (b, c) = (o1, o2), (o2, o1) (o1 < o2 the axes other than a),
+// sb = +, -, sc = +, - and the channel values summed in precision R.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    insertion_contract_sym_kernel(Geo g, int S, int r_max, int nd, int count, const Cx<R>* __restrict__ tk3,
+                                  const R* __restrict__ ok12, double2* __restrict__ bsum3)
+{
+    const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const long per_axis = static_cast<long>(S) * r_max * nd * g.L3;
+    if (idx >= 3 * per_axis) return;
+    const int a = static_cast<int>(idx / per_axis) + 1;
+    long rest = idx - (a - 1) * per_axis;
+    const int x0 = static_cast<int>(rest % g.L3);
+    rest /= g.L3;
+    const int d = static_cast<int>(rest % nd);
+    rest /= nd;
+    const int r = static_cast<int>(rest % r_max) + 1;
+    const int s = static_cast<int>(rest / r_max);
+    const int L = g.L;
+    const int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
+    const int m = sym_shift(L, x0, a, r / 2);
+    const long SL3 = static_cast<long>(S) * L * L * L;
+    const int pa = a - 1;
+
+    InsertionAcc<R> acc[8];
+    for (int k = 0; k < count; ++k) {
+        const Cx<R> T = tk3[((static_cast<long>(k * 3 + a - 1) * S + s) * r_max + (r - 1)) * g.L3 + x0];
+        const R* O = ok12 + (static_cast<long>(k) * SL3 + static_cast<long>(s) * g.L3) * 12;
+        R C[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) C[ch] = R(0);
+#pragma unroll
+        for (int pair = 0; pair < 2; ++pair) {
+            const int b = pair == 0 ? o1 : o2, c = pair == 0 ? o2 : o1;
+            const int pb = b - 1, pc = c - 1;
+            const int pbc = sym_plane(b < c ? b : c, b < c ? c : b);
+            const R ori = b < c ? R(1) : R(-1); // Im of P_{bc} = ori Im of the stored plane
+#pragma unroll
+            for (int sbi = 0; sbi < 2; ++sbi) {
+                const int y = sym_shift(L, m, b, sbi == 0 ? d : -d);
+                const int yb = sym_shift(L, y, b, -1), yc = sym_shift(L, y, c, -1), ybc = sym_shift(L, yb, c, -1);
+                const R* Oy = O + static_cast<long>(y) * 12;
+                const R* Ob = O + static_cast<long>(yb) * 12;
+                const R* Oc = O + static_cast<long>(yc) * 12;
+                const R* Obc = O + static_cast<long>(ybc) * 12;
+#pragma unroll
+                for (int sci = 0; sci < 2; ++sci) {
+                    // (0, +a)
+                    C[0] += Oy[2 * pa];
+                    C[1] += Oy[2 * pa + 1];
+                    // (0, sb b)
+                    if (sbi == 0) {
+                        C[2] += Oy[2 * pb];
+                        C[3] += Oy[2 * pb + 1];
+                    } else {
+                        C[2] -= Ob[2 * pb];
+                        C[3] += Ob[2 * pb + 1];
+                    }
+                    // (0, sc c)
+                    if (sci == 0) {
+                        C[4] += Oy[2 * pc];
+                        C[5] += Oy[2 * pc + 1];
+                    } else {
+                        C[4] -= Oc[2 * pc];
+                        C[5] += Oc[2 * pc + 1];
+                    }
+                    // (sb b, sc c)
+                    const R* Q = sbi == 0 ? (sci == 0 ? Oy : Oc) : (sci == 0 ? Ob : Obc);
+                    const R sgn = (sbi == sci) ? ori : -ori;
+                    C[6] += sgn * Q[2 * pbc];
+                    C[7] += Q[2 * pbc + 1];
+                }
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, C[ch]);
+    }
+    const long base = (a - 1) * (per_axis * 8) + (((static_cast<long>(s) * r_max + (r - 1)) * nd + d) * 8) * g.L3 + x0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+        double2 bv = bsum3[base + ch * g.L3];
+        bv.x += acc[ch].total_re();
+        bv.y += acc[ch].total_im();
+        bsum3[base + ch * g.L3] = bv;
+    }
+}
+
+template <typename R>
+cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_max, int slot, double2* asum3,
+                               void* tk3, void* ok12, double* osum12, cudaStream_t st)
+{
+    const int S = g.Nt / slab_t;
+    measure_sym_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
+        g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, slot, asum3, static_cast<Cx<R>*>(tk3),
+        static_cast<R*>(ok12), osum12);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
+                                          const void* ok12, double2* bsum3, cudaStream_t st)
+{
+    const int S = g.Nt / slab_t;
+    const long total = 3L * S * r_max * nd * g.L3;
+    insertion_contract_sym_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
+        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk3), static_cast<const R*>(ok12), bsum3);
+    return cudaGetLastError();
+}
+
+} // namespace ul

@@ -1,0 +1,101 @@
+"""Symmetrised insertions (ul_multilevel_fields_sym) against the oracle's symmetrised
+estimator: the same trajectory (FP64 links bit for bit) and observables within 1e-12."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1208_0166_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+OBS_TOL = 1e-12
+
+
+def angle_diff(a, b):
+    return np.abs(np.remainder(np.asarray(a) - np.asarray(b) + np.pi, 2 * np.pi) - np.pi)
+
+
+@pytest.mark.parametrize("L,Nt,tau,seed", [(4, 4, 2, 3), (4, 6, 1, 5), (6, 4, 2, 7), (4, 8, 4, 9)])
+def test_symmetrised_matches_oracle_fp64(L, Nt, tau, seed):
+    n_sub, r_max, d_max = 3, 2, 2
+    g = _lib.Lattice(L, Nt, 1.0, seed)
+    c = O.Lattice(L, Nt, 1.0, seed)
+    g.sweep(1, 3)
+    c.sweep(1, 3)
+    gr = g.multilevel_fields_sym(tau, n_sub, r_max, d_max)
+    cr = c.multilevel_sym(tau, n_sub, r_max, d_max)
+    assert angle_diff(g.get_links(), c.theta).max() == 0.0
+    for key in ("corr", "fields", "vac"):
+        assert np.max(np.abs(np.asarray(gr[key]) - np.asarray(cr[key]))) < OBS_TOL, key
+
+
+def test_symmetrised_frozen_configuration_fp32_close_to_fp64():
+    """No updates between measurements: FP32 links and products against FP64."""
+    out = []
+    for prec in (_lib.UL_FP64, _lib.UL_FP32_ACC64):
+        g = _lib.Lattice(8, 8, 1.0, 11, prec)
+        for _ in range(3):
+            g.sweep(1, 3)
+        th = g.get_links()
+        out.append(th)
+    g64 = _lib.Lattice(8, 8, 1.0, 11, _lib.UL_FP64)
+    g32 = _lib.Lattice(8, 8, 1.0, 11, _lib.UL_FP32_ACC64)
+    g64.set_links(out[0])
+    g32.set_links(out[0])
+    res = []
+    for g in (g64, g32):
+        g.set_option("sub_metro", 0)
+        g.set_option("sub_or", 0)
+        res.append(g.multilevel_fields_sym(2, 2, 3, 3))
+    for key in ("corr", "fields", "vac"):
+        assert np.max(np.abs(np.asarray(res[0][key]) - np.asarray(res[1][key]))) < 2e-6, key
+
+
+@pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
+def test_symmetrised_chunks_and_graphs(prec):
+    """Several contractions (small insertion buffers) and direct launches instead of graphs
+    give the same trajectory; observables agree to rounding."""
+    ref = None
+    for graphs, chunk in ((1, 4096), (0, 1), (1, 1)):
+        g = _lib.Lattice(8, 8, 1.0, 13, prec)
+        g.set_option("graphs", graphs)
+        g.set_option("insertion_chunk_mb", chunk)
+        g.sweep(1, 3)
+        r = g.multilevel_fields_sym(2, 5, 3, 2)
+        cur = (g.get_links(), r)
+        if ref is None:
+            ref = cur
+            continue
+        assert np.array_equal(cur[0], ref[0])
+        assert np.array_equal(cur[1]["corr"], ref[1]["corr"])
+        for key in ("fields", "vac"):
+            assert np.max(np.abs(np.asarray(cur[1][key]) - np.asarray(ref[1][key]))) < 1e-9, key
+
+
+def test_measuring_symmetrised_leaves_the_trajectory_unchanged():
+    """The measurement only reads links: the trajectory and the plaquette do not depend on
+    which estimator measured."""
+    a = _lib.Lattice(6, 6, 1.0, 17)
+    b = _lib.Lattice(6, 6, 1.0, 17)
+    a.sweep(1, 3)
+    b.sweep(1, 3)
+    a.multilevel_fields_sym(2, 3, 2, 1)
+    b.multilevel_fields(2, 3, 2, 1)
+    assert np.array_equal(a.get_links(), b.get_links())
+    assert a.plaquette() == b.plaquette()
+
+
+def test_symmetrised_rejects_multihit_and_bad_arguments():
+    g = _lib.Lattice(4, 4, 1.0, 1)
+    g.set_option("multihit", 1)
+    with pytest.raises(_lib.ULError):
+        g.multilevel_fields_sym(2, 1, 1, 1)
+    g.set_option("multihit", 0)
+    with pytest.raises(_lib.ULError):
+        g.multilevel_fields_sym(3, 1, 1, 1)
+    with pytest.raises(_lib.ULError):
+        g.multilevel_fields_sym(2, 1, 3, 1)
+    with pytest.raises(_lib.ULError):
+        g.multilevel_fields_sym(2, 1, 1, 4)
