@@ -158,6 +158,13 @@ def _dist():
     return ws, rank, local
 
 
+def _measure(lat, args):
+    """One multilevel level with insertions: the paper's frame, or all 24 frames."""
+    if args.estimator == "sym":
+        return lat.multilevel_fields_sym(SLAB_T, W.n_sub, W.r_max, W.d_max)
+    return lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+
+
 def _options(args):
     out = {}
     for kv in args.option:
@@ -173,6 +180,8 @@ def _apply_options(lat, args):
 
 def _config(args):
     extra = {"options": _options(args)} if args.option else {}
+    if args.estimator == "sym":
+        extra["estimator"] = "symmetrised over the 24 frames of the source pair (ul_multilevel_fields_sym)"
     return {**extra, "workload": W.name + f" beta={W.beta} 100 sweeps (1 Metropolis + 3 OR) per configuration",
             "lattice": f"{W.L}^3x{W.Nt}", "beta": W.beta, "slab_t": SLAB_T, "slabs": S, "n_sub": W.n_sub,
             "sweeps_per_config": W.therm_sweeps, "r_max": W.r_max, "d_max": W.d_max,
@@ -252,7 +261,7 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
         for _ in range(W.therm_sweeps):
             lat.sweep(W.sweep_metro, W.sweep_or)
         e1 = ev()
-        res = lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+        res = _measure(lat, args)
         e2 = ev()
         plaq = lat.plaquette()
         e3 = ev()
@@ -299,7 +308,7 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
             lat.set_links(host)
             for _ in range(W.therm_sweeps):
                 lat.sweep(W.sweep_metro, W.sweep_or)
-            r = lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+            r = _measure(lat, args)
             p = lat.plaquette()
             assert np.isfinite(r["corr"]).all() and np.isfinite(p)
         stream.synchronize()
@@ -430,7 +439,7 @@ def profile_step(args):
     _apply_options(lat, args)
     for _ in range(W.therm_sweeps):
         lat.sweep(W.sweep_metro, W.sweep_or)
-    lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
+    _measure(lat, args)
     lat.plaquette()
     lat.synchronize()
     lat.close()
@@ -537,6 +546,8 @@ def main():
                          "serve: Poisson stream through the continuous-batching loop")
     ap.add_argument("--serve-jobs", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--estimator", default="paper", choices=["paper", "sym"],
+                    help="paper: insertions in the paper's frame; sym: averaged over the 24 frames")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="library run option set on the lattice (ul_set_option), e.g. slab_resident=1")
     ap.add_argument("--profile-step", action="store_true",

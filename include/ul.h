@@ -122,7 +122,9 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
  * Outputs and their layouts as in ul_multilevel_fields (out_fields required, out_vac may be
  * NULL).  Runs one launch per class; options "slab_resident" and "persistent" do not apply;
  * "multihit" must be 0 (UL_EINVAL otherwise).  Extra device memory: three transporter and
- * insertion accumulators and 12 (instead of 8) channel sums per site.
+ * insertion accumulators, 12 (instead of 8) channel sums per site, and per stored sample the
+ * transporters of three axes and the frame sums of every insertion midpoint (3 (d_max+1) 8
+ * values per site and slab), bounded by the option "insertion_chunk_mb".
  */
 int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max,
                              double* out_corr, double* out_fields, double* out_vac);

@@ -598,22 +598,25 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
     const int nd = d_max + 1;
     const int S = g.Nt / slab_t;
 
-    // Scratch: asum3 | bsum3 | osum12 | tk3 | ok12 | partials | out3 (three axes) | vac12
+    // Scratch: asum3 | bsum3 | osum12 | tk3 (per sample) | csym (per sample) | o12 (one
+    // sample) | partials | out3 (three axes) | vac12
     const size_t rs = real_size(h);
     const size_t n_a = static_cast<size_t>(S) * r_max * g.L3;
     const size_t n_b = n_a * nd * 8;
     const size_t n_o = 12ull * S * g.L3;
+    const size_t n_c = 3ull * S * nd * 8 * g.L3; // frame sums of one sample
     const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
     const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
-    const size_t per_sample = (3 * n_a * 2 + 12ull * S * g.L3) * rs;
+    const size_t per_sample = (3 * n_a * 2 + n_c) * rs;
     const size_t cap = static_cast<size_t>(h->chunk_mb) << 20;
     const int chunk = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(n_sub), cap / per_sample)));
     auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
     const size_t off_b = al(3 * n_a * sizeof(double2));
     const size_t off_o = off_b + al(3 * n_b * sizeof(double2));
     const size_t off_t = off_o + al(n_o * sizeof(double));
-    const size_t off_k = off_t + al(3 * n_a * 2 * rs * chunk);
-    const size_t off_p = off_k + al(12ull * S * g.L3 * rs * chunk);
+    const size_t off_c = off_t + al(3 * n_a * 2 * rs * chunk);
+    const size_t off_k = off_c + al(n_c * rs * chunk);
+    const size_t off_p = off_k + al(n_o * rs);
     const size_t off_out = off_p + al(n_p * sizeof(double));
     const size_t bytes = off_out + al((3 * n_out + 12) * sizeof(double));
     int rc = ensure_ml(h, bytes);
@@ -623,7 +626,8 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
     double2* bsum3 = reinterpret_cast<double2*>(base + off_b);
     double* osum12 = reinterpret_cast<double*>(base + off_o);
     void* tk3 = base + off_t;
-    void* ok12 = base + off_k;
+    void* csym = base + off_c;
+    void* o12 = base + off_k;
     double* partials = reinterpret_cast<double*>(base + off_p);
     double* dout = reinterpret_cast<double*>(base + off_out);
     UL_CK(h, cudaMemsetAsync(asum3, 0, 3 * n_a * sizeof(double2), h->stream));
@@ -637,7 +641,7 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
                                             bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
                                             reinterpret_cast<long long>(asum3), reinterpret_cast<long long>(bsum3),
                                             reinterpret_cast<long long>(osum12), reinterpret_cast<long long>(tk3),
-                                            reinterpret_cast<long long>(ok12)};
+                                            reinterpret_cast<long long>(csym), reinterpret_cast<long long>(o12)};
         rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* pb) -> long {
             long n = 0;
             for (int j = 0; j < count; ++j) {
@@ -645,14 +649,14 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
                 if (m < 0) return m;
                 n += m;
                 cudaError_t e = is_f64(h)
-                    ? ul::launch_measure_sym<double>(g, h->cs, slab_t, r_max, j, asum3, tk3, ok12, osum12, st)
-                    : ul::launch_measure_sym<float>(g, h->cs, slab_t, r_max, j, asum3, tk3, ok12, osum12, st);
+                    ? ul::launch_measure_sym<double>(g, h->cs, slab_t, r_max, nd, j, asum3, tk3, o12, csym, osum12, st)
+                    : ul::launch_measure_sym<float>(g, h->cs, slab_t, r_max, nd, j, asum3, tk3, o12, csym, osum12, st);
                 if (e != cudaSuccess) return cuda_fail(h, e, "symmetrised measurement launch");
-                ++n;
+                n += 2;
             }
             cudaError_t e = is_f64(h)
-                ? ul::launch_insertion_contract_sym<double>(g, slab_t, r_max, nd, count, tk3, ok12, bsum3, st)
-                : ul::launch_insertion_contract_sym<float>(g, slab_t, r_max, nd, count, tk3, ok12, bsum3, st);
+                ? ul::launch_insertion_contract_sym<double>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, st)
+                : ul::launch_insertion_contract_sym<float>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "symmetrised contraction launch");
             return n + 1;
         });

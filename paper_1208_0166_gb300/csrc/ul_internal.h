@@ -53,14 +53,16 @@ cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r
                                  double2* asum, void* tk, void* ok, double* osum, const void* ubar, cudaStream_t st);
 
 // Symmetrised measurement after one sub-sample (transporters along the three axes into
-// asum3 / tk3, the six plaquette planes per site into ok12 / osum12) and the symmetrised
-// contraction of the first `count` stored samples into bsum3 (see ul_sym.cuh for layouts).
+// asum3 / tk3 slot `slot`, the six plaquette planes per site into the one-sample scratch o12
+// and osum12, the frame sums per insertion midpoint into csym slot `slot`) and the
+// symmetrised contraction of the first `count` stored samples into bsum3 (layouts in
+// ul_sym.cuh).
 template <typename R>
-cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_max, int slot, double2* asum3,
-                               void* tk3, void* ok12, double* osum12, cudaStream_t st);
+cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_max, int nd, int slot, double2* asum3,
+                               void* tk3, void* o12, void* csym, double* osum12, cudaStream_t st);
 template <typename R>
 cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
-                                          const void* ok12, double2* bsum3, cudaStream_t st);
+                                          const void* csym, double2* bsum3, cudaStream_t st);
 
 // Multihit temporal links ubar[i] (lexicographic site i, complex in precision R).
 template <typename R>

@@ -1032,8 +1032,8 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
 }
 
 #define UL_INSTANTIATE_KERNELS(R)                                                                                  \
-    template cudaError_t launch_measure_sym<R>(const Geo&, const void*, int, int, int, double2*, void*, void*,     \
-                                               double*, cudaStream_t);                                            \
+    template cudaError_t launch_measure_sym<R>(const Geo&, const void*, int, int, int, int, double2*, void*,       \
+                                               void*, void*, double*, cudaStream_t);                              \
     template cudaError_t launch_insertion_contract_sym<R>(const Geo&, int, int, int, int, const void*,             \
                                                           const void*, double2*, cudaStream_t);                   \
     template cudaError_t slab_plan<R>(const Geo&, int, int, int*, int*);                                           \

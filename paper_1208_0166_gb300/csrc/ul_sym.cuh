@@ -10,8 +10,9 @@
 // a shifted corner:
 //   P_{mu,-nu}(x) = P*_{mu nu}(x - nu),  P_{-mu,nu}(x) = P*_{mu nu}(x - mu),
 //   P_{-mu,-nu}(x) = P_{mu nu}(x - mu - nu),  P_{nu mu}(x) = P*_{mu nu}(x),
-// so the measurement stores the six planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) once per site
-// and the contraction forms every frame's channels from them.
+// so the measurement stores the six planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) once per site,
+// a second kernel sums every axis's 8 frames per insertion midpoint, and the contraction
+// multiplies those sums by the axis's transporters.
 #pragma once
 
 namespace ul {
@@ -32,11 +33,11 @@ __device__ __forceinline__ int sym_shift(int L, int x0, int a, int n)
 //   T_a(s, x0, r) = W*(s, x0) W(s, x0 + r e_a)  (W the slab line),
 //   asum3[(a-1) nA + (s R + r-1) L3 + x0] += T,  tk3[(((slot*3 + a-1) S + s) R + r-1) L3 + x0] = T,
 //   O(s, x0, 2p + part) = sum_{t in slab} {Im, Re} P_p(x0, t)  (the six planes p),
-//   ok12[(slot SL3 + s L3 + x0) 12 + ch] = O,  osum12[ch SL3 + s L3 + x0] += O.
+//   o12[ch SL3 + s L3 + x0] = O (this sample only),  osum12[ch SL3 + s L3 + x0] += O.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     measure_sym_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int slot,
-                       double2* __restrict__ asum3, Cx<R>* __restrict__ tk3, R* __restrict__ ok12,
+                       double2* __restrict__ asum3, Cx<R>* __restrict__ tk3, R* __restrict__ o12,
                        double* __restrict__ osum12)
 {
     const int S = g.Nt / slab_t;
@@ -74,10 +75,9 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
     const long SL3 = static_cast<long>(S) * g.L3;
-    R* o = ok12 + (static_cast<long>(slot) * SL3 + k) * 12;
 #pragma unroll
     for (int ch = 0; ch < 12; ++ch) {
-        o[ch] = acc[ch];
+        o12[ch * SL3 + k] = acc[ch];
         osum12[ch * SL3 + k] += static_cast<double>(acc[ch]);
     }
 }
@@ -88,16 +88,84 @@ __device__ __forceinline__ int sym_plane(int mu, int nu)
     return mu == 0 ? nu - 1 : (mu == 1 ? (nu == 2 ? 3 : 4) : 5);
 }
 
-// Symmetrised contraction over the `count` stored samples, thread per (a, s, r, d, x0), x0
-// fastest: with m = x0 + floor(r/2) e_a and the 8 frames (b, c, sb, sc) of axis a,
-//   bsum3[(a-1) nB + (((s R + r-1) nd + d) 8 + ch) L3 + x0]
-//       += sum_k T_a,k(s, x0, r) sum_frames channel_ch of the frame at m + d sb e_b,
+// Frame sums of one sub-sample, thread per (a, s, d, m), m fastest: the 8 frames (b, c, sb,
+// sc) of axis a put their channels at y = m + d sb e_b; their sum does not depend on how the
+// midpoint m = x0 + floor(r/2) e_a was reached, so it is formed once per (a, s, d, m):
+//   csym[((((slot*3 + a-1) S + s) nd + d) 8 + ch) L3 + m] = sum over the frames of channel ch,
 // the frames taken in the order (b, c) = (o1, o2), (o2, o1) (o1 < o2 the axes other than a),
-// sb = +, -, sc = +, - and the channel values summed in precision R.
+// sb = +, -, sc = +, -, summed in precision R.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    combine_sym_kernel(Geo g, int S, int nd, int slot, const R* __restrict__ o12, R* __restrict__ csym)
+{
+    const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const long per_axis = static_cast<long>(S) * nd * g.L3;
+    if (idx >= 3 * per_axis) return;
+    const int a = static_cast<int>(idx / per_axis) + 1;
+    long rest = idx - (a - 1) * per_axis;
+    const int m = static_cast<int>(rest % g.L3);
+    rest /= g.L3;
+    const int d = static_cast<int>(rest % nd);
+    const int s = static_cast<int>(rest / nd);
+    const int L = g.L;
+    const int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
+    const long SL3 = static_cast<long>(S) * g.L3;
+    const R* O = o12 + static_cast<long>(s) * g.L3; // channel ch of site y: O[ch SL3 + y]
+    const int pa = a - 1;
+    R C[8];
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) C[ch] = R(0);
+#pragma unroll
+    for (int pair = 0; pair < 2; ++pair) {
+        const int b = pair == 0 ? o1 : o2, c = pair == 0 ? o2 : o1;
+        const int pb = b - 1, pc = c - 1;
+        const int pbc = sym_plane(b < c ? b : c, b < c ? c : b);
+        const R ori = b < c ? R(1) : R(-1); // Im of P_{bc} = ori Im of the stored plane
+#pragma unroll
+        for (int sbi = 0; sbi < 2; ++sbi) {
+            const int y = sym_shift(L, m, b, sbi == 0 ? d : -d);
+            const int yb = sym_shift(L, y, b, -1), yc = sym_shift(L, y, c, -1), ybc = sym_shift(L, yb, c, -1);
+#pragma unroll
+            for (int sci = 0; sci < 2; ++sci) {
+                // (0, +a)
+                C[0] += O[(2 * pa) * SL3 + y];
+                C[1] += O[(2 * pa + 1) * SL3 + y];
+                // (0, sb b)
+                if (sbi == 0) {
+                    C[2] += O[(2 * pb) * SL3 + y];
+                    C[3] += O[(2 * pb + 1) * SL3 + y];
+                } else {
+                    C[2] -= O[(2 * pb) * SL3 + yb];
+                    C[3] += O[(2 * pb + 1) * SL3 + yb];
+                }
+                // (0, sc c)
+                if (sci == 0) {
+                    C[4] += O[(2 * pc) * SL3 + y];
+                    C[5] += O[(2 * pc + 1) * SL3 + y];
+                } else {
+                    C[4] -= O[(2 * pc) * SL3 + yc];
+                    C[5] += O[(2 * pc + 1) * SL3 + yc];
+                }
+                // (sb b, sc c)
+                const int q = sbi == 0 ? (sci == 0 ? y : yc) : (sci == 0 ? yb : ybc);
+                const R sgn = (sbi == sci) ? ori : -ori;
+                C[6] += sgn * O[(2 * pbc) * SL3 + q];
+                C[7] += O[(2 * pbc + 1) * SL3 + q];
+            }
+        }
+    }
+    R* out = csym + ((static_cast<long>(slot * 3 + a - 1) * S + s) * nd + d) * 8 * g.L3 + m;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) out[ch * g.L3] = C[ch];
+}
+
+// Symmetrised contraction over the `count` stored samples, thread per (a, s, r, d, x0), x0
+// fastest, m = x0 + floor(r/2) e_a:
+//   bsum3[(a-1) nB + (((s R + r-1) nd + d) 8 + ch) L3 + x0] += sum_k T_a,k(s, x0, r) csym_k(a, s, d, m, ch).
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     insertion_contract_sym_kernel(Geo g, int S, int r_max, int nd, int count, const Cx<R>* __restrict__ tk3,
-                                  const R* __restrict__ ok12, double2* __restrict__ bsum3)
+                                  const R* __restrict__ csym, double2* __restrict__ bsum3)
 {
     const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
     const long per_axis = static_cast<long>(S) * r_max * nd * g.L3;
@@ -110,64 +178,13 @@ __global__ void __launch_bounds__(kThreads)
     rest /= nd;
     const int r = static_cast<int>(rest % r_max) + 1;
     const int s = static_cast<int>(rest / r_max);
-    const int L = g.L;
-    const int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
-    const int m = sym_shift(L, x0, a, r / 2);
-    const long SL3 = static_cast<long>(S) * L * L * L;
-    const int pa = a - 1;
-
+    const int m = sym_shift(g.L, x0, a, r / 2);
     InsertionAcc<R> acc[8];
     for (int k = 0; k < count; ++k) {
         const Cx<R> T = tk3[((static_cast<long>(k * 3 + a - 1) * S + s) * r_max + (r - 1)) * g.L3 + x0];
-        const R* O = ok12 + (static_cast<long>(k) * SL3 + static_cast<long>(s) * g.L3) * 12;
-        R C[8];
+        const R* C = csym + ((static_cast<long>(k * 3 + a - 1) * S + s) * nd + d) * 8 * g.L3 + m;
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) C[ch] = R(0);
-#pragma unroll
-        for (int pair = 0; pair < 2; ++pair) {
-            const int b = pair == 0 ? o1 : o2, c = pair == 0 ? o2 : o1;
-            const int pb = b - 1, pc = c - 1;
-            const int pbc = sym_plane(b < c ? b : c, b < c ? c : b);
-            const R ori = b < c ? R(1) : R(-1); // Im of P_{bc} = ori Im of the stored plane
-#pragma unroll
-            for (int sbi = 0; sbi < 2; ++sbi) {
-                const int y = sym_shift(L, m, b, sbi == 0 ? d : -d);
-                const int yb = sym_shift(L, y, b, -1), yc = sym_shift(L, y, c, -1), ybc = sym_shift(L, yb, c, -1);
-                const R* Oy = O + static_cast<long>(y) * 12;
-                const R* Ob = O + static_cast<long>(yb) * 12;
-                const R* Oc = O + static_cast<long>(yc) * 12;
-                const R* Obc = O + static_cast<long>(ybc) * 12;
-#pragma unroll
-                for (int sci = 0; sci < 2; ++sci) {
-                    // (0, +a)
-                    C[0] += Oy[2 * pa];
-                    C[1] += Oy[2 * pa + 1];
-                    // (0, sb b)
-                    if (sbi == 0) {
-                        C[2] += Oy[2 * pb];
-                        C[3] += Oy[2 * pb + 1];
-                    } else {
-                        C[2] -= Ob[2 * pb];
-                        C[3] += Ob[2 * pb + 1];
-                    }
-                    // (0, sc c)
-                    if (sci == 0) {
-                        C[4] += Oy[2 * pc];
-                        C[5] += Oy[2 * pc + 1];
-                    } else {
-                        C[4] -= Oc[2 * pc];
-                        C[5] += Oc[2 * pc + 1];
-                    }
-                    // (sb b, sc c)
-                    const R* Q = sbi == 0 ? (sci == 0 ? Oy : Oc) : (sci == 0 ? Ob : Obc);
-                    const R sgn = (sbi == sci) ? ori : -ori;
-                    C[6] += sgn * Q[2 * pbc];
-                    C[7] += Q[2 * pbc + 1];
-                }
-            }
-        }
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, C[ch]);
+        for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, C[ch * g.L3]);
     }
     const long base = (a - 1) * (per_axis * 8) + (((static_cast<long>(s) * r_max + (r - 1)) * nd + d) * 8) * g.L3 + x0;
 #pragma unroll
@@ -180,24 +197,26 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename R>
-cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_max, int slot, double2* asum3,
-                               void* tk3, void* ok12, double* osum12, cudaStream_t st)
+cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_max, int nd, int slot, double2* asum3,
+                               void* tk3, void* o12, void* csym, double* osum12, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
     measure_sym_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
         g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, slot, asum3, static_cast<Cx<R>*>(tk3),
-        static_cast<R*>(ok12), osum12);
+        static_cast<R*>(o12), osum12);
+    combine_sym_kernel<R><<<blocks_for(3L * S * nd * g.L3), kThreads, 0, st>>>(
+        g, S, nd, slot, static_cast<const R*>(o12), static_cast<R*>(csym));
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
-                                          const void* ok12, double2* bsum3, cudaStream_t st)
+                                          const void* csym, double2* bsum3, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
     const long total = 3L * S * r_max * nd * g.L3;
     insertion_contract_sym_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
-        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk3), static_cast<const R*>(ok12), bsum3);
+        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk3), static_cast<const R*>(csym), bsum3);
     return cudaGetLastError();
 }
 
