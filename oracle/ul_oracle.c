@@ -279,10 +279,19 @@ double ulo_wrap(double theta)
     return theta - two_pi * floor((theta + PI_D) / two_pi);
 }
 
+/* A += p * q with both components accumulated by fused multiply-adds:
+ * Re: fma(p.re, q.re, fma(-p.im, q.im, A.re)),  Im: fma(p.re, q.im, fma(p.im, q.re, A.im)). */
+static cplx cmul_acc(cplx A, cplx p, cplx q)
+{
+    return cmk(fma(p.re, q.re, fma(-p.im, q.im, A.re)), fma(p.re, q.im, fma(p.im, q.re, A.im)));
+}
+
 /* A(x,mu) = sum_{nu != mu} [ U_nu(x+mu) U*_mu(x+nu) U*_nu(x)
  *                           + U*_nu(x+mu-nu) U*_mu(x-nu) U_nu(x-nu) ]
  * The first term completes the plaquette U_mu nu(x); the second is the conjugate of
- * the plaquette U_mu nu(x-nu) with U*_mu(x) removed, so that both enter as Re(U_mu(x) A). */
+ * the plaquette U_mu nu(x-nu) with U*_mu(x) removed, so that both enter as Re(U_mu(x) A).
+ * Terms in the order nu ascending, forward before backward; each term's last product is
+ * accumulated into A (cmul_acc). */
 static cplx staple(const lat_t* g, const double* theta, int mu, long i)
 {
     int c[4];
@@ -290,13 +299,12 @@ static cplx staple(const lat_t* g, const double* theta, int mu, long i)
     cplx A = cmk(0.0, 0.0);
     for (int nu = 0; nu < 4; nu++) {
         if (nu == mu) continue;
-        cplx fwd = cmul(cmul(link(g, theta, nu, shifted(g, c, mu, 1, nu, 0)),
-                             cconj(link(g, theta, mu, shifted(g, c, nu, 1, mu, 0)))),
-                        cconj(link(g, theta, nu, i)));
-        cplx bwd = cmul(cmul(cconj(link(g, theta, nu, shifted(g, c, mu, 1, nu, -1))),
-                             cconj(link(g, theta, mu, shifted(g, c, nu, -1, mu, 0)))),
-                        link(g, theta, nu, shifted(g, c, nu, -1, mu, 0)));
-        A = cadd(A, cadd(fwd, bwd));
+        cplx f = cmul(link(g, theta, nu, shifted(g, c, mu, 1, nu, 0)),
+                      cconj(link(g, theta, mu, shifted(g, c, nu, 1, mu, 0))));
+        A = cmul_acc(A, f, cconj(link(g, theta, nu, i)));
+        cplx b = cmul(cconj(link(g, theta, nu, shifted(g, c, mu, 1, nu, -1))),
+                      cconj(link(g, theta, mu, shifted(g, c, nu, -1, mu, 0))));
+        A = cmul_acc(A, b, link(g, theta, nu, shifted(g, c, nu, -1, mu, 0)));
     }
     return A;
 }
@@ -324,15 +332,18 @@ double ulo_local_action(int L, int Nt, double beta, const double* theta, int mu,
     return -beta * re_link_times(theta[(long)mu * g.V + i], A.re, A.im);
 }
 
-/* Metropolis: propose theta' = wrap(theta + width (2 u1 - 1)); with
- * dS = S_loc(theta') - S_loc(theta), S_loc = -beta Re(e^{i theta} A), accept iff u2 < exp(-dS). */
+/* Metropolis: propose theta' = wrap(theta + width (2 u1 - 1)) (2 u1 - 1 is exact; the step
+ * is added by one fused multiply-add); with S_loc = -beta Re(e^{i theta} A),
+ * dS = S_loc(theta') - S_loc(theta) = beta [(cos theta - cos theta') Re A - (sin theta - sin theta') Im A],
+ * formed as beta * fma(dc, Re A, -(ds Im A)); accept iff u2 < exp(-dS). */
 double ulo_metropolis_link(double theta, double a_re, double a_im, double beta,
                            double width, double u1, double u2, int* accepted)
 {
-    double proposal = ulo_wrap(theta + width * (2.0 * u1 - 1.0));
-    double s_old = -beta * re_link_times(theta, a_re, a_im);
-    double s_new = -beta * re_link_times(proposal, a_re, a_im);
-    double dS = s_new - s_old;
+    double proposal = ulo_wrap(fma(width, 2.0 * u1 - 1.0, theta));
+    double s0, c0, s1, c1;
+    ulo_sincos(theta, &s0, &c0);
+    ulo_sincos(proposal, &s1, &c1);
+    double dS = beta * fma(c0 - c1, a_re, -((s0 - s1) * a_im));
     if (u2 < ulo_exp(-dS)) {
         *accepted = 1;
         return proposal;

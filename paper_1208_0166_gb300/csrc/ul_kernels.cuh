@@ -136,19 +136,21 @@ __device__ __forceinline__ Cx<R> load_link(const cs_t<R>* __restrict__ cs, int V
 }
 
 // One plane's contribution to the staple sum, from its six links:
-//   A += U_nu(x+mu) U*_mu(x+nu) U*_nu(x) + U*_nu(x+mu-nu) U*_mu(x-nu) U_nu(x-nu),
-// the forward and the backward staple formed by staple_fwd and staple_bwd and added as
-// A + (fwd + bwd).  Every update kernel (one class per launch, persistent, batched,
-// slab-resident) uses these functions, so a link's new value does not depend on the kernel.
+//   A += U_nu(x+mu) U*_mu(x+nu) U*_nu(x)   (forward, staple_acc_fwd)
+//   A += U*_nu(x+mu-nu) U*_mu(x-nu) U_nu(x-nu)   (backward, staple_acc_bwd)
+// each term's last product accumulated into A by fused multiply-adds (cmul_acc), the
+// forward term before the backward one.  Every update kernel (one class per launch,
+// persistent, batched, slab-resident) uses these functions, so a link's new value does not
+// depend on the kernel.
 template <typename R>
-__device__ __forceinline__ Cx<R> staple_fwd(Cx<R> nu_up_mu, Cx<R> mu_up_nu, Cx<R> nu_here)
+__device__ __forceinline__ void staple_acc_fwd(Cx<R>& A, Cx<R> nu_up_mu, Cx<R> mu_up_nu, Cx<R> nu_here)
 {
-    return cmul(cmul(nu_up_mu, cconj(mu_up_nu)), cconj(nu_here));
+    cmul_acc(A, cmul(nu_up_mu, cconj(mu_up_nu)), cconj(nu_here));
 }
 template <typename R>
-__device__ __forceinline__ Cx<R> staple_bwd(Cx<R> nu_diag, Cx<R> mu_dn_nu, Cx<R> nu_dn_nu)
+__device__ __forceinline__ void staple_acc_bwd(Cx<R>& A, Cx<R> nu_diag, Cx<R> mu_dn_nu, Cx<R> nu_dn_nu)
 {
-    return cmul(cmul(cconj(nu_diag), cconj(mu_dn_nu)), nu_dn_nu);
+    cmul_acc(A, cmul(cconj(nu_diag), cconj(mu_dn_nu)), nu_dn_nu);
 }
 
 template <typename R, int MU, int NU, bool CG>
@@ -158,16 +160,17 @@ __device__ __forceinline__ void staple_term(Cx<R>& A, const cs_t<R>* __restrict_
     const int q = p ^ 1;
     const int up_nu = step_up<NU>(c[NU], L, Nt);
     const int dn_nu = step_down<NU>(c[NU], L, Nt);
-    const Cx<R> fwd = staple_fwd(load_link<R, CG>(cs, Vh, NU, q, i + up_mu), load_link<R, CG>(cs, Vh, MU, q, i + up_nu),
-                                 load_link<R, CG>(cs, Vh, NU, p, i));
-    const Cx<R> bwd = staple_bwd(load_link<R, CG>(cs, Vh, NU, p, i + up_mu + dn_nu),
-                                 load_link<R, CG>(cs, Vh, MU, q, i + dn_nu), load_link<R, CG>(cs, Vh, NU, q, i + dn_nu));
-    A = cadd(A, cadd(fwd, bwd));
+    staple_acc_fwd(A, load_link<R, CG>(cs, Vh, NU, q, i + up_mu), load_link<R, CG>(cs, Vh, MU, q, i + up_nu),
+                   load_link<R, CG>(cs, Vh, NU, p, i));
+    staple_acc_bwd(A, load_link<R, CG>(cs, Vh, NU, p, i + up_mu + dn_nu), load_link<R, CG>(cs, Vh, MU, q, i + dn_nu),
+                   load_link<R, CG>(cs, Vh, NU, q, i + dn_nu));
 }
 
 // Metropolis decision for a link with angle th, phase old() = (cos th, sin th) (read after
 // the proposal is formed, which keeps it out of registers during the generator) and staple
 // sum A; the two uniforms come from Philox(counter (link_id, pass, 0, 0), key (seed, 1)).
+// Proposal wrap(fma(width, 2 u1 - 1, th)); action change
+// dS = beta [(cos th - cos th') Re A - (sin th - sin th') Im A] = beta fma(dc, Re A, -(ds Im A)).
 // On acceptance returns true with the new angle and phase in nth, ncs.
 template <typename R, class OldPhase>
 __device__ __forceinline__ bool metropolis_new(R th, OldPhase old_phase, Cx<R> A, uint64_t link_id, uint64_t pass,
@@ -177,13 +180,11 @@ __device__ __forceinline__ bool metropolis_new(R th, OldPhase old_phase, Cx<R> A
     const Philox4 w = philox4x64_10(link_id, pass, 0, 0, seed, kStreamMetropolis);
     const R u1 = P::uniform(w.w[0]);
     const R u2 = P::uniform(w.w[1]);
-    const R prop = P::wrap(th + width * (R(2) * u1 - R(1)));
+    const R prop = P::wrap(fma_r(width, R(2) * u1 - R(1), th));
     const cs_t<R> old = old_phase();
-    const R s_old = -beta * (old.x * A.re - old.y * A.im);
     R sn, cn;
     P::sincos(prop, &sn, &cn);
-    const R s_new = -beta * (cn * A.re - sn * A.im);
-    const R dS = s_new - s_old;
+    const R dS = beta * fma_r(old.x - cn, A.re, -((old.y - sn) * A.im));
     if (u2 < P::exp(-dS)) {
         nth = prop;
         ncs = cs_t<R>{cn, sn};

@@ -249,6 +249,20 @@ __device__ __forceinline__ Cx<double> cmul_rn(Cx<double> a, Cx<double> b)
     // explicit fused form: as deterministic as separate roundings, two FP64 instructions fewer
     return Cx<double>{__fma_rn(a.re, b.re, -__dmul_rn(a.im, b.im)), __fma_rn(a.re, b.im, __dmul_rn(a.im, b.re))};
 }
+// Explicitly fused multiply-add in precision R.
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// A += p q, both components accumulated by fused multiply-adds:
+//   Re: fma(p.re, q.re, fma(-p.im, q.im, A.re)),  Im: fma(p.re, q.im, fma(p.im, q.re, A.im))
+// (the FP64 oracle accumulates its staple terms the same way).
+template <typename T>
+__device__ __forceinline__ void cmul_acc(Cx<T>& A, Cx<T> p, Cx<T> q)
+{
+    A.re = fma_r(p.re, q.re, fma_r(-p.im, q.im, A.re));
+    A.im = fma_r(p.re, q.im, fma_r(p.im, q.re, A.im));
+}
+
 template <typename T>
 __device__ __forceinline__ Cx<T> cconj(Cx<T> a)
 {

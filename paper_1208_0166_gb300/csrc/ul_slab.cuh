@@ -106,11 +106,10 @@ __device__ __forceinline__ void slab_staple_term(Cx<R>& A, const SlabLinks<R, LC
     const int li_nu = li + st.up<NU>();
     const int li_nd = li + st.dn<NU>();
     const int li_dg = li_mu + st.dn<NU>();
-    const Cx<R> fwd = staple_fwd(S.template ld<ZM>(NU, tl + TM, li_mu, q), S.template ld<ZN>(MU, tl + TN, li_nu, q),
-                                 S.template ld<0>(NU, tl, li, p));
-    const Cx<R> bwd = staple_bwd(S.template ld<ZM - ZN>(NU, tl + TM - TN, li_dg, p),
-                                 S.template ld<-ZN>(MU, tl - TN, li_nd, q), S.template ld<-ZN>(NU, tl - TN, li_nd, q));
-    A = cadd(A, cadd(fwd, bwd));
+    staple_acc_fwd(A, S.template ld<ZM>(NU, tl + TM, li_mu, q), S.template ld<ZN>(MU, tl + TN, li_nu, q),
+                   S.template ld<0>(NU, tl, li, p));
+    staple_acc_bwd(A, S.template ld<ZM - ZN>(NU, tl + TM - TN, li_dg, p), S.template ld<-ZN>(MU, tl - TN, li_nd, q),
+                   S.template ld<-ZN>(NU, tl - TN, li_nd, q));
 }
 
 // Global offset in [dir][parity][h] of link dir at site (x, y, zg, tg).
