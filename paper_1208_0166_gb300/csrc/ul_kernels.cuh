@@ -554,24 +554,38 @@ struct InsertionAcc<double> {
         re = fma(T.re, o, re);
         im = fma(T.im, o, im);
     }
+    __device__ __forceinline__ void fold() {}
     __device__ __forceinline__ double total_re() const { return re; }
     __device__ __forceinline__ double total_im() const { return im; }
 };
 
+// FP32: the products of a block of samples are summed by fused multiply-adds into a block
+// partial; fold() adds the partial to a compensated (Kahan) sum, so the rounding error grows
+// with the block length (kInsertionBlock) and not with the number of samples.
+constexpr int kInsertionBlock = 8;
+
 template <>
 struct InsertionAcc<float> {
-    float re = 0.f, re_c = 0.f, im = 0.f, im_c = 0.f;
+    float re = 0.f, re_c = 0.f, im = 0.f, im_c = 0.f; // Kahan sums of block partials
+    float bre = 0.f, bim = 0.f;                       // partial sums of the current block
     static __device__ __forceinline__ void kahan(float& sum, float& comp, float v)
     {
-        const float y = v - comp;
+        const float y = __fsub_rn(v, comp);
         const float t = __fadd_rn(sum, y);
         comp = __fsub_rn(__fsub_rn(t, sum), y);
         sum = t;
     }
     __device__ __forceinline__ void add(Cx<float> T, float o)
     {
-        kahan(re, re_c, __fmul_rn(T.re, o));
-        kahan(im, im_c, __fmul_rn(T.im, o));
+        bre = __fmaf_rn(T.re, o, bre);
+        bim = __fmaf_rn(T.im, o, bim);
+    }
+    __device__ __forceinline__ void fold()
+    {
+        kahan(re, re_c, bre);
+        kahan(im, im_c, bim);
+        bre = 0.f;
+        bim = 0.f;
     }
     __device__ __forceinline__ double total_re() const { return static_cast<double>(re) - static_cast<double>(re_c); }
     __device__ __forceinline__ double total_im() const { return static_cast<double>(im) - static_cast<double>(im_c); }
@@ -602,23 +616,30 @@ struct Vec8<double> {
     }
 };
 
-// Deferred insertion contraction over the `count` samples stored in tk/ok, thread per
-// (s, r, d, x0) with x0 fastest:
+// Deferred insertion contraction over the `count` samples stored in tk/ok:
 //   bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] += sum_k T_k(s,x0,r) O_k(s, x0 + floor(r/2) xhat + d yhat, ch)
+// thread per output (s, r, d, x0), one block per kThreads consecutive x0 of one (s, r, d);
+// the blocks of a tile of x0 are neighbours in the grid for all (r, d) (d fastest, then r),
+// so the transporters and channel rows they share are read from DRAM about once.  Each
+// output is summed over k in order by one thread.  The register bound keeps three
+// 256-thread blocks per SM (the FP32 form holds 48 accumulator registers).
+constexpr int kContractMinBlocks = 3;
+
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     insertion_contract_kernel(Geo g, int S, int r_max, int nd, int count, const Cx<R>* __restrict__ tk,
                               const R* __restrict__ ok, double2* __restrict__ bsum)
 {
-    const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const long total = static_cast<long>(S) * r_max * nd * g.L3;
-    if (idx >= total) return;
-    const int x0 = static_cast<int>(idx % g.L3);
-    long rest = idx / g.L3;
-    const int d = static_cast<int>(rest % nd);
-    rest /= nd;
-    const int r = static_cast<int>(rest % r_max) + 1;
-    const int s = static_cast<int>(rest / r_max);
+    const int tiles = (g.L3 + kThreads - 1) / kThreads;
+    int b = static_cast<int>(blockIdx.x);
+    const int d = b % nd;
+    b /= nd;
+    const int r = b % r_max + 1;
+    b /= r_max;
+    const int tile = b % tiles;
+    const int s = b / tiles;
+    const int x0 = tile * kThreads + static_cast<int>(threadIdx.x);
+    if (x0 >= g.L3) return;
     const int px = x0 % g.L, py = (x0 / g.L) % g.L, pz = x0 / (g.L * g.L);
     const int y = (px + r / 2) % g.L + g.L * ((py + d) % g.L + g.L * pz);
     const long SL3 = static_cast<long>(S) * g.L3;
@@ -629,7 +650,12 @@ __global__ void __launch_bounds__(kThreads)
         Vec8<R>::load(ok + (k * SL3 + static_cast<long>(s) * g.L3 + y) * 8, o);
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, o[ch]);
+        if (k % kInsertionBlock == kInsertionBlock - 1)
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
     }
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
     const long base = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d) * 8) * g.L3 + x0;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
@@ -958,7 +984,7 @@ cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int n
                                       const void* ok, double2* bsum, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
-    const long total = static_cast<long>(S) * r_max * nd * g.L3;
+    const long total = static_cast<long>(S) * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
         g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk), static_cast<const R*>(ok), bsum);
     return cudaGetLastError();

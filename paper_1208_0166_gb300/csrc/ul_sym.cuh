@@ -159,25 +159,28 @@ __global__ void __launch_bounds__(kThreads)
     for (int ch = 0; ch < 8; ++ch) out[ch * g.L3] = C[ch];
 }
 
-// Symmetrised contraction over the `count` stored samples, thread per (a, s, r, d, x0), x0
-// fastest, m = x0 + floor(r/2) e_a:
-//   bsum3[(a-1) nB + (((s R + r-1) nd + d) 8 + ch) L3 + x0] += sum_k T_a,k(s, x0, r) csym_k(a, s, d, m, ch).
+// Symmetrised contraction over the `count` stored samples, m = x0 + floor(r/2) e_a:
+//   bsum3[(a-1) nB + (((s R + r-1) nd + d) 8 + ch) L3 + x0] += sum_k T_a,k(s, x0, r) csym_k(a, s, d, m, ch),
+// thread per output (a, s, r, d, x0) summing over k in order, blocks ordered as in
+// insertion_contract_kernel (a tile of x0 for all (r, d) together).
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     insertion_contract_sym_kernel(Geo g, int S, int r_max, int nd, int count, const Cx<R>* __restrict__ tk3,
                                   const R* __restrict__ csym, double2* __restrict__ bsum3)
 {
-    const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
     const long per_axis = static_cast<long>(S) * r_max * nd * g.L3;
-    if (idx >= 3 * per_axis) return;
-    const int a = static_cast<int>(idx / per_axis) + 1;
-    long rest = idx - (a - 1) * per_axis;
-    const int x0 = static_cast<int>(rest % g.L3);
-    rest /= g.L3;
-    const int d = static_cast<int>(rest % nd);
-    rest /= nd;
-    const int r = static_cast<int>(rest % r_max) + 1;
-    const int s = static_cast<int>(rest / r_max);
+    const int tiles = (g.L3 + kThreads - 1) / kThreads;
+    int b = static_cast<int>(blockIdx.x);
+    const int d = b % nd;
+    b /= nd;
+    const int r = b % r_max + 1;
+    b /= r_max;
+    const int tile = b % tiles;
+    b /= tiles;
+    const int s = b % S;
+    const int a = b / S + 1;
+    const int x0 = tile * kThreads + static_cast<int>(threadIdx.x);
+    if (x0 >= g.L3) return;
     const int m = sym_shift(g.L, x0, a, r / 2);
     InsertionAcc<R> acc[8];
     for (int k = 0; k < count; ++k) {
@@ -185,7 +188,12 @@ __global__ void __launch_bounds__(kThreads)
         const R* C = csym + ((static_cast<long>(k * 3 + a - 1) * S + s) * nd + d) * 8 * g.L3 + m;
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, C[ch * g.L3]);
+        if (k % kInsertionBlock == kInsertionBlock - 1)
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
     }
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
     const long base = (a - 1) * (per_axis * 8) + (((static_cast<long>(s) * r_max + (r - 1)) * nd + d) * 8) * g.L3 + x0;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
@@ -214,7 +222,7 @@ cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, i
                                           const void* csym, double2* bsum3, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
-    const long total = 3L * S * r_max * nd * g.L3;
+    const long total = 3L * S * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_sym_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
         g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk3), static_cast<const R*>(csym), bsum3);
     return cudaGetLastError();

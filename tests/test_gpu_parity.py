@@ -261,6 +261,26 @@ def test_fp32_measurement_path_on_a_fixed_configuration():
         assert err < 2e-6
 
 
+def test_fp32_insertion_sums_over_many_blocks():
+    """The FP32 contraction sums blocks of 8 samples by FMA and the blocks by compensated
+    addition: over 41 samples (six blocks, the last one partial) of a frozen configuration
+    the FP32 estimators stay within FP32 link rounding of FP64."""
+    L, Nt = 8, 8
+    th = random_angles(L, Nt, 45)
+    out = {}
+    for prec in (_lib.UL_FP64, _lib.UL_FP32_ACC64):
+        g = _lib.Lattice(L, Nt, 1.0, 3, prec)
+        g.set_links(th)
+        g.set_option("sub_metro", 0)
+        g.set_option("sub_or", 0)
+        out[prec] = g.multilevel_fields(2, 41, 4, 3)
+    a, b = out[_lib.UL_FP64], out[_lib.UL_FP32_ACC64]
+    for key in ("corr", "fields", "vac"):
+        err = np.max(np.abs(a[key] - b[key]))
+        print(f"FP32 vs FP64 {key}: max abs diff {err:.2e}")
+        assert err < 2e-6
+
+
 @pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
 def test_graph_replay_equals_direct_launches(prec):
     """Captured-and-replayed launch sequences give bit-identical states and results."""
