@@ -60,6 +60,11 @@ struct ul_lattice {
     unsigned int* d_bar = nullptr;    // [0] arrivals, [1] generation
     int* d_status = nullptr;          // nonzero after a wait gave up
     cudaStream_t cap_stream = nullptr;
+    // second stream of the slab-resident form: the insertion contraction of one chunk runs
+    // on it while the next chunk's slab kernel runs on the handle's stream
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_slab[2] = {nullptr, nullptr};
+    cudaEvent_t ev_contract[2] = {nullptr, nullptr};
 
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
@@ -114,6 +119,12 @@ void release(ul_lattice* h)
     cudaFree(h->d_bar);
     cudaFree(h->d_status);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->aux_stream) cudaStreamSynchronize(h->aux_stream);
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_slab[b]) cudaEventDestroy(h->ev_slab[b]);
+        if (h->ev_contract[b]) cudaEventDestroy(h->ev_contract[b]);
+    }
+    if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     cudaFree(h->theta);
     cudaFree(h->cs);
     cudaFree(h->canon);
@@ -288,6 +299,17 @@ int check_device_status(ul_lattice* h)
                 "the link state is incomplete");
 }
 
+// Sub-samples per insertion contraction: a quarter of the level (so that the contraction of
+// one chunk can overlap the next chunk's updates), bounded so that two chunk buffers fit
+// into the option "insertion_chunk_mb".  The same chunks in every launch mode, so that the
+// modes give the same sums.
+int chunk_samples(const ul_lattice* h, int n_sub, size_t per_sample)
+{
+    const size_t cap = (static_cast<size_t>(h->chunk_mb) << 20) / 2;
+    const size_t quarter = (static_cast<size_t>(n_sub) + 3) / 4;
+    return static_cast<int>(std::max<size_t>(1, std::min<size_t>(quarter, cap / per_sample)));
+}
+
 int compound_sweep(ul_lattice* h, int n_metro, int n_or)
 {
     if (h->use_persistent) {
@@ -364,6 +386,13 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
     h->slab_mode = precision == UL_FP32_ACC64 ? 1 : 0;
     if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "capture stream");
+    if ((e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "auxiliary stream");
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaEventCreateWithFlags(&h->ev_slab[b], cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
+        if ((e = cudaEventCreateWithFlags(&h->ev_contract[b], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e, "event");
+    }
     if ((e = cudaMalloc(&h->plaq_partials, ul::plaquette_partials(h->g) * sizeof(double))) != cudaSuccess)
         return bail(e, "plaquette partials");
     if ((e = cudaMemsetAsync(h->d_accepted, 0, sizeof(unsigned long long), h->stream)) != cudaSuccess)
@@ -419,17 +448,13 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
     const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
     const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
     const size_t per_sample = fields ? (n_a * 2 + 8ull * S * g.L3) * rs : 0;
-    int chunk = 0;
-    if (fields) {
-        const size_t cap = static_cast<size_t>(h->chunk_mb) << 20;
-        chunk = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(n_sub), cap / per_sample)));
-    }
+    const int chunk = fields ? chunk_samples(h, n_sub, per_sample) : 0;
     auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
     const size_t off_b = al(n_a * sizeof(double2));
     const size_t off_o = off_b + al(n_b * sizeof(double2));
     const size_t off_t = off_o + al(n_o * sizeof(double));
-    const size_t off_k = off_t + al(fields ? n_a * 2 * rs * chunk : 0);
-    const size_t off_u = off_k + al(fields ? 8ull * S * g.L3 * rs * chunk : 0);
+    const size_t off_k = off_t + al(fields ? n_a * 2 * rs * chunk * 2 : 0); // two chunk buffers
+    const size_t off_u = off_k + al(fields ? 8ull * S * g.L3 * rs * chunk * 2 : 0);
     const size_t off_p = off_u + al(h->multihit ? static_cast<size_t>(g.V) * 2 * rs : 0);
     const size_t off_out = off_p + al(n_p * sizeof(double));
     const size_t bytes = off_out + al(n_out * sizeof(double));
@@ -463,10 +488,17 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
     // Sub-samples in chunks; each chunk (passes + measurement per sample, then the insertion
     // contraction of the chunk) is one launch sequence, replayed as a graph.
     const int seq = fields ? chunk : (slab_cl ? n_sub : std::min(n_sub, 64));
+    int chunk_index = 0;
     for (int k = 0; k < n_sub;) {
         const int count = std::min(seq, n_sub - k);
         const int sm = h->sub_metro, so = h->sub_or;
         if (slab_cl) {
+            // chunk c fills buffer c % 2 on the handle's stream; its contraction runs on the
+            // auxiliary stream (on the SMs the cluster grid leaves free) while chunk c + 1 runs
+            const int buf = chunk_index % 2;
+            void* tkb = static_cast<char*>(tk) + static_cast<size_t>(buf) * n_a * 2 * rs * chunk;
+            void* okb = static_cast<char*>(ok) + static_cast<size_t>(buf) * 8ull * S * g.L3 * rs * chunk;
+            if (fields && chunk_index >= 2) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
             ul::SlabArgs a{};
             a.u = persist_args(h, count, sm, so, slab_t).u;
             a.n_units = count;
@@ -478,8 +510,8 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
             a.fields = fields ? 1 : 0;
             a.slot0 = 0;
             a.asum = asum;
-            a.tk = tk;
-            a.ok = ok;
+            a.tk = tkb;
+            a.ok = okb;
             a.osum = osum;
             cudaError_t e = is_f64(h)
                 ? ul::launch_slab<double>(g, static_cast<double*>(h->theta), h->cs, a, slab_threads, h->stream)
@@ -487,13 +519,18 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
             if (e != cudaSuccess) return cuda_fail(h, e, "slab-resident launch");
             h->launches += 1;
             if (fields) {
-                e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream)
-                              : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream);
+                UL_CK(h, cudaEventRecord(h->ev_slab[buf], h->stream));
+                UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_slab[buf], 0));
+                e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream)
+                              : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+                UL_CK(h, cudaEventRecord(h->ev_contract[buf], h->aux_stream));
                 h->launches += 1;
             }
             account_passes(h, sm * count, slab_t);
             k += count;
+            ++chunk_index;
+            if (k >= n_sub && fields) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
             continue;
         }
         const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
