@@ -169,6 +169,20 @@ int ul_plaquette(ul_lattice* h, double* out);
  */
 int ul_plaquette_noalloc(const double* theta_dev, int L, int Nt, double* out_dev, void* cuda_stream);
 
+/*
+ * ul_rng_uniforms — the Metropolis uniforms (u1, u2) that the update kernels of `precision`
+ * draw for links link0 .. link0+n-1 in Metropolis pass `pass` with `seed` (random numbers
+ * are not specified by the paper; the choice is Philox, Salmon et al., SC'11):
+ *   UL_FP64:       words 0, 1 of Philox4x64-10(counter (link, pass, 0, 0), key (seed, 1)),
+ *                  u = (w >> 11) 2^-53;
+ *   UL_FP32_ACC64: words 0, 1 of Philox4x32-10(counter (link, pass low 32 bits, pass high
+ *                  32 bits, 1), key (seed low, seed high)), u = (w >> 8) 2^-24.
+ * link = mu V + i for link (mu, lexicographic site i).  out: 2n doubles (u1, u2 per link),
+ * caller-owned host memory.  0 <= n <= 2^24.  Synchronous (default stream); allocates.
+ * For tests and reproduction of the update kernels' random numbers.
+ */
+int ul_rng_uniforms(int precision, uint64_t seed, uint64_t pass, uint64_t link0, int n, double* out);
+
 /* ul_free — release the handle and its device memory.  NULL is accepted. */
 int ul_free(ul_lattice* h);
 

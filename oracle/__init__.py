@@ -52,6 +52,8 @@ def _load():
     up = ctypes.POINTER(ctypes.c_uint64)
     ip = ctypes.POINTER(ctypes.c_int)
     lib.ulo_philox4x64_10.argtypes = [up, up, up]
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib.ulo_philox4x32_10.argtypes = [u32p, u32p, u32p]
     lib.ulo_u53.argtypes = [u64]
     lib.ulo_u53.restype = d
     lib.ulo_sincos.argtypes = [d, dp, dp]
@@ -113,6 +115,15 @@ def philox4x64_10(ctr, key) -> np.ndarray:
     o = (ctypes.c_uint64 * 4)()
     lib.ulo_philox4x64_10(c, k, o)
     return np.array(list(o), dtype=np.uint64)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    p = ctypes.POINTER(ctypes.c_uint32)
+    _load().ulo_philox4x32_10(c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
+    return out
 
 
 def u53(w: int) -> float:

@@ -213,6 +213,30 @@ void ulo_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 
 double ulo_u53(uint64_t w) { return (double)(w >> 11) * 0x1.0p-53; }
 
+/* Philox4x32-10 (same paper): per round (hi, lo) = M * c for M0 = 0xD2511F53 on c0 and
+ * M1 = 0xCD9E8D57 on c2, c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), then the key is bumped
+ * by (0x9E3779B9, 0xBB67AE85).  The FP32 path draws its Metropolis uniforms from it. */
+void ulo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        uint64_t pa = (uint64_t)0xD2511F53u * c0, pb = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hiA = (uint32_t)(pa >> 32), loA = (uint32_t)pa;
+        uint32_t hiB = (uint32_t)(pb >> 32), loB = (uint32_t)pb;
+        uint32_t n0 = hiB ^ c1 ^ k0, n2 = hiA ^ c3 ^ k1;
+        c0 = n0;
+        c1 = loB;
+        c2 = n2;
+        c3 = loA;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Geometry                                                                  */
 /* ------------------------------------------------------------------------ */

@@ -28,6 +28,9 @@ void ulo_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 /* Uniform in [0,1) from a 64-bit word: (w >> 11) * 2^-53. */
 double ulo_u53(uint64_t w);
 
+/* Philox4x32-10 (Salmon et al., SC'11): out = Philox4x32-10(ctr, key), 32-bit words. */
+void ulo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
 /* Elementary functions with a fixed IEEE operation sequence (see ul_oracle.c). */
 void ulo_sincos(double x, double* s, double* c);
 double ulo_exp(double x);

@@ -45,6 +45,7 @@ SIGNATURES = [
     ("ul_multilevel", _I, [_P, _I, _I, _I, _DP]),
     ("ul_multilevel_fields", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
     ("ul_multilevel_fields_sym", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
+    ("ul_rng_uniforms", _I, [_I, _U64, _U64, _U64, _I, _DP]),
     ("ul_multilevel2", _I, [_P, _I, _I, _I, _I, _I, _DP]),
     ("ul_plaquette", _I, [_P, _DP]),
     ("ul_free", _I, [_P]),
@@ -291,3 +292,10 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def rng_uniforms(precision: int, seed: int, pass_: int, link0: int, n: int) -> np.ndarray:
+    """(n, 2) array of the Metropolis uniforms the update kernels draw (ul_rng_uniforms)."""
+    out = np.zeros(2 * n)
+    _check(load().ul_rng_uniforms(int(precision), int(seed), int(pass_), int(link0), int(n), _dp(out)))
+    return out.reshape(n, 2)

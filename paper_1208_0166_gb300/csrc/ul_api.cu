@@ -1008,6 +1008,28 @@ int ul_set_stream(ul_lattice* h, void* cuda_stream)
     return UL_OK;
 }
 
+int ul_rng_uniforms(int precision, uint64_t seed, uint64_t pass, uint64_t link0, int n, double* out)
+{
+    if (precision != UL_FP64 && precision != UL_FP32_ACC64)
+        return fail(nullptr, UL_EINVAL, "ul_rng_uniforms: precision must be UL_FP64 or UL_FP32_ACC64");
+    if (n < 0 || n > (1 << 24) || (n > 0 && !out))
+        return fail(nullptr, UL_EINVAL, "ul_rng_uniforms: n must be in [0, 2^24] and out non-NULL");
+    if (n == 0) return UL_OK;
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2ull * n * sizeof(double));
+    if (e == cudaSuccess)
+        e = precision == UL_FP64 ? ul::launch_rng_uniforms<double>(seed, pass, link0, n, d, nullptr)
+                                 : ul::launch_rng_uniforms<float>(seed, pass, link0, n, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, 2ull * n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? UL_ENOMEM : UL_ECUDA,
+                    std::string("ul_rng_uniforms: ") + cudaGetErrorString(e));
+    }
+    return UL_OK;
+}
+
 const char* ul_last_error(const ul_lattice* h) { return h ? h->err.c_str() : g_init_error.c_str(); }
 
 int ul_precision(const ul_lattice* h) { return h ? h->precision : UL_EINVAL; }

@@ -111,7 +111,41 @@ __device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint6
     return r;
 }
 
-// Philox stream ids (second key word)
+// Philox4x32-10 (same paper): ten rounds of two 32x32->64 multiplications, 32-bit Weyl key
+// schedule; used for the Metropolis uniforms of the FP32 path, which need 48 random bits.
+struct Philox4x32 {
+    uint32_t w[4];
+};
+
+__device__ __forceinline__ Philox4x32 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                     uint32_t k1)
+{
+    constexpr uint32_t kMulA = 0xD2511F53u;
+    constexpr uint32_t kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kWeylA = 0x9E3779B9u;
+    constexpr uint32_t kWeylB = 0xBB67AE85u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hiA = __umulhi(kMulA, c0), loA = kMulA * c0;
+        const uint32_t hiB = __umulhi(kMulB, c2), loB = kMulB * c2;
+        const uint32_t n0 = hiB ^ c1 ^ k0;
+        const uint32_t n2 = hiA ^ c3 ^ k1;
+        c0 = n0;
+        c1 = loB;
+        c2 = n2;
+        c3 = loA;
+        k0 += kWeylA;
+        k1 += kWeylB;
+    }
+    Philox4x32 r;
+    r.w[0] = c0;
+    r.w[1] = c1;
+    r.w[2] = c2;
+    r.w[3] = c3;
+    return r;
+}
+
+// Philox stream ids (second key word of Philox4x64, fourth counter word of Philox4x32)
 enum : uint64_t { kStreamHotStart = 0, kStreamMetropolis = 1 };
 
 } // namespace ul

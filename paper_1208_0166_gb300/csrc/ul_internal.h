@@ -32,6 +32,10 @@ cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int pa
                                 double width, int slab_t, unsigned long long* accepted, cudaStream_t st,
                                 int* launched, bool pdl);
 
+// Metropolis uniforms of links link0 .. link0+n-1 (out: 2n doubles, device memory).
+template <typename R>
+cudaError_t launch_rng_uniforms(uint64_t seed, uint64_t pass, uint64_t link0, int n, double* out, cudaStream_t st);
+
 // *p = v (one thread); sets the pass base read by graph-replayed update kernels.
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 

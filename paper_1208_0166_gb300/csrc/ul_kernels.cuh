@@ -177,9 +177,8 @@ __device__ __forceinline__ bool metropolis_new(R th, OldPhase old_phase, Cx<R> A
                                                uint64_t seed, R width, R beta, R& nth, cs_t<R>& ncs)
 {
     using P = Prec<R>;
-    const Philox4 w = philox4x64_10(link_id, pass, 0, 0, seed, kStreamMetropolis);
-    const R u1 = P::uniform(w.w[0]);
-    const R u2 = P::uniform(w.w[1]);
+    R u1, u2;
+    P::metro_uniforms(link_id, pass, seed, &u1, &u2);
     const R prop = P::wrap(fma_r(width, R(2) * u1 - R(1), th));
     const cs_t<R> old = old_phase();
     R sn, cn;
@@ -251,6 +250,27 @@ __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta,
     theta[off] = nth;
     cs[off] = ncs;
     return false;
+}
+
+// The Metropolis uniforms (u1, u2) of links link0 .. link0 + n - 1 in pass `pass`, as the update
+// kernels draw them (for tests of the generator against its reference).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) rng_uniforms_kernel(uint64_t seed, uint64_t pass, uint64_t link0, int n,
+                                                                 double* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    R u1, u2;
+    Prec<R>::metro_uniforms(link0 + static_cast<uint64_t>(i), pass, seed, &u1, &u2);
+    out[2 * i] = static_cast<double>(u1);
+    out[2 * i + 1] = static_cast<double>(u2);
+}
+
+template <typename R>
+cudaError_t launch_rng_uniforms(uint64_t seed, uint64_t pass, uint64_t link0, int n, double* out, cudaStream_t st)
+{
+    rng_uniforms_kernel<R><<<blocks_for(n), kThreads, 0, st>>>(seed, pass, link0, n, out);
+    return cudaGetLastError();
 }
 
 // Threads per block of the one-class-per-launch update kernel: small blocks spread the
@@ -1063,6 +1083,7 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
                                                void*, void*, double*, cudaStream_t);                              \
     template cudaError_t launch_insertion_contract_sym<R>(const Geo&, int, int, int, int, const void*,             \
                                                           const void*, double2*, cudaStream_t);                   \
+    template cudaError_t launch_rng_uniforms<R>(uint64_t, uint64_t, uint64_t, int, double*, cudaStream_t);        \
     template cudaError_t slab_plan<R>(const Geo&, int, int, int*, int*);                                           \
     template cudaError_t launch_slab<R>(const Geo&, R*, void*, const SlabArgs&, int, cudaStream_t);               \
     template cudaError_t launch_persistent<R>(const Geo&, R*, void*, const PersistArgs&, int, cudaStream_t);       \

@@ -22,6 +22,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ul_device.cuh"
+
 namespace ul {
 
 struct c64 {
@@ -167,6 +169,15 @@ struct Prec<double> {
     {
         return static_cast<double>(w >> 11) * 0x1.0p-53;
     }
+    // Metropolis uniforms of link link_id in pass `pass`: words 0 and 1 of
+    // Philox4x64-10(counter (link_id, pass, 0, 0), key (seed, 1))
+    static __device__ __forceinline__ void metro_uniforms(uint64_t link_id, uint64_t pass, uint64_t seed, double* u1,
+                                                          double* u2)
+    {
+        const Philox4 w = philox4x64_10(link_id, pass, 0, 0, seed, kStreamMetropolis);
+        *u1 = uniform(w.w[0]);
+        *u2 = uniform(w.w[1]);
+    }
     // th - 2pi floor((th + pi) / 2pi).  For a = th + pi in [-2pi, 4pi) the floor of the
     // correctly rounded quotient a / 2pi is -1, 0 or 1 exactly where a < 0, a < 2pi,
     // a < 4pi (no quotient in that range rounds across an integer: the double nearest
@@ -196,6 +207,17 @@ struct Prec<float> {
     static __device__ __forceinline__ float uniform(uint64_t w)
     {
         return static_cast<float>(static_cast<uint32_t>(w >> 40)) * 0x1.0p-24f;
+    }
+    // Metropolis uniforms: words 0 and 1 of Philox4x32-10(counter (link_id, pass low, pass
+    // high, 1), key (seed low, seed high)), 24 bits each: u = (w >> 8) 2^-24
+    static __device__ __forceinline__ void metro_uniforms(uint64_t link_id, uint64_t pass, uint64_t seed, float* u1,
+                                                          float* u2)
+    {
+        const Philox4x32 w = philox4x32_10(static_cast<uint32_t>(link_id), static_cast<uint32_t>(pass),
+                                           static_cast<uint32_t>(pass >> 32), static_cast<uint32_t>(kStreamMetropolis),
+                                           static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+        *u1 = static_cast<float>(w.w[0] >> 8) * 0x1.0p-24f;
+        *u2 = static_cast<float>(w.w[1] >> 8) * 0x1.0p-24f;
     }
     static __device__ __forceinline__ float wrap(float th)
     {

@@ -20,6 +20,22 @@ mp = pytest.importorskip("mpmath")
 
 
 # --------------------------------------------------------------------------
+# Random numbers: Philox4x32-10 (FP32 Metropolis uniforms) against the published
+# known-answer vectors
+# --------------------------------------------------------------------------
+
+def test_philox4x32_known_answers():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(w, 16) for w in row]
+        got = O.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in got] == v[6:10]
+
+
+# --------------------------------------------------------------------------
 # Random numbers: Philox4x64-10 against numpy's independent implementation
 # --------------------------------------------------------------------------
 
