@@ -165,6 +165,36 @@ def _measure(lat, args):
     return lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
 
 
+def fp32_error_vs_fp64(lib):
+    """Error of the FP32+FP64-accumulation estimators against the FP64 path on one frozen
+    24^4 configuration (the same angles in both precisions, sub-samples without updates, so
+    the difference is the FP32 arithmetic alone; the FP64 path equals the oracle bit for bit).
+    Max absolute difference per observable, and relative to the largest FP64 value."""
+    import numpy as np
+
+    g64 = lib.Lattice(W.L, W.Nt, W.beta, 77, lib.UL_FP64)
+    for _ in range(5):
+        g64.sweep(1, 3)
+    th = g64.get_links()
+    g32 = lib.Lattice(W.L, W.Nt, W.beta, 77, lib.UL_FP32_ACC64)
+    g32.set_links(th)
+    out = {}
+    res = []
+    for g in (g64, g32):
+        g.set_option("sub_metro", 0)
+        g.set_option("sub_or", 0)
+        res.append(g.multilevel_fields(SLAB_T, 16, W.r_max, W.d_max))
+        res[-1]["plaquette"] = np.array([g.plaquette()])
+    for key in ("corr", "fields", "vac", "plaquette"):
+        a, b = np.asarray(res[0][key]), np.asarray(res[1][key])
+        err = float(np.max(np.abs(a - b)))
+        out[key] = {"max_abs": err, "rel_to_max": err / max(float(np.max(np.abs(a))), 1e-300)}
+    g64.close()
+    g32.close()
+    out["workload"] = "24^4 after 5 FP64 sweeps, frozen (16 sub-samples without updates), both precisions"
+    return out
+
+
 def _options(args):
     out = {}
     for kv in args.option:
@@ -490,7 +520,8 @@ def run_ours(args):
                    "sweep_ms_per_step": o["sweep_ms"] / K, "multilevel_ms_per_step": o["ml_ms"] / K,
                    "correlator_samples_per_s": SAMPLES_PER_STEP * K * ws / o_s,
                    "ms_per_step": o_s / K * 1e3, "gpu_launches": o["launches"],
-                   "C_r": [[z.real, z.imag] for z in o["corr"][:4]]}
+                   "C_r": [[z.real, z.imag] for z in o["corr"][:4]],
+                   "fp32_error_vs_fp64": fp32_error_vs_fp64(lib)}
 
     peaks = _peaks()
     update_launches = W.therm_sweeps * (W.sweep_metro + W.sweep_or) * 8

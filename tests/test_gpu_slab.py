@@ -108,3 +108,15 @@ def test_slab_resident_benchmark_shape(prec, L):
     assert np.array_equal(a.get_links(), b.get_links())
     for key in ("corr", "fields", "vac"):
         assert np.array_equal(ra[key], rb[key])
+
+
+def test_slab_resident_sixteen_cta_clusters_at_32():
+    """L = 32 in FP32 needs 16 CTAs per slab (a non-portable cluster size); where the GPU
+    cannot launch that shape the per-class path runs.  Either way the trajectory and the
+    observables are those of the per-class path bit for bit."""
+    a, ra, la = _run(32, 4, 9, _lib.UL_FP32_ACC64, 1, 2, 2, 4, 3, sweeps=1)
+    b, rb, lb = _run(32, 4, 9, _lib.UL_FP32_ACC64, 0, 2, 2, 4, 3, sweeps=1)
+    print(f"L=32 FP32 slab-form launches {la} (per-class {lb})")
+    assert np.array_equal(a.get_links(), b.get_links())
+    for key in ("corr", "fields", "vac"):
+        assert np.array_equal(ra[key], rb[key])
