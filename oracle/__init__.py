@@ -89,6 +89,8 @@ def _load():
     lib.ulo_multilevel.restype = i
     lib.ulo_gauge_transform.argtypes = [i, i, u64, dp]
     lib.ulo_multilevel_sym.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, dp, dp, dp]
+    lib.ulo_multilevel2_fields.argtypes = [i, i, d, u64, d, dp, up, i, i, i, i, i, i, i, i, dp, dp, dp]
+    lib.ulo_multilevel2_fields.restype = i
     lib.ulo_multilevel_sym.restype = i
     lib.ulo_symmetry_transform.argtypes = [i, i, dp, ip, ip, dp]
     _lib = lib
@@ -262,6 +264,21 @@ class Lattice:
                                         int(sub_or), int(r_max), int(d_max), _dp(corr), _dp(fields), _dp(vac))
         if rc != 0:
             raise ValueError("invalid multilevel arguments")
+        return {"corr": _cplx(corr.reshape(-1, 2)),
+                "fields": _cplx(fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)), "vac": vac}
+
+    def multilevel2_fields(self, tau1: int, n1: int, tau2: int, n2: int, r_max: int, d_max: int,
+                           sub_metro: int = 1, sub_or: int = 3):
+        """Two-level estimator with field insertions; dict(corr, fields, vac)."""
+        corr = np.empty(2 * r_max, dtype=np.float64)
+        fields = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64)
+        vac = np.empty(N_CHANNELS, dtype=np.float64)
+        rc = _load().ulo_multilevel2_fields(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+                                            ctypes.byref(self.metro_pass), int(tau1), int(n1), int(tau2), int(n2),
+                                            int(sub_metro), int(sub_or), int(r_max), int(d_max), _dp(corr),
+                                            _dp(fields), _dp(vac))
+        if rc != 0:
+            raise ValueError("invalid two-level arguments")
         return {"corr": _cplx(corr.reshape(-1, 2)),
                 "fields": _cplx(fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)), "vac": vac}
 

@@ -769,6 +769,131 @@ int ulo_multilevel(int L, int Nt, double beta, uint64_t seed, double width, doub
     return 0;
 }
 
+/* Two-level estimator with field insertions (Section 2.2: the bracketed factors of the field
+ * estimator are level-1 averages over the level-2 slabs inside a level-1 slab).  Level-2
+ * means over the n2 samples of one level-1 iteration, per level-2 slab s2:
+ *   A2(s2) = <T>,  B2(s2, d, ch) = <T O(x0 + floor(r/2) xhat + d yhat, ch)>;
+ * one level-1 sample per level-1 slab s1 (level-2 slabs j = 0..m-1 inside it):
+ *   a1 = prod_j A2(j),  b1 = sum_j B2(j) prod_{j' != j} A2(j');
+ * with A1, B1 their means over the n1 level-1 samples,
+ *   corr = (1/L^3) sum_x0 prod_s1 A1(s1),  fields = (1/V) sum_x0 sum_s1 B1(s1) prod_{s1' != s1} A1(s1'),
+ *   vac = <O> over all sites, slices and the n1 n2 level-2 samples. */
+int ulo_multilevel2_fields(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
+                           uint64_t* metro_pass, int tau1, int n1, int tau2, int n2, int sub_metro, int sub_or,
+                           int r_max, int d_max, double* corr, double* fields, double* vac)
+{
+    if (tau1 < 1 || tau2 < 1 || Nt % tau1 != 0 || tau1 % tau2 != 0 || n1 < 1 || n2 < 1 || r_max < 1 ||
+        r_max > L / 2 || d_max < 0 || d_max >= L)
+        return -1;
+    lat_t g = mk(L, Nt);
+    long L3 = (long)L * L * L;
+    int S1 = Nt / tau1, S2 = Nt / tau2, m = tau1 / tau2, nd = d_max + 1;
+    long nA1 = (long)S1 * L3 * r_max, nA2 = (long)S2 * L3 * r_max;
+    cplx* A1 = (cplx*)calloc((size_t)nA1, sizeof(cplx));
+    cplx* B1 = (cplx*)calloc((size_t)(nA1 * nd * 8), sizeof(cplx));
+    cplx* A2 = (cplx*)calloc((size_t)nA2, sizeof(cplx));
+    cplx* B2 = (cplx*)calloc((size_t)(nA2 * nd * 8), sizeof(cplx));
+    double Osum[8] = {0};
+    if (!A1 || !B1 || !A2 || !B2) {
+        free(A1);
+        free(B1);
+        free(A2);
+        free(B2);
+        return -2;
+    }
+    for (int k1 = 0; k1 < n1; k1++) {
+        ulo_sweep(L, Nt, beta, seed, width, theta, metro_pass, sub_metro, sub_or, tau1);
+        memset(A2, 0, sizeof(cplx) * (size_t)nA2);
+        memset(B2, 0, sizeof(cplx) * (size_t)(nA2 * nd * 8));
+        for (int k2 = 0; k2 < n2; k2++) {
+            ulo_sweep(L, Nt, beta, seed, width, theta, metro_pass, sub_metro, sub_or, tau2);
+            for (int s = 0; s < S2; s++)
+                for (long x0 = 0; x0 < L3; x0++)
+                    for (int r = 1; r <= r_max; r++) {
+                        cplx T = slab_transporter(&g, theta, tau2, s, x0, r, 0, beta);
+                        long a = ((long)s * L3 + x0) * r_max + (r - 1);
+                        A2[a] = cadd(A2[a], T);
+                        for (int d = 0; d < nd; d++) {
+                            long y = spatial_shift(&g, x0, r / 2, d);
+                            for (int ch = 0; ch < 8; ch++) {
+                                double O = 0.0;
+                                for (int t = s * tau2; t < (s + 1) * tau2; t++)
+                                    O += channel_value(&g, theta, ch, spatial_to_site(&g, y, t));
+                                long b = (a * nd + d) * 8 + ch;
+                                B2[b] = cadd(B2[b], cscale(T, O));
+                            }
+                        }
+                    }
+            if (vac)
+                for (int ch = 0; ch < 8; ch++)
+                    for (long i = 0; i < g.V; i++) Osum[ch] += channel_value(&g, theta, ch, i);
+        }
+        for (int s1 = 0; s1 < S1; s1++)
+            for (long x0 = 0; x0 < L3; x0++)
+                for (int r = 1; r <= r_max; r++) {
+                    long a1 = ((long)s1 * L3 + x0) * r_max + (r - 1);
+                    cplx prod = cmk(1.0, 0.0);
+                    for (int j = 0; j < m; j++)
+                        prod = cmul(prod, cdivr(A2[((long)(s1 * m + j) * L3 + x0) * r_max + (r - 1)], (double)n2));
+                    A1[a1] = cadd(A1[a1], prod);
+                    for (int d = 0; d < nd; d++)
+                        for (int ch = 0; ch < 8; ch++) {
+                            cplx b = cmk(0.0, 0.0);
+                            for (int j = 0; j < m; j++) {
+                                long a2 = ((long)(s1 * m + j) * L3 + x0) * r_max + (r - 1);
+                                cplx term = cdivr(B2[(a2 * nd + d) * 8 + ch], (double)n2);
+                                for (int j2 = 0; j2 < m; j2++) {
+                                    if (j2 == j) continue;
+                                    term = cmul(term, cdivr(A2[((long)(s1 * m + j2) * L3 + x0) * r_max + (r - 1)],
+                                                            (double)n2));
+                                }
+                                b = cadd(b, term);
+                            }
+                            long ib = (a1 * nd + d) * 8 + ch;
+                            B1[ib] = cadd(B1[ib], b);
+                        }
+                }
+    }
+    for (int r = 1; r <= r_max; r++) {
+        cplx sum = cmk(0.0, 0.0);
+        for (long x0 = 0; x0 < L3; x0++) {
+            cplx prod = cmk(1.0, 0.0);
+            for (int s1 = 0; s1 < S1; s1++)
+                prod = cmul(prod, cdivr(A1[((long)s1 * L3 + x0) * r_max + (r - 1)], (double)n1));
+            sum = cadd(sum, prod);
+        }
+        sum = cdivr(sum, (double)L3);
+        corr[2 * (r - 1)] = sum.re;
+        corr[2 * (r - 1) + 1] = sum.im;
+    }
+    for (int r = 1; r <= r_max; r++)
+        for (int d = 0; d < nd; d++)
+            for (int ch = 0; ch < 8; ch++) {
+                cplx sum = cmk(0.0, 0.0);
+                for (long x0 = 0; x0 < L3; x0++)
+                    for (int s1 = 0; s1 < S1; s1++) {
+                        long a1 = ((long)s1 * L3 + x0) * r_max + (r - 1);
+                        cplx term = cdivr(B1[(a1 * nd + d) * 8 + ch], (double)n1);
+                        for (int s2 = 0; s2 < S1; s2++) {
+                            if (s2 == s1) continue;
+                            term = cmul(term, cdivr(A1[((long)s2 * L3 + x0) * r_max + (r - 1)], (double)n1));
+                        }
+                        sum = cadd(sum, term);
+                    }
+                sum = cdivr(sum, (double)g.V);
+                long o = (((long)(r - 1) * nd + d) * 8 + ch) * 2;
+                fields[o] = sum.re;
+                fields[o + 1] = sum.im;
+            }
+    if (vac)
+        for (int ch = 0; ch < 8; ch++) vac[ch] = Osum[ch] / ((double)n1 * (double)n2 * (double)g.V);
+    free(A1);
+    free(B1);
+    free(A2);
+    free(B2);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Symmetrised insertions: the one-level estimator averaged over the 24      */
 /* lattice symmetries that keep the time axis and send the separation        */

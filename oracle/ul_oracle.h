@@ -139,6 +139,18 @@ int ulo_multilevel_sym(int L, int Nt, double beta, uint64_t seed, double width, 
 void ulo_symmetry_transform(int L, int Nt, const double* theta, const int axis_of[4], const int sign_of[4],
                             double* out);
 
+/*
+ * Two-level estimator with field insertions (the paper's bracketed field estimator, Section
+ * 2.2): level-2 means A2 = <T>, B2 = <T O> per level-2 slab over the n2 samples of a level-1
+ * iteration; per level-1 slab one sample a1 = prod_j A2(j), b1 = sum_j B2(j) prod_{j' != j} A2(j');
+ * corr, fields as ulo_multilevel with the level-1 means of a1, b1 as the slab factors; vac
+ * the mean of O over all level-2 samples.  Insertion geometry, channels and output layouts as
+ * ulo_multilevel (fields required, vac may be NULL); no multihit.  0 on success.
+ */
+int ulo_multilevel2_fields(int L, int Nt, double beta, uint64_t seed, double width, double* theta,
+                           uint64_t* metro_pass, int tau1, int n1, int tau2, int n2, int sub_metro, int sub_or,
+                           int r_max, int d_max, double* corr, double* fields, double* vac);
+
 /* I1(x)/I0(x), x >= 0 (power series; asymptotic series beyond x = 600). */
 double ulo_bessel_ratio(double x);
 
