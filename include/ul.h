@@ -110,6 +110,24 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
                          double* out_corr, double* out_fields, double* out_vac);
 
 /*
+ * ul_multilevel2_fields — the two-level estimator with field insertions: the paper's
+ * field estimator (Section 2.2) with its bracketed factors read as level-1 averages.
+ * n1 times: "sub_metro" + "sub_or" passes with the spatial links on t = 0 mod tau1 frozen,
+ * then n2 sub-samples with t = 0 mod tau2 also frozen, each measured as in
+ * ul_multilevel_fields (thickness tau2); per level-1 iteration the level-2 means
+ * A2 = <T>, B2 = <T O> of each level-2 slab, and per level-1 slab (level-2 slabs j inside it)
+ * one level-1 sample  a1 = prod_j A2(j),  b1 = sum_j B2(j) prod_{j' != j} A2(j').
+ *   out_corr  : (1/L^3) sum_x0 prod_{level-1 slabs} <a1>                     (2*r_max doubles)
+ *   out_fields: (1/V) sum_x0 sum_s1 <b1>(s1) prod_{s1' != s1} <a1>(s1')  (layout of ul_multilevel_fields)
+ *   out_vac   : <O> over all sites, slices and the n1*n2 level-2 samples (8 doubles, may be NULL).
+ * tau2 divides tau1, tau1 divides Nt, tau1/tau2 <= 16, n1, n2 >= 1, 1 <= r_max <= L/2,
+ * 0 <= d_max < L; "multihit" must be 0 (UL_EINVAL otherwise).  The level-2 sub-samples run
+ * slab-resident under the same conditions as in ul_multilevel_fields.
+ */
+int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int r_max, int d_max,
+                          double* out_corr, double* out_fields, double* out_vac);
+
+/*
  * ul_multilevel_fields_sym — ul_multilevel_fields averaged over the 24 frames of the source
  * pair: the estimator of Section 2.2, which the paper evaluates in one frame, evaluated in
  * every frame to which a lattice symmetry keeping the time axis and the orientation of the

@@ -46,6 +46,7 @@ SIGNATURES = [
     ("ul_multilevel_fields", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
     ("ul_multilevel_fields_sym", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
     ("ul_rng_uniforms", _I, [_I, _U64, _U64, _U64, _I, _DP]),
+    ("ul_multilevel2_fields", _I, [_P, _I, _I, _I, _I, _I, _I, _DP, _DP, _DP]),
     ("ul_multilevel2", _I, [_P, _I, _I, _I, _I, _I, _DP]),
     ("ul_plaquette", _I, [_P, _DP]),
     ("ul_free", _I, [_P]),
@@ -154,6 +155,16 @@ class Lattice:
         vac = np.zeros(N_CHANNELS)
         _check(load().ul_multilevel_fields(self._h, int(slab_t), int(n_sub), int(r_max), int(d_max), _dp(corr),
                                            _dp(fields), _dp(vac)), self._h)
+        f = fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)
+        return {"corr": corr[0::2] + 1j * corr[1::2], "fields": f[..., 0] + 1j * f[..., 1], "vac": vac}
+
+    def multilevel2_fields(self, tau1: int, n1: int, tau2: int, n2: int, r_max: int, d_max: int):
+        """Two-level estimator with field insertions (ul_multilevel2_fields)."""
+        corr = np.zeros(2 * r_max)
+        fields = np.zeros(2 * r_max * (d_max + 1) * N_CHANNELS)
+        vac = np.zeros(N_CHANNELS)
+        _check(load().ul_multilevel2_fields(self._h, int(tau1), int(n1), int(tau2), int(n2), int(r_max), int(d_max),
+                                            _dp(corr), _dp(fields), _dp(vac)), self._h)
         f = fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)
         return {"corr": corr[0::2] + 1j * corr[1::2], "fields": f[..., 0] + 1j * f[..., 1], "vac": vac}
 

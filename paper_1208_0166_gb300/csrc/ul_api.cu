@@ -328,6 +328,160 @@ int compound_sweep(ul_lattice* h, int n_metro, int n_or)
     return UL_OK;
 }
 
+// Buffers of one multilevel level: accumulators (sum of T per (s, r, x0); sum of T O per
+// (s, r, d, ch, x0); sum of O per (ch, s, x0)), the per-sample T / O storage for two chunks of
+// `chunk` sub-samples, and the multihit links (may be null).
+struct LevelBufs {
+    double2* asum;
+    double2* bsum;
+    double* osum;
+    void* tk;
+    void* ok;
+    void* ubar;
+    int chunk;
+};
+
+// n_sub sub-samples of one level (slab thickness slab_t): passes with the slab boundaries
+// frozen, a measurement after each, and with fields the insertion contraction of each
+// chunk, added into the accumulators of b.  Slab-resident where the slab fits (and neither
+// multihit nor persistent mode is on), else persistent or per-class launches.
+int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fields, const LevelBufs& b)
+{
+    const ul::Geo& g = h->g;
+    const int S = g.Nt / slab_t;
+    const size_t rs = real_size(h);
+    const size_t n_a = static_cast<size_t>(S) * r_max * g.L3;
+    double2* asum = b.asum;
+    double2* bsum = b.bsum;
+    double* osum = b.osum;
+    void* tk = b.tk;
+    void* ok = b.ok;
+    void* ubar = b.ubar;
+    const int chunk = b.chunk;
+    int rc = UL_OK;
+
+    // Slab-resident form: one cluster launch per chunk of sub-samples, where the slab fits
+    // into the shared memory of a cluster (multihit values are formed by their own kernel,
+    // so that mode keeps the per-class launches).
+    int slab_cl = 0, slab_threads = 0;
+    if (h->slab_mode && !ubar && !h->use_persistent) {
+        cudaError_t e = is_f64(h) ? ul::slab_plan<double>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads)
+                                  : ul::slab_plan<float>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads);
+        if (e != cudaSuccess) return cuda_fail(h, e, "slab plan");
+    }
+
+    // Sub-samples in chunks; each chunk (passes + measurement per sample, then the insertion
+    // contraction of the chunk) is one launch sequence, replayed as a graph.
+    const int seq = fields ? chunk : (slab_cl ? n_sub : std::min(n_sub, 64));
+    int chunk_index = 0;
+    for (int k = 0; k < n_sub;) {
+        const int count = std::min(seq, n_sub - k);
+        const int sm = h->sub_metro, so = h->sub_or;
+        if (slab_cl) {
+            // chunk c fills buffer c % 2 on the handle's stream; its contraction runs on the
+            // auxiliary stream (on the SMs the cluster grid leaves free) while chunk c + 1 runs
+            const int buf = chunk_index % 2;
+            void* tkb = static_cast<char*>(tk) + static_cast<size_t>(buf) * n_a * 2 * rs * chunk;
+            void* okb = static_cast<char*>(ok) + static_cast<size_t>(buf) * 8ull * S * g.L3 * rs * chunk;
+            if (fields && chunk_index >= 2) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
+            ul::SlabArgs a{};
+            a.u = persist_args(h, count, sm, so, slab_t).u;
+            a.n_units = count;
+            a.n_metro = sm;
+            a.n_or = so;
+            a.cluster = slab_cl;
+            a.nz = g.L / slab_cl;
+            a.r_max = r_max;
+            a.fields = fields ? 1 : 0;
+            a.slot0 = 0;
+            a.asum = asum;
+            a.tk = tkb;
+            a.ok = okb;
+            a.osum = osum;
+            cudaError_t e = is_f64(h)
+                ? ul::launch_slab<double>(g, static_cast<double*>(h->theta), h->cs, a, slab_threads, h->stream)
+                : ul::launch_slab<float>(g, static_cast<float*>(h->theta), h->cs, a, slab_threads, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "slab-resident launch");
+            h->launches += 1;
+            if (fields) {
+                UL_CK(h, cudaEventRecord(h->ev_slab[buf], h->stream));
+                UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_slab[buf], 0));
+                e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream)
+                              : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+                UL_CK(h, cudaEventRecord(h->ev_contract[buf], h->aux_stream));
+                h->launches += 1;
+            }
+            account_passes(h, sm * count, slab_t);
+            k += count;
+            ++chunk_index;
+            if (k >= n_sub && fields) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
+            continue;
+        }
+        const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
+                                            bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
+                                            reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
+                                            reinterpret_cast<long long>(tk), reinterpret_cast<long long>(ok),
+                                            reinterpret_cast<long long>(osum), reinterpret_cast<long long>(ubar)};
+        if (h->use_persistent) {
+            ul::PersistArgs a = persist_args(h, count, sm, so, slab_t);
+            a.measure = 1;
+            a.r_max = r_max;
+            a.fields = fields ? 1 : 0;
+            a.slot0 = 0;
+            a.asum = asum;
+            a.tk = tk;
+            a.ok = ok;
+            a.osum = osum;
+            a.ubar = ubar;
+            rc = launch_persistent(h, a);
+            if (rc) return rc;
+            if (fields) {
+                cudaError_t e = is_f64(h)
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream)
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+                h->launches += 1;
+            }
+            account_passes(h, sm * count, slab_t);
+            k += count;
+            continue;
+        }
+        rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* base) -> long {
+            long n = 0;
+            for (int j = 0; j < count; ++j) {
+                const long m = enqueue_passes(h, st, sm, so, slab_t, first + static_cast<uint64_t>(j) * sm, base);
+                if (m < 0) return m;
+                n += m;
+                cudaError_t e;
+                if (ubar) {
+                    e = is_f64(h) ? ul::launch_multihit<double>(g, h->cs, h->beta, ubar, st)
+                                  : ul::launch_multihit<float>(g, h->cs, h->beta, ubar, st);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "multihit launch");
+                    ++n;
+                }
+                e = is_f64(h)
+                    ? ul::launch_measure_store<double>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st)
+                    : ul::launch_measure_store<float>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
+                ++n;
+            }
+            if (fields) {
+                cudaError_t e = is_f64(h)
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, st)
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+                ++n;
+            }
+            return n;
+        });
+        if (rc) return rc;
+        account_passes(h, sm * count, slab_t);
+        k += count;
+    }
+    return UL_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -475,125 +629,8 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
         UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
     }
 
-    // Slab-resident form: one cluster launch per chunk of sub-samples, where the slab fits
-    // into the shared memory of a cluster (multihit values are formed by their own kernel,
-    // so that mode keeps the per-class launches).
-    int slab_cl = 0, slab_threads = 0;
-    if (h->slab_mode && !ubar && !h->use_persistent) {
-        cudaError_t e = is_f64(h) ? ul::slab_plan<double>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads)
-                                  : ul::slab_plan<float>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads);
-        if (e != cudaSuccess) return cuda_fail(h, e, "slab plan");
-    }
-
-    // Sub-samples in chunks; each chunk (passes + measurement per sample, then the insertion
-    // contraction of the chunk) is one launch sequence, replayed as a graph.
-    const int seq = fields ? chunk : (slab_cl ? n_sub : std::min(n_sub, 64));
-    int chunk_index = 0;
-    for (int k = 0; k < n_sub;) {
-        const int count = std::min(seq, n_sub - k);
-        const int sm = h->sub_metro, so = h->sub_or;
-        if (slab_cl) {
-            // chunk c fills buffer c % 2 on the handle's stream; its contraction runs on the
-            // auxiliary stream (on the SMs the cluster grid leaves free) while chunk c + 1 runs
-            const int buf = chunk_index % 2;
-            void* tkb = static_cast<char*>(tk) + static_cast<size_t>(buf) * n_a * 2 * rs * chunk;
-            void* okb = static_cast<char*>(ok) + static_cast<size_t>(buf) * 8ull * S * g.L3 * rs * chunk;
-            if (fields && chunk_index >= 2) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
-            ul::SlabArgs a{};
-            a.u = persist_args(h, count, sm, so, slab_t).u;
-            a.n_units = count;
-            a.n_metro = sm;
-            a.n_or = so;
-            a.cluster = slab_cl;
-            a.nz = g.L / slab_cl;
-            a.r_max = r_max;
-            a.fields = fields ? 1 : 0;
-            a.slot0 = 0;
-            a.asum = asum;
-            a.tk = tkb;
-            a.ok = okb;
-            a.osum = osum;
-            cudaError_t e = is_f64(h)
-                ? ul::launch_slab<double>(g, static_cast<double*>(h->theta), h->cs, a, slab_threads, h->stream)
-                : ul::launch_slab<float>(g, static_cast<float*>(h->theta), h->cs, a, slab_threads, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "slab-resident launch");
-            h->launches += 1;
-            if (fields) {
-                UL_CK(h, cudaEventRecord(h->ev_slab[buf], h->stream));
-                UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_slab[buf], 0));
-                e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream)
-                              : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream);
-                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
-                UL_CK(h, cudaEventRecord(h->ev_contract[buf], h->aux_stream));
-                h->launches += 1;
-            }
-            account_passes(h, sm * count, slab_t);
-            k += count;
-            ++chunk_index;
-            if (k >= n_sub && fields) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
-            continue;
-        }
-        const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
-                                            bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
-                                            reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
-                                            reinterpret_cast<long long>(tk), reinterpret_cast<long long>(ok),
-                                            reinterpret_cast<long long>(osum), reinterpret_cast<long long>(ubar)};
-        if (h->use_persistent) {
-            ul::PersistArgs a = persist_args(h, count, sm, so, slab_t);
-            a.measure = 1;
-            a.r_max = r_max;
-            a.fields = fields ? 1 : 0;
-            a.slot0 = 0;
-            a.asum = asum;
-            a.tk = tk;
-            a.ok = ok;
-            a.osum = osum;
-            a.ubar = ubar;
-            rc = launch_persistent(h, a);
-            if (rc) return rc;
-            if (fields) {
-                cudaError_t e = is_f64(h)
-                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream)
-                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream);
-                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
-                h->launches += 1;
-            }
-            account_passes(h, sm * count, slab_t);
-            k += count;
-            continue;
-        }
-        rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* base) -> long {
-            long n = 0;
-            for (int j = 0; j < count; ++j) {
-                const long m = enqueue_passes(h, st, sm, so, slab_t, first + static_cast<uint64_t>(j) * sm, base);
-                if (m < 0) return m;
-                n += m;
-                cudaError_t e;
-                if (ubar) {
-                    e = is_f64(h) ? ul::launch_multihit<double>(g, h->cs, h->beta, ubar, st)
-                                  : ul::launch_multihit<float>(g, h->cs, h->beta, ubar, st);
-                    if (e != cudaSuccess) return cuda_fail(h, e, "multihit launch");
-                    ++n;
-                }
-                e = is_f64(h)
-                    ? ul::launch_measure_store<double>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st)
-                    : ul::launch_measure_store<float>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st);
-                if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
-                ++n;
-            }
-            if (fields) {
-                cudaError_t e = is_f64(h)
-                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, st)
-                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, st);
-                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
-                ++n;
-            }
-            return n;
-        });
-        if (rc) return rc;
-        account_passes(h, sm * count, slab_t);
-        k += count;
-    }
+    rc = run_level(h, slab_t, n_sub, r_max, nd, fields, LevelBufs{asum, bsum, osum, tk, ok, ubar, chunk});
+    if (rc) return rc;
     cudaError_t e = ul::launch_ml_reduce(g, slab_t, n_sub, r_max, nd, asum, bsum, fields ? osum : nullptr, partials,
                                          dout, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
@@ -860,6 +897,97 @@ int ul_multilevel2(ul_lattice* h, int tau1, int n1, int tau2, int n2, int r_max,
     rc = check_device_status(h);
     if (rc) return rc;
     std::memcpy(out, host, 2ull * r_max * sizeof(double));
+    return UL_OK;
+}
+
+int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int r_max, int d_max,
+                          double* out_corr, double* out_fields, double* out_vac)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_multilevel2_fields: NULL handle");
+    const ul::Geo& g = h->g;
+    if (tau1 < 1 || tau2 < 1 || g.Nt % tau1 != 0 || tau1 % tau2 != 0)
+        return fail(h, UL_EINVAL, "ul_multilevel2_fields: tau2 must divide tau1 and tau1 must divide Nt");
+    if (tau1 / tau2 > 16) return fail(h, UL_EINVAL, "ul_multilevel2_fields: tau1 / tau2 must not exceed 16");
+    if (g.Nt / tau2 > ul::kMaxSlabs) return fail(h, UL_EINVAL, "ul_multilevel2_fields: more than 256 level-2 slabs");
+    if (n1 < 1 || n2 < 1) return fail(h, UL_EINVAL, "ul_multilevel2_fields: n1 and n2 must be >= 1");
+    if (r_max < 1 || r_max > g.L / 2) return fail(h, UL_EINVAL, "ul_multilevel2_fields: r_max must be in [1, L/2]");
+    if (d_max < 0 || d_max >= g.L) return fail(h, UL_EINVAL, "ul_multilevel2_fields: d_max must be in [0, L)");
+    if (!out_corr || !out_fields) return fail(h, UL_EINVAL, "ul_multilevel2_fields: output pointer is NULL");
+    if (h->multihit) return fail(h, UL_EINVAL, "ul_multilevel2_fields: not available with the multihit option");
+    const int S1 = g.Nt / tau1, S2 = g.Nt / tau2, nd = d_max + 1;
+
+    // Scratch: asum1 | bsum1 | asum2 | bsum2 | osum (level-2 layout) | tk | ok | partials | out
+    const size_t rs = real_size(h);
+    const size_t n_a1 = static_cast<size_t>(S1) * r_max * g.L3, n_a2 = static_cast<size_t>(S2) * r_max * g.L3;
+    const size_t n_b1 = n_a1 * nd * 8, n_b2 = n_a2 * nd * 8;
+    const size_t n_o = 8ull * S2 * g.L3;
+    const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
+    const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
+    const size_t per_sample = (n_a2 * 2 + 8ull * S2 * g.L3) * rs;
+    const int chunk = chunk_samples(h, n2, per_sample);
+    auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+    const size_t off_b1 = al(n_a1 * sizeof(double2));
+    const size_t off_a2 = off_b1 + al(n_b1 * sizeof(double2));
+    const size_t off_b2 = off_a2 + al(n_a2 * sizeof(double2));
+    const size_t off_o = off_b2 + al(n_b2 * sizeof(double2));
+    const size_t off_t = off_o + al(n_o * sizeof(double));
+    const size_t off_k = off_t + al(n_a2 * 2 * rs * chunk * 2);
+    const size_t off_p = off_k + al(8ull * S2 * g.L3 * rs * chunk * 2);
+    const size_t off_out = off_p + al(n_p * sizeof(double));
+    int rc = ensure_ml(h, off_out + al(n_out * sizeof(double)));
+    if (rc) return rc;
+    char* base = static_cast<char*>(h->ml_buf);
+    double2* asum1 = reinterpret_cast<double2*>(base);
+    double2* bsum1 = reinterpret_cast<double2*>(base + off_b1);
+    double2* asum2 = reinterpret_cast<double2*>(base + off_a2);
+    double2* bsum2 = reinterpret_cast<double2*>(base + off_b2);
+    double* osum = reinterpret_cast<double*>(base + off_o);
+    void* tk = base + off_t;
+    void* ok = base + off_k;
+    double* partials = reinterpret_cast<double*>(base + off_p);
+    double* dout = reinterpret_cast<double*>(base + off_out);
+    UL_CK(h, cudaMemsetAsync(asum1, 0, n_a1 * sizeof(double2), h->stream));
+    UL_CK(h, cudaMemsetAsync(bsum1, 0, n_b1 * sizeof(double2), h->stream));
+    UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
+    const int sm = h->sub_metro, so = h->sub_or;
+    const long long kb = bits_of(h->beta), kw = bits_of(h->width), ks = static_cast<long long>(h->seed);
+
+    for (int k1 = 0; k1 < n1; ++k1) {
+        // level-1 update: passes with the spatial links on t = 0 mod tau1 frozen
+        if (h->use_persistent) {
+            rc = launch_persistent(h, persist_args(h, 1, sm, so, tau1));
+        } else {
+            const std::vector<long long> key = {kGraphLevel2, 1, tau1, sm, so, kb, kw, ks};
+            rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* pb) {
+                return enqueue_passes(h, st, sm, so, tau1, first, pb);
+            });
+        }
+        if (rc) return rc;
+        account_passes(h, sm, tau1);
+        // level 2: n2 sub-samples with t = 0 mod tau2 frozen, measured into fresh accumulators
+        UL_CK(h, cudaMemsetAsync(asum2, 0, n_a2 * sizeof(double2), h->stream));
+        UL_CK(h, cudaMemsetAsync(bsum2, 0, n_b2 * sizeof(double2), h->stream));
+        rc = run_level(h, tau2, n2, r_max, nd, true, LevelBufs{asum2, bsum2, osum, tk, ok, nullptr, chunk});
+        if (rc) return rc;
+        cudaError_t e = ul::launch_fold_level2_fields(g, tau1, tau2, r_max, nd, n2, asum2, bsum2, asum1, bsum1,
+                                                      h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "level-2 fold launch");
+        h->launches += 1;
+    }
+    cudaError_t e = ul::launch_ml_reduce(g, tau1, n1, r_max, nd, asum1, bsum1, nullptr, partials, dout, h->stream);
+    if (e == cudaSuccess)
+        e = ul::launch_ml_vacuum(S2 * g.L3, osum, 8, static_cast<double>(n1) * n2 * static_cast<double>(g.V),
+                                 dout + 2 * r_max + 2 * r_max * nd * 8, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
+    h->launches += 3;
+    std::vector<double> host(n_out);
+    UL_CK(h, cudaMemcpyAsync(host.data(), dout, n_out * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    UL_CK(h, cudaStreamSynchronize(h->stream));
+    rc = check_device_status(h);
+    if (rc) return rc;
+    std::memcpy(out_corr, host.data(), 2ull * r_max * sizeof(double));
+    std::memcpy(out_fields, host.data() + 2 * r_max, 2ull * r_max * nd * 8 * sizeof(double));
+    if (out_vac) std::memcpy(out_vac, host.data() + 2 * r_max + 2 * r_max * nd * 8, 8 * sizeof(double));
     return UL_OK;
 }
 

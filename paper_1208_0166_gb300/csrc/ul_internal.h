@@ -92,6 +92,12 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
 cudaError_t launch_fold_level2(const Geo& g, int tau1, int tau2, int r_max, int n2, const double2* asum2,
                                double2* asum1, cudaStream_t st);
 
+// Two-level multilevel with insertions: add the level-1 samples of the level-2 accumulators
+// (asum2, bsum2 over n2 samples) to asum1, bsum1 (tau1 / tau2 <= 16).
+cudaError_t launch_fold_level2_fields(const Geo& g, int tau1, int tau2, int r_max, int nd, int n2,
+                                      const double2* asum2, const double2* bsum2, double2* asum1, double2* bsum1,
+                                      cudaStream_t st);
+
 // Persistent cooperative sweep kernel (256 threads per block; `threads` is ignored).
 template <typename R>
 cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st);

@@ -142,7 +142,67 @@ __global__ void __launch_bounds__(kT) fold_level2_kernel(int L3, int S1, int m, 
     asum1[k] = a;
 }
 
+// Two-level multilevel with insertions: one level-1 sample per (level-1 slab s1, r, x0) from
+// the level-2 means of the m level-2 slabs j inside s1,
+//   asum1 += prod_j A2(j),   bsum1[d, ch] += sum_j B2(j, d, ch) prod_{j' != j} A2(j'),
+// with A2 = asum2 / n2 and B2 = bsum2 / n2 (products in j order, sums in j order).
+constexpr int kMaxFoldM = 16;
+
+__global__ void __launch_bounds__(kT) fold_level2_fields_kernel(int L3, int S1, int m, int r_max, int nd, int n2,
+                                                                const double2* __restrict__ asum2,
+                                                                const double2* __restrict__ bsum2,
+                                                                double2* __restrict__ asum1,
+                                                                double2* __restrict__ bsum1)
+{
+    const long k = static_cast<long>(blockIdx.x) * kT + threadIdx.x;
+    const long total = static_cast<long>(S1) * r_max * L3;
+    if (k >= total) return;
+    const int x0 = static_cast<int>(k % L3);
+    const long sr = k / L3;
+    const int r = static_cast<int>(sr % r_max);
+    const int s1 = static_cast<int>(sr / r_max);
+    const double n = 1.0 / static_cast<double>(n2);
+    Cx<double> A[kMaxFoldM];
+    Cx<double> prod{1.0, 0.0};
+    for (int j = 0; j < m; ++j) {
+        A[j] = mean_of(asum2[(static_cast<long>(s1 * m + j) * r_max + r) * L3 + x0], n);
+        prod = cmul(prod, A[j]);
+    }
+    double2 a = asum1[k];
+    a.x += prod.re;
+    a.y += prod.im;
+    asum1[k] = a;
+    for (int d = 0; d < nd; ++d)
+        for (int ch = 0; ch < 8; ++ch) {
+            Cx<double> b{0.0, 0.0};
+            for (int j = 0; j < m; ++j) {
+                const long i2 = ((static_cast<long>(s1 * m + j) * r_max + r) * nd + d) * 8 + ch;
+                Cx<double> term = mean_of(bsum2[i2 * L3 + x0], n);
+                for (int j2 = 0; j2 < m; ++j2)
+                    if (j2 != j) term = cmul(term, A[j2]);
+                b = cadd(b, term);
+            }
+            const long i1 = ((static_cast<long>(s1) * r_max + r) * nd + d) * 8 + ch;
+            double2 v = bsum1[i1 * L3 + x0];
+            v.x += b.re;
+            v.y += b.im;
+            bsum1[i1 * L3 + x0] = v;
+        }
+}
+
 } // namespace
+
+cudaError_t launch_fold_level2_fields(const Geo& g, int tau1, int tau2, int r_max, int nd, int n2,
+                                      const double2* asum2, const double2* bsum2, double2* asum1, double2* bsum1,
+                                      cudaStream_t st)
+{
+    const int S1 = g.Nt / tau1, m = tau1 / tau2;
+    if (m > kMaxFoldM) return cudaErrorInvalidValue;
+    const long total = static_cast<long>(S1) * r_max * g.L3;
+    fold_level2_fields_kernel<<<static_cast<int>((total + kT - 1) / kT), kT, 0, st>>>(g.L3, S1, m, r_max, nd, n2,
+                                                                                      asum2, bsum2, asum1, bsum1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st)
 {
