@@ -43,6 +43,10 @@ UPDATES_PER_PASS_SUB = 4 * V - 3 * L3 * S      # spatial links on slab boundarie
 SWEEP_UPDATES = W.therm_sweeps * (W.sweep_metro + W.sweep_or) * UPDATES_PER_PASS_FULL
 SUB_UPDATES = W.n_sub * (W.sweep_metro + W.sweep_or) * UPDATES_PER_PASS_SUB
 UPDATES_PER_STEP = SWEEP_UPDATES + SUB_UPDATES
+# two-level estimator: TWO_LEVEL_N1 level-1 iterations; their level-1 updates (spatial links
+# on t = 0 mod 2 SLAB_T frozen) come on top of the level-2 sub-samples
+TWO_LEVEL_N1 = 5
+LEVEL1_UPDATES = TWO_LEVEL_N1 * (W.sweep_metro + W.sweep_or) * (4 * V - 3 * L3 * (W.Nt // (2 * SLAB_T)))
 SAMPLES_PER_STEP = W.n_sub * S * L3 * W.r_max              # T(s, x0, r) accumulations
 INSERTION_SAMPLES_PER_STEP = SAMPLES_PER_STEP * (W.d_max + 1) * 8
 H2D_BYTES = 4 * V * 8                                       # canonical FP64 link angles
@@ -162,6 +166,11 @@ def _measure(lat, args):
     """One multilevel level with insertions: the paper's frame, or all 24 frames."""
     if args.estimator == "sym":
         return lat.multilevel_fields_sym(SLAB_T, W.n_sub, W.r_max, W.d_max)
+    if args.estimator == "two-level":
+        # the paper's two-level scheme at the same number of level-2 sub-samples as the
+        # one-level step: level-1 slabs of 4 slices (pairs of the level-2 slabs of 2),
+        # TWO_LEVEL_N1 level-1 iterations of W.n_sub / TWO_LEVEL_N1 level-2 sub-samples
+        return lat.multilevel2_fields(2 * SLAB_T, TWO_LEVEL_N1, SLAB_T, W.n_sub // TWO_LEVEL_N1, W.r_max, W.d_max)
     return lat.multilevel_fields(SLAB_T, W.n_sub, W.r_max, W.d_max)
 
 
@@ -212,6 +221,10 @@ def _config(args):
     extra = {"options": _options(args)} if args.option else {}
     if args.estimator == "sym":
         extra["estimator"] = "symmetrised over the 24 frames of the source pair (ul_multilevel_fields_sym)"
+    if args.estimator == "two-level":
+        extra["estimator"] = ("two-level with insertions (ul_multilevel2_fields): level-1 slabs of %d slices, "
+                              "%d level-1 iterations of %d level-2 sub-samples (slabs of %d)"
+                              % (2 * SLAB_T, TWO_LEVEL_N1, W.n_sub // TWO_LEVEL_N1, SLAB_T))
     return {**extra, "workload": W.name + f" beta={W.beta} 100 sweeps (1 Metropolis + 3 OR) per configuration",
             "lattice": f"{W.L}^3x{W.Nt}", "beta": W.beta, "slab_t": SLAB_T, "slabs": S, "n_sub": W.n_sub,
             "sweeps_per_config": W.therm_sweeps, "r_max": W.r_max, "d_max": W.d_max,
@@ -476,6 +489,10 @@ def profile_step(args):
     return 0
 
 
+def updates_per_step(args):
+    return UPDATES_PER_STEP + (LEVEL1_UPDATES if args.estimator == "two-level" else 0)
+
+
 def run_ours(args):
     ws, rank, local = _dist()
     import torch
@@ -505,7 +522,8 @@ def run_ours(args):
     def gmax(x):
         return aggregate(x, 0.0, dist, "cuda")[0]
 
-    total_s, total_updates = aggregate(main["total_ms"] / 1e3, UPDATES_PER_STEP * K, dist, "cuda")
+    ups = updates_per_step(args)
+    total_s, total_updates = aggregate(main["total_ms"] / 1e3, ups * K, dist, "cuda")
     e2e_s = gmax(main["e2e_s"])
     value = total_updates / total_s
     samples = SAMPLES_PER_STEP * K * ws / total_s
@@ -516,7 +534,7 @@ def run_ours(args):
         o = _run_gpu(args, other, K, Wm, rank, ws, dist, torch, lib, e2e=False)
         o_s = gmax(o["total_ms"]) / 1e3
         compare = {"precision": "fp32_acc64" if other == lib.UL_FP32_ACC64 else "fp64",
-                   "value": UPDATES_PER_STEP * K * ws / o_s, "unit": UNIT,
+                   "value": ups * K * ws / o_s, "unit": UNIT,
                    "sweep_ms_per_step": o["sweep_ms"] / K, "multilevel_ms_per_step": o["ml_ms"] / K,
                    "correlator_samples_per_s": SAMPLES_PER_STEP * K * ws / o_s,
                    "ms_per_step": o_s / K * 1e3, "gpu_launches": o["launches"],
@@ -551,9 +569,9 @@ def run_ours(args):
             "data": "synthetic", "config": _config(args),
             "correlator_samples_per_s": samples,
             "phases_ms_per_step": {"sweeps": main["sweep_ms"] / K, "multilevel": main["ml_ms"] / K}, "insertion_samples_per_s": INSERTION_SAMPLES_PER_STEP * K * ws / total_s,
-            "link_updates_per_step": UPDATES_PER_STEP, "compare": compare,
+            "link_updates_per_step": ups, "compare": compare,
             "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": UPDATES_PER_STEP * K * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H2D_BYTES,
+            "e2e": {"value": ups * K * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H2D_BYTES,
                     "d2h_bytes_per_step": D2H_BYTES},
             "gpu_launches": main["launches"], "clocks": clk,
             "observables": {"C_r": [[z.real, z.imag] for z in main["corr"][:4]], "plaquette": main["plaquette"]}}
@@ -577,8 +595,9 @@ def main():
                          "serve: Poisson stream through the continuous-batching loop")
     ap.add_argument("--serve-jobs", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--estimator", default="paper", choices=["paper", "sym"],
-                    help="paper: insertions in the paper's frame; sym: averaged over the 24 frames")
+    ap.add_argument("--estimator", default="paper", choices=["paper", "sym", "two-level"],
+                    help="paper: one level, insertions in the paper's frame; sym: averaged over the 24 "
+                         "frames; two-level: the two-level scheme with insertions")
     ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
                     help="library run option set on the lattice (ul_set_option), e.g. slab_resident=1")
     ap.add_argument("--profile-step", action="store_true",
