@@ -204,6 +204,30 @@ def test_full_size_24_sampled():
         assert abs(f["fields"][r - 1, d, ch] - c.field_correlator_one(r, d, ch)) < OBS_TOL
 
 
+def test_fp32_full_size_frozen_configuration():
+    """24^4 in the FP32 benchmark's launch form (slab-resident sub-samples, four chunks with
+    the contraction on a second stream) on a frozen configuration: within FP32 rounding of
+    the FP64 path, which equals the oracle (the bench reports these differences)."""
+    L = 24
+    g64 = _lib.Lattice(L, L, 1.0, 5, _lib.UL_FP64)
+    g64.sweep(1, 3)
+    th = g64.get_links()
+    g32 = _lib.Lattice(L, L, 1.0, 5, _lib.UL_FP32_ACC64)
+    g32.set_links(th)
+    res = []
+    for g in (g64, g32):
+        g.set_option("sub_metro", 0)
+        g.set_option("sub_or", 0)
+        n0 = g.launch_count()
+        res.append(g.multilevel_fields(2, 8, 8, 6))
+        res[-1]["launches"] = g.launch_count() - n0
+    assert res[1]["launches"] <= 2 * 4 + 3  # slab-resident: one slab launch and one contraction per chunk
+    for key in ("corr", "fields", "vac"):
+        err = np.max(np.abs(res[0][key] - res[1][key]))
+        print(f"24^4 FP32 vs FP64 {key}: {err:.2e}")
+        assert err < 2e-6, key
+
+
 def _binned(x, nb=10):
     x = np.asarray(x)
     n = len(x) // nb * nb
