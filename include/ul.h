@@ -44,8 +44,8 @@ enum {
 
 enum {
     UL_FP64 = 0,      /* link angles, updates and accumulation in FP64 */
-    UL_FP32_ACC64 = 1 /* link angles and updates in FP32; measurement products,
-                         slab accumulators, cross-slab products and reductions in FP64 */
+    UL_FP32_ACC64 = 1 /* link angles, updates and per-sample measurement products in
+                         FP32; slab accumulators, cross-slab products and reductions in FP64 */
 };
 
 /*
@@ -68,7 +68,8 @@ int ul_init_ex(ul_lattice** h, int L, int Nt, double beta, uint64_t seed, int pr
  *   Metropolis: theta' = wrap(theta + w (2 u1 - 1)), w = option "metro_width" (1.0);
  *     accept iff u2 < exp(-dS), dS = -beta Re[(e^{i theta'} - e^{i theta}) A], with A the
  *     staple sum of the link; u1, u2 from words 0, 1 of Philox4x64-10(counter =
- *     (mu V + i, pass, 0, 0), key = (seed, 1)), pass = number of earlier Metropolis passes.
+ *     (mu V + i, pass, 0, 0), key = (seed, 1)) (UL_FP32_ACC64: Philox4x32-10, see
+ *     ul_rng_uniforms), pass = number of earlier Metropolis passes.
  *   Overrelaxation: theta' = wrap(-2 arg(A) - theta) (leaves Re(e^{i theta} A) unchanged).
  * n_metro, n_or >= 0.  Returns once the passes are enqueued on the handle's stream.
  */
@@ -232,7 +233,8 @@ int ul_free(ul_lattice* h);
  *   "graphs"       1 (default): recurring launch sequences (a compound sweep, a chunk of
  *                  sub-samples) are captured once into CUDA graphs and replayed; 0: every
  *                  kernel is launched directly.  Results are identical either way.
- *   "slab_resident"  1: ul_multilevel / ul_multilevel_fields run each chunk of sub-samples
+ *   "slab_resident"  1: ul_multilevel, ul_multilevel_fields and the level-2 sub-samples of
+ *                  ul_multilevel2_fields run each chunk of sub-samples
  *                  as one launch in which a thread-block cluster owns one time slab: its
  *                  links are held in the shared memory of the cluster's CTAs (Section 2.2:
  *                  with the slab boundaries frozen a slab's updates read only its own links)
@@ -243,9 +245,12 @@ int ul_free(ul_lattice* h);
  *   "slab_cluster" CTAs per slab in the slab-resident form (a divisor of L, at most 16;
  *                  0, the default: the most CTAs up to 8 that keep every slab resident).
  *                  A size whose slab share does not fit falls back to one launch per class.
- *   "insertion_chunk_mb"  bound (MiB, default 4096) on the buffers that hold the per-sample
- *                  transporters and channel sums between insertion contractions; fewer
- *                  MiB means more, smaller contractions (results change only by rounding)
+ *   "insertion_chunk_mb"  bound (MiB, default 4096) on the two buffers that hold the
+ *                  per-sample transporters and channel sums between insertion contractions
+ *                  (a level is contracted in chunks of a quarter of its sub-samples, smaller
+ *                  where the bound requires; in the slab-resident form one chunk's
+ *                  contraction overlaps the next chunk's updates); fewer MiB means more,
+ *                  smaller contractions (results change only by rounding)
  */
 int ul_set_option(ul_lattice* h, const char* key, double value);
 
