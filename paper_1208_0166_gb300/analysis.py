@@ -55,14 +55,20 @@ def fit_flux_profile(x, O, dO, p0=(1.0, 2.0, 0.0, 0.0)):
                      sigma=np.asarray(dO, float), absolute_sigma=True, maxfev=20000)
 
 
-def width2(params, rho_max: float = 60.0) -> float:
-    """Squared width of a fitted profile f(rho) in the transverse plane:
-    w^2 = int d^2x x^2 f / int d^2x f = int rho^3 f drho / int rho f drho
-    (the normalised second moment; the printed denominator of the width formula is garbled)."""
+def width2(params, rho_max: float = 60.0, dim: int = 1) -> float:
+    """Squared width of a fitted profile f (Section 1.1's definition, its denominator read as
+    the integral of the profile):
+      dim = 1: w^2 = int dx x^2 f(x) / int dx f(x) over one transverse coordinate x, the
+               literal form of the printed formula (a single transverse integral; the
+               profile is measured along one transverse axis);
+      dim = 2: w^2 = int d^2x |x|^2 f / int d^2x f = int rho^3 f drho / int rho f drho for a
+               profile that depends on the transverse radius rho only."""
     from scipy.integrate import quad
 
-    num = quad(lambda p: p ** 3 * flux_ansatz(p, *params), 0.0, rho_max, epsabs=1e-13, epsrel=1e-12, limit=200)[0]
-    den = quad(lambda p: p * flux_ansatz(p, *params), 0.0, rho_max, epsabs=1e-13, epsrel=1e-12, limit=200)[0]
+    k = 2 if dim == 1 else 3
+    num = quad(lambda p: p ** k * flux_ansatz(p, *params), 0.0, rho_max, epsabs=1e-13, epsrel=1e-12, limit=200)[0]
+    den = quad(lambda p: p ** (k - 2) * flux_ansatz(p, *params), 0.0, rho_max, epsabs=1e-13, epsrel=1e-12,
+               limit=200)[0]
     return float(num / den)
 
 

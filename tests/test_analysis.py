@@ -22,9 +22,11 @@ def test_potential_fit_recovers_string_model_parameters():
 
 
 def test_width_of_a_gaussian_profile_is_its_scale():
-    """For f = A exp(-rho^2/s): int rho^3 f / int rho f = s."""
+    """For f = A exp(-x^2/s): along one transverse axis int x^2 f / int f = s/2; over the
+    transverse plane int rho^3 f / int rho f = s."""
     for s in (0.7, 2.0, 5.0):
-        assert abs(an.width2((1.3, s, 0.0, 0.0)) - s) < 1e-6
+        assert abs(an.width2((1.3, s, 0.0, 0.0)) - s / 2) < 1e-6
+        assert abs(an.width2((1.3, s, 0.0, 0.0), dim=2) - s) < 1e-6
 
 
 def test_flux_profile_fit_recovers_ansatz_parameters():
