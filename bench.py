@@ -221,6 +221,9 @@ def _config(args):
     extra = {"options": _options(args)} if args.option else {}
     if args.estimator == "sym":
         extra["estimator"] = "symmetrised over the 24 frames of the source pair (ul_multilevel_fields_sym)"
+    if args.pipeline and args.estimator == "paper":
+        extra["pipeline"] = ("each level collected (ul_multilevel_fields_end) after the next configuration's "
+                             "sweeps are queued; timed as one interval over the K steps, L2 flushes included")
     if args.estimator == "two-level":
         extra["estimator"] = ("two-level with insertions (ul_multilevel2_fields): level-1 slabs of %d slices, "
                               "%d level-1 iterations of %d level-2 sub-samples (slabs of %d)"
@@ -310,8 +313,29 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
         e3 = ev()
         return (e0, e1, e2, e3), res, plaq
 
-    for _ in range(Wm):
-        step()
+    pipelined = args.pipeline and args.estimator == "paper"
+
+    def step_pipelined(first):
+        # configuration k's sweeps are queued before the host collects level k - 1, whose
+        # last contraction, reduction and result copy run on the library's second stream
+        e0 = ev()
+        for _ in range(W.therm_sweeps):
+            lat.sweep(W.sweep_metro, W.sweep_or)
+        e1 = ev()
+        prev = None if first else lat.multilevel_fields_end()
+        lat.multilevel_fields_begin(SLAB_T, W.n_sub, W.r_max, W.d_max)
+        e2 = ev()
+        plaq = lat.plaquette()
+        e3 = ev()
+        return (e0, e1, e2, e3), prev, plaq
+
+    if pipelined:
+        for i in range(Wm):
+            step_pipelined(i == 0)
+        lat.multilevel_fields_end()
+    else:
+        for _ in range(Wm):
+            step()
     stream.synchronize()
     if dist:
         dist.barrier()
@@ -319,17 +343,38 @@ def _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib, e2e=True):
     launches0 = lat.launch_count()
     total_ms, sweep_ms, ml_ms, step_ms = 0.0, 0.0, 0.0, []
     last = None
-    for _ in range(K):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        (e0, e1, e2, e3), res, plaq = step()
+    if pipelined:
+        # one interval from before the first step to the collection of the last level (the
+        # K L2 flushes between the steps included, so the step time is an upper bound)
+        start = ev()
+        marks = []
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            (e0, e1, e2, e3), prev, plaq = step_pipelined(k == 0)
+            marks.append((e0, e1, e2))
+            last = (prev, plaq)
+        res = lat.multilevel_fields_end()
+        stop = ev()
         stream.synchronize()
-        ms = e0.elapsed_time(e3)
-        total_ms += ms
-        sweep_ms += e0.elapsed_time(e1)
-        ml_ms += e1.elapsed_time(e2)
-        step_ms.append(ms)
-        last = (res, plaq)
+        total_ms = start.elapsed_time(stop)
+        for e0, e1, e2 in marks:
+            sweep_ms += e0.elapsed_time(e1)
+            ml_ms += e1.elapsed_time(e2)
+        step_ms = [total_ms / K] * K
+        last = (res, last[1])
+    else:
+        for _ in range(K):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            (e0, e1, e2, e3), res, plaq = step()
+            stream.synchronize()
+            ms = e0.elapsed_time(e3)
+            total_ms += ms
+            sweep_ms += e0.elapsed_time(e1)
+            ml_ms += e1.elapsed_time(e2)
+            step_ms.append(ms)
+            last = (res, plaq)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -590,6 +635,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pipeline", type=int, default=0, choices=[0, 1],
+                    help="1: collect each configuration's level after queueing the next one's sweeps "
+                         "(ul_multilevel_fields_begin/_end; one-level estimator only)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: the 24^4 configuration step (default); batch: 32 uneven lattices; "
                          "serve: Poisson stream through the continuous-batching loop")

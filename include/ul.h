@@ -111,6 +111,25 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
                          double* out_corr, double* out_fields, double* out_vac);
 
 /*
+ * ul_multilevel_fields_begin / ul_multilevel_fields_end — ul_multilevel_fields in two
+ * halves, so that the host can queue the next configuration's sweeps while the level's
+ * final reduction and result copy are still running.  _begin validates the arguments (as
+ * ul_multilevel_fields; d_max < 0 means no insertions, the correlator of ul_multilevel),
+ * enqueues the level's sub-samples on the handle's stream, then the reduction and the copy
+ * of its results into library-owned pinned host memory on the handle's second stream, and
+ * returns without waiting.  _end waits for that copy and writes out_corr (2*r_max doubles),
+ * and, when the level was begun with d_max >= 0, out_fields (may be NULL) and out_vac (may
+ * be NULL) in the layouts of ul_multilevel_fields.  Between the two calls the handle takes
+ * any call except a second _begin or ul_multilevel_fields (UL_ESTATE); calls that use the
+ * level scratch (the other estimators) wait on the device for the pending reduction.
+ * Results are those of ul_multilevel_fields bit for bit.  _end without a _begin:
+ * UL_ESTATE.  A grid-barrier timeout of a persistent sweep inside the level is reported by
+ * _end (UL_ETIMEOUT).  ul_free with a level pending waits for it and drops its results.
+ */
+int ul_multilevel_fields_begin(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max);
+int ul_multilevel_fields_end(ul_lattice* h, double* out_corr, double* out_fields, double* out_vac);
+
+/*
  * ul_multilevel2_fields — the two-level estimator with field insertions: the paper's
  * field estimator (Section 2.2) with its bracketed factors read as level-1 averages.
  * n1 times: "sub_metro" + "sub_or" passes with the spatial links on t = 0 mod tau1 frozen,

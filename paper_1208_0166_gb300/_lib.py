@@ -45,6 +45,8 @@ SIGNATURES = [
     ("ul_multilevel", _I, [_P, _I, _I, _I, _DP]),
     ("ul_multilevel_fields", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
     ("ul_multilevel_fields_sym", _I, [_P, _I, _I, _I, _I, _DP, _DP, _DP]),
+    ("ul_multilevel_fields_begin", _I, [_P, _I, _I, _I, _I]),
+    ("ul_multilevel_fields_end", _I, [_P, _DP, _DP, _DP]),
     ("ul_rng_uniforms", _I, [_I, _U64, _U64, _U64, _I, _DP]),
     ("ul_multilevel2_fields", _I, [_P, _I, _I, _I, _I, _I, _I, _DP, _DP, _DP]),
     ("ul_multilevel2", _I, [_P, _I, _I, _I, _I, _I, _DP]),
@@ -157,6 +159,29 @@ class Lattice:
                                            _dp(fields), _dp(vac)), self._h)
         f = fields.reshape(r_max, d_max + 1, N_CHANNELS, 2)
         return {"corr": corr[0::2] + 1j * corr[1::2], "fields": f[..., 0] + 1j * f[..., 1], "vac": vac}
+
+    def multilevel_fields_begin(self, slab_t: int, n_sub: int, r_max: int, d_max: int) -> None:
+        """First half of multilevel_fields (ul_multilevel_fields_begin): queues the level and
+        returns; d_max < 0 queues the correlator alone."""
+        _check(load().ul_multilevel_fields_begin(self._h, int(slab_t), int(n_sub), int(r_max), int(d_max)), self._h)
+        self._pending = (int(r_max), int(d_max))
+
+    def multilevel_fields_end(self):
+        """Second half (ul_multilevel_fields_end): waits for the begun level; returns the dict
+        of multilevel_fields (without "fields" and "vac" for a correlator-only level)."""
+        r_max, d_max = getattr(self, "_pending", None) or (1, -1)
+        corr = np.zeros(2 * r_max)
+        nd = max(d_max + 1, 0)
+        fields = np.zeros(2 * r_max * nd * N_CHANNELS)
+        vac = np.zeros(N_CHANNELS)
+        _check(load().ul_multilevel_fields_end(self._h, _dp(corr), _dp(fields) if nd else None,
+                                               _dp(vac) if nd else None), self._h)
+        self._pending = None
+        out = {"corr": corr[0::2] + 1j * corr[1::2]}
+        if nd:
+            f = fields.reshape(r_max, nd, N_CHANNELS, 2)
+            out.update(fields=f[..., 0] + 1j * f[..., 1], vac=vac)
+        return out
 
     def multilevel2_fields(self, tau1: int, n1: int, tau2: int, n2: int, r_max: int, d_max: int):
         """Two-level estimator with field insertions (ul_multilevel2_fields)."""

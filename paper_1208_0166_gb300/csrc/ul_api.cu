@@ -65,6 +65,16 @@ struct ul_lattice {
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_slab[2] = {nullptr, nullptr};
     cudaEvent_t ev_contract[2] = {nullptr, nullptr};
+    // a level begun by ul_multilevel_fields_begin: its reduction and result copy run on
+    // aux_stream into the pinned staging buffer; ev_result marks their completion
+    bool pending = false;
+    int pend_r_max = 0, pend_nd = 0;
+    size_t pend_n_out = 0;
+    bool pend_fields = false;
+    double* pinned = nullptr;
+    size_t pinned_n = 0;
+    cudaEvent_t ev_main = nullptr;
+    cudaEvent_t ev_result = nullptr;
 
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
@@ -125,6 +135,9 @@ void release(ul_lattice* h)
         if (h->ev_contract[b]) cudaEventDestroy(h->ev_contract[b]);
     }
     if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+    if (h->ev_main) cudaEventDestroy(h->ev_main);
+    if (h->ev_result) cudaEventDestroy(h->ev_result);
+    if (h->pinned) cudaFreeHost(h->pinned);
     cudaFree(h->theta);
     cudaFree(h->cs);
     cudaFree(h->canon);
@@ -138,6 +151,9 @@ void release(ul_lattice* h)
 
 int ensure_ml(ul_lattice* h, size_t bytes)
 {
+    // work on the multilevel scratch waits for a begun level's reduction and result copy
+    // (a no-op when nothing was begun: the event has not been recorded)
+    UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_result, 0));
     if (bytes <= h->ml_bytes) return UL_OK;
     UL_CK(h, cudaStreamSynchronize(h->stream));
     drop_graphs(h, kGraphChunk); // they reference the old buffer
@@ -345,7 +361,8 @@ struct LevelBufs {
 // frozen, a measurement after each, and with fields the insertion contraction of each
 // chunk, added into the accumulators of b.  Slab-resident where the slab fits (and neither
 // multihit nor persistent mode is on), else persistent or per-class launches.
-int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fields, const LevelBufs& b)
+int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fields, const LevelBufs& b,
+              bool wait_contraction = true)
 {
     const ul::Geo& g = h->g;
     const int S = g.Nt / slab_t;
@@ -415,7 +432,8 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             account_passes(h, sm * count, slab_t);
             k += count;
             ++chunk_index;
-            if (k >= n_sub && fields) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
+            if (k >= n_sub && fields && wait_contraction)
+                UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
             continue;
         }
         const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
@@ -482,6 +500,112 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
     return UL_OK;
 }
 
+// First half of a level with insertions (everything enqueued; results collected by level_end).
+int level_begin(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max, bool fields)
+{
+    const ul::Geo& g = h->g;
+    if (h->pending)
+        return fail(h, UL_ESTATE, "ul_multilevel: the results of a begun level have not been collected "
+                                  "(ul_multilevel_fields_end)");
+    if (slab_t < 1 || g.Nt % slab_t != 0) return fail(h, UL_EINVAL, "ul_multilevel: slab_t must divide Nt");
+    if (g.Nt / slab_t > ul::kMaxSlabs) return fail(h, UL_EINVAL, "ul_multilevel: more than 256 slabs");
+    if (n_sub < 1) return fail(h, UL_EINVAL, "ul_multilevel: n_sub must be >= 1");
+    if (r_max < 1 || r_max > g.L / 2) return fail(h, UL_EINVAL, "ul_multilevel: r_max must be in [1, L/2]");
+    if (fields && (d_max < 0 || d_max >= g.L)) return fail(h, UL_EINVAL, "ul_multilevel: d_max must be in [0, L)");
+    const int nd = fields ? d_max + 1 : 0;
+    const int S = g.Nt / slab_t;
+
+    // Scratch (each region 256-byte aligned): asum | bsum | osum | tk | ok | partials | out.
+    // tk / ok hold the T and O of up to `chunk` sub-samples for the deferred insertion
+    // contraction; the chunk is bounded by the option "insertion_chunk_mb".
+    const size_t rs = real_size(h);
+    const size_t n_a = static_cast<size_t>(S) * r_max * g.L3;
+    const size_t n_b = n_a * nd * 8;
+    const size_t n_o = fields ? 8ull * S * g.L3 : 0;
+    const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
+    const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
+    const size_t per_sample = fields ? (n_a * 2 + 8ull * S * g.L3) * rs : 0;
+    const int chunk = fields ? chunk_samples(h, n_sub, per_sample) : 0;
+    auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+    const size_t off_b = al(n_a * sizeof(double2));
+    const size_t off_o = off_b + al(n_b * sizeof(double2));
+    const size_t off_t = off_o + al(n_o * sizeof(double));
+    const size_t off_k = off_t + al(fields ? n_a * 2 * rs * chunk * 2 : 0); // two chunk buffers
+    const size_t off_u = off_k + al(fields ? 8ull * S * g.L3 * rs * chunk * 2 : 0);
+    const size_t off_p = off_u + al(h->multihit ? static_cast<size_t>(g.V) * 2 * rs : 0);
+    const size_t off_out = off_p + al(n_p * sizeof(double));
+    const size_t bytes = off_out + al(n_out * sizeof(double));
+    int rc = ensure_ml(h, bytes);
+    if (rc) return rc;
+    char* base = static_cast<char*>(h->ml_buf);
+    double2* asum = reinterpret_cast<double2*>(base);
+    double2* bsum = reinterpret_cast<double2*>(base + off_b);
+    double* osum = reinterpret_cast<double*>(base + off_o);
+    void* tk = base + off_t;
+    void* ok = base + off_k;
+    void* ubar = h->multihit ? static_cast<void*>(base + off_u) : nullptr;
+    double* partials = reinterpret_cast<double*>(base + off_p);
+    double* dout = reinterpret_cast<double*>(base + off_out);
+    UL_CK(h, cudaMemsetAsync(asum, 0, n_a * sizeof(double2), h->stream));
+    if (fields) {
+        UL_CK(h, cudaMemsetAsync(bsum, 0, n_b * sizeof(double2), h->stream));
+        UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
+    }
+
+    rc = run_level(h, slab_t, n_sub, r_max, nd, fields, LevelBufs{asum, bsum, osum, tk, ok, ubar, chunk}, false);
+    if (rc) return rc;
+    // The reduction and the result copy run on the auxiliary stream after everything the
+    // level put on the handle's stream (and after the last contraction, already there), so
+    // the handle's stream is free for the next configuration's sweeps meanwhile.
+    UL_CK(h, cudaEventRecord(h->ev_main, h->stream));
+    UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_main, 0));
+    cudaError_t e = ul::launch_ml_reduce(g, slab_t, n_sub, r_max, nd, asum, bsum, fields ? osum : nullptr, partials,
+                                         dout, h->aux_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
+    h->launches += fields ? 3 : 2;
+    // pinned staging: the results, then the device status word as of the level's end
+    if (h->pinned_n < n_out + 1) {
+        if (h->pinned) cudaFreeHost(h->pinned);
+        h->pinned = nullptr;
+        h->pinned_n = 0;
+        UL_CK(h, cudaMallocHost(&h->pinned, (n_out + 1) * sizeof(double)));
+        h->pinned_n = n_out + 1;
+    }
+    UL_CK(h, cudaMemcpyAsync(h->pinned, dout, n_out * sizeof(double), cudaMemcpyDeviceToHost, h->aux_stream));
+    UL_CK(h, cudaMemcpyAsync(h->pinned + n_out, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->aux_stream));
+    UL_CK(h, cudaEventRecord(h->ev_result, h->aux_stream));
+    h->pend_n_out = n_out;
+    h->pending = true;
+    h->pend_r_max = r_max;
+    h->pend_nd = nd;
+    h->pend_fields = fields;
+    return UL_OK;
+}
+
+// Second half: wait for the level's reduction, then copy the results to the caller.
+int level_end(ul_lattice* h, double* out_corr, double* out_fields, double* out_vac)
+{
+    if (!h->pending) return fail(h, UL_ESTATE, "ul_multilevel_fields_end: no level was begun");
+    h->pending = false;
+    UL_CK(h, cudaEventSynchronize(h->ev_result));
+    UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_result, 0));
+    int st = 0;
+    std::memcpy(&st, h->pinned + h->pend_n_out, sizeof(int));
+    if (st) {
+        // a persistent sweep of the level gave up at a grid barrier: report it and clear the flag
+        const int rc = check_device_status(h);
+        if (rc) return rc;
+    }
+    const int r_max = h->pend_r_max, nd = h->pend_nd;
+    const double* host = h->pinned;
+    std::memcpy(out_corr, host, 2ull * r_max * sizeof(double));
+    if (h->pend_fields) {
+        if (out_fields) std::memcpy(out_fields, host + 2 * r_max, 2ull * r_max * nd * 8 * sizeof(double));
+        if (out_vac) std::memcpy(out_vac, host + 2 * r_max + 2 * r_max * nd * 8, 8 * sizeof(double));
+    }
+    return UL_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -542,6 +666,8 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
         return bail(e, "capture stream");
     if ((e = cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(e, "auxiliary stream");
+    if ((e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
+    if ((e = cudaEventCreateWithFlags(&h->ev_result, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
     for (int b = 0; b < 2; ++b) {
         if ((e = cudaEventCreateWithFlags(&h->ev_slab[b], cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
         if ((e = cudaEventCreateWithFlags(&h->ev_contract[b], cudaEventDisableTiming)) != cudaSuccess)
@@ -581,80 +707,23 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
                          double* out_fields, double* out_vac)
 {
     if (!h) return fail(nullptr, UL_EINVAL, "ul_multilevel: NULL handle");
-    const ul::Geo& g = h->g;
-    if (slab_t < 1 || g.Nt % slab_t != 0) return fail(h, UL_EINVAL, "ul_multilevel: slab_t must divide Nt");
-    if (g.Nt / slab_t > ul::kMaxSlabs) return fail(h, UL_EINVAL, "ul_multilevel: more than 256 slabs");
-    if (n_sub < 1) return fail(h, UL_EINVAL, "ul_multilevel: n_sub must be >= 1");
-    if (r_max < 1 || r_max > g.L / 2) return fail(h, UL_EINVAL, "ul_multilevel: r_max must be in [1, L/2]");
     if (!out_corr) return fail(h, UL_EINVAL, "ul_multilevel: output pointer is NULL");
-    const bool fields = out_fields != nullptr;
-    if (fields && (d_max < 0 || d_max >= g.L)) return fail(h, UL_EINVAL, "ul_multilevel: d_max must be in [0, L)");
-    const int nd = fields ? d_max + 1 : 0;
-    const int S = g.Nt / slab_t;
-
-    // Scratch (each region 256-byte aligned): asum | bsum | osum | tk | ok | partials | out.
-    // tk / ok hold the T and O of up to `chunk` sub-samples for the deferred insertion
-    // contraction; the chunk is bounded by the option "insertion_chunk_mb".
-    const size_t rs = real_size(h);
-    const size_t n_a = static_cast<size_t>(S) * r_max * g.L3;
-    const size_t n_b = n_a * nd * 8;
-    const size_t n_o = fields ? 8ull * S * g.L3 : 0;
-    const size_t n_p = ul::ml_partials_doubles(g, r_max, nd);
-    const size_t n_out = 2ull * r_max + 2ull * r_max * nd * 8 + 8;
-    const size_t per_sample = fields ? (n_a * 2 + 8ull * S * g.L3) * rs : 0;
-    const int chunk = fields ? chunk_samples(h, n_sub, per_sample) : 0;
-    auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
-    const size_t off_b = al(n_a * sizeof(double2));
-    const size_t off_o = off_b + al(n_b * sizeof(double2));
-    const size_t off_t = off_o + al(n_o * sizeof(double));
-    const size_t off_k = off_t + al(fields ? n_a * 2 * rs * chunk * 2 : 0); // two chunk buffers
-    const size_t off_u = off_k + al(fields ? 8ull * S * g.L3 * rs * chunk * 2 : 0);
-    const size_t off_p = off_u + al(h->multihit ? static_cast<size_t>(g.V) * 2 * rs : 0);
-    const size_t off_out = off_p + al(n_p * sizeof(double));
-    const size_t bytes = off_out + al(n_out * sizeof(double));
-    int rc = ensure_ml(h, bytes);
+    const int rc = level_begin(h, slab_t, n_sub, r_max, d_max, out_fields != nullptr);
     if (rc) return rc;
-    char* base = static_cast<char*>(h->ml_buf);
-    double2* asum = reinterpret_cast<double2*>(base);
-    double2* bsum = reinterpret_cast<double2*>(base + off_b);
-    double* osum = reinterpret_cast<double*>(base + off_o);
-    void* tk = base + off_t;
-    void* ok = base + off_k;
-    void* ubar = h->multihit ? static_cast<void*>(base + off_u) : nullptr;
-    double* partials = reinterpret_cast<double*>(base + off_p);
-    double* dout = reinterpret_cast<double*>(base + off_out);
-    UL_CK(h, cudaMemsetAsync(asum, 0, n_a * sizeof(double2), h->stream));
-    if (fields) {
-        UL_CK(h, cudaMemsetAsync(bsum, 0, n_b * sizeof(double2), h->stream));
-        UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
-    }
+    return level_end(h, out_corr, out_fields, out_vac);
+}
 
-    rc = run_level(h, slab_t, n_sub, r_max, nd, fields, LevelBufs{asum, bsum, osum, tk, ok, ubar, chunk});
-    if (rc) return rc;
-    cudaError_t e = ul::launch_ml_reduce(g, slab_t, n_sub, r_max, nd, asum, bsum, fields ? osum : nullptr, partials,
-                                         dout, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "reduction launch");
-    h->launches += fields ? 3 : 2;
-    double* host = static_cast<double*>(std::malloc(n_out * sizeof(double)));
-    if (!host) return fail(h, UL_ENOMEM, "ul_multilevel: host staging allocation failed");
-    e = cudaMemcpyAsync(host, dout, n_out * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-        std::free(host);
-        return cuda_fail(h, e, "ul_multilevel: result copy");
-    }
-    rc = check_device_status(h);
-    if (rc) {
-        std::free(host);
-        return rc;
-    }
-    std::memcpy(out_corr, host, 2ull * r_max * sizeof(double));
-    if (fields) {
-        std::memcpy(out_fields, host + 2 * r_max, 2ull * r_max * nd * 8 * sizeof(double));
-        if (out_vac) std::memcpy(out_vac, host + 2 * r_max + 2 * r_max * nd * 8, 8 * sizeof(double));
-    }
-    std::free(host);
-    return UL_OK;
+int ul_multilevel_fields_begin(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_multilevel_fields_begin: NULL handle");
+    return level_begin(h, slab_t, n_sub, r_max, d_max, d_max >= 0);
+}
+
+int ul_multilevel_fields_end(ul_lattice* h, double* out_corr, double* out_fields, double* out_vac)
+{
+    if (!h) return fail(nullptr, UL_EINVAL, "ul_multilevel_fields_end: NULL handle");
+    if (!out_corr) return fail(h, UL_EINVAL, "ul_multilevel_fields_end: output pointer is NULL");
+    return level_end(h, out_corr, out_fields, out_vac);
 }
 
 int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max, double* out_corr,
