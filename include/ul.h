@@ -120,8 +120,9 @@ int ul_multilevel_fields(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_
  * returns without waiting.  _end waits for that copy and writes out_corr (2*r_max doubles),
  * and, when the level was begun with d_max >= 0, out_fields (may be NULL) and out_vac (may
  * be NULL) in the layouts of ul_multilevel_fields.  Between the two calls the handle takes
- * any call except a second _begin or ul_multilevel_fields (UL_ESTATE); calls that use the
- * level scratch (the other estimators) wait on the device for the pending reduction.
+ * any call except a second _begin, ul_multilevel or ul_multilevel_fields (UL_ESTATE);
+ * calls that use the level scratch (the other estimators) wait on the device for the
+ * pending reduction.
  * Results are those of ul_multilevel_fields bit for bit.  _end without a _begin:
  * UL_ESTATE.  A grid-barrier timeout of a persistent sweep inside the level is reported by
  * _end (UL_ETIMEOUT).  ul_free with a level pending waits for it and drops its results.
@@ -270,6 +271,14 @@ int ul_free(ul_lattice* h);
  *                  where the bound requires; in the slab-resident form one chunk's
  *                  contraction overlaps the next chunk's updates); fewer MiB means more,
  *                  smaller contractions (results change only by rounding)
+ *   "contract_tiled"  1 (default): for UL_FP32_ACC64 the insertion contraction runs in a
+ *                  tiled form (per block one slab, one z-plane, a tile of y-rows, two
+ *                  separations and a set of offsets d; batches of 8 samples staged in shared
+ *                  memory by bulk copies, two blocks per SM); 0: one thread per output
+ *                  reading its operands from global memory.  Results are identical either
+ *                  way; UL_FP64 always uses the untiled form.  A staging-copy wait that
+ *                  reaches its time limit (about a second) is reported as UL_ETIMEOUT by the
+ *                  level's result call.
  */
 int ul_set_option(ul_lattice* h, const char* key, double value);
 

@@ -56,6 +56,7 @@ struct ul_lattice {
     // slab-resident sub-samples (one thread-block cluster per slab, links in shared memory)
     int slab_mode = 0;    // 0: off, 1: on where the slab fits
     int slab_cluster = 0; // CTAs per slab (0: chosen by slab_plan)
+    bool contract_tiled = true; // FP32 insertion contraction in the shared-memory tiled form
     unsigned long long spin_limit = 1ull << 24;
     unsigned int* d_bar = nullptr;    // [0] arrivals, [1] generation
     int* d_status = nullptr;          // nonzero after a wait gave up
@@ -310,6 +311,10 @@ int check_device_status(ul_lattice* h)
     UL_CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream));
     UL_CK(h, cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned int), h->stream));
     UL_CK(h, cudaStreamSynchronize(h->stream));
+    if (st == 2)
+        return fail(h, UL_ETIMEOUT,
+                    "a staging-copy wait of the insertion contraction reached its limit; the field sums of "
+                    "this level are incomplete");
     return fail(h, UL_ETIMEOUT,
                 "a grid-barrier wait of a persistent sweep reached its limit; the sweep stopped early and "
                 "the link state is incomplete");
@@ -423,8 +428,10 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             if (fields) {
                 UL_CK(h, cudaEventRecord(h->ev_slab[buf], h->stream));
                 UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_slab[buf], 0));
-                e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream)
-                              : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum, h->aux_stream);
+                e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum,
+                                                                      h->aux_stream, h->contract_tiled, h->d_status)
+                              : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum,
+                                                                     h->aux_stream, h->contract_tiled, h->d_status);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 UL_CK(h, cudaEventRecord(h->ev_contract[buf], h->aux_stream));
                 h->launches += 1;
@@ -456,8 +463,10 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             if (rc) return rc;
             if (fields) {
                 cudaError_t e = is_f64(h)
-                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream)
-                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream);
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream,
+                                                            h->contract_tiled, h->d_status)
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream,
+                                                           h->contract_tiled, h->d_status);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 h->launches += 1;
             }
@@ -486,8 +495,10 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             }
             if (fields) {
                 cudaError_t e = is_f64(h)
-                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, st)
-                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, st);
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, st,
+                                                            h->contract_tiled, h->d_status)
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, st,
+                                                           h->contract_tiled, h->d_status);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 ++n;
             }
@@ -673,6 +684,10 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
         if ((e = cudaEventCreateWithFlags(&h->ev_contract[b], cudaEventDisableTiming)) != cudaSuccess)
             return bail(e, "event");
     }
+    if ((e = is_f64(h) ? ul::prepare_insertion_contract<double>() : ul::prepare_insertion_contract<float>()) !=
+        cudaSuccess)
+        return bail(e, "kernel attributes");
+    if ((e = ul::prepare_ml_reduce()) != cudaSuccess) return bail(e, "kernel attributes");
     if ((e = cudaMalloc(&h->plaq_partials, ul::plaquette_partials(h->g) * sizeof(double))) != cudaSuccess)
         return bail(e, "plaquette partials");
     if ((e = cudaMemsetAsync(h->d_accepted, 0, sizeof(unsigned long long), h->stream)) != cudaSuccess)
@@ -1116,6 +1131,10 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
         if (!(v >= 0.0) || v > 16.0 || v != static_cast<int>(v))
             return fail(h, UL_EINVAL, "slab_cluster must be an integer in [0, 16]");
         h->slab_cluster = static_cast<int>(v);
+    } else if (!std::strcmp(key, "contract_tiled")) {
+        if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "contract_tiled must be 0 or 1");
+        h->contract_tiled = v != 0.0;
+        drop_graphs(h, 0); // captured sequences hold the contraction launch
     } else if (!std::strcmp(key, "insertion_chunk_mb")) {
         if (!(v >= 1.0) || v > 1e6 || v != static_cast<int>(v))
             return fail(h, UL_EINVAL, "insertion_chunk_mb must be an integer in [1, 1e6]");

@@ -1,0 +1,328 @@
+// ul_contract.cuh — tiled form of the deferred insertion contraction (FP32 links).
+// Included at the end of ul_kernels.cuh.
+//
+// Paper: arXiv:1208.0166, Section 2.2 (the insertion term of a slab is the slab average of
+// T(s,x0,r) times the insertion O at the plaquette x0 + floor(r/2) xhat + d yhat).
+//
+// The per-sample buffers hold, for every stored sub-sample k, the transporters
+// T_k(s, x0, r) and the channel sums O_k(s, site, ch) of every slab.  The contraction is
+//   bsum(s, r, d, ch, x0) += sum_k T_k(s, x0, r) O_k(s, x0 + floor(r/2) xhat + d yhat, ch).
+// Both shifts stay inside the z-plane of x0 (periodic in x and y), so one block owns
+//   one slab s, one z-plane, a tile of `ny` y-rows of that plane (all L x values),
+//   one group of two separations (ra, rb) and a subset of `ndb` offsets d,
+// and runs over the samples in batches of kInsertionBlock: each batch of transporters (the
+// tile's x0, both separations) and channel rows (rows py0 + d0 ... py0 + ny - 1 + d0 +
+// ndb - 1 of the plane) is copied into shared memory with cp.async, double-buffered, while
+// the previous batch is contracted.  A thread owns the 8 channels of one output (x0, r, d);
+// the two separations of a pair sit in neighbouring lanes, so that for the pairs (2,3),
+// (4,5), ... (equal shift floor(r/2)) the two lanes read the same channel row (one
+// shared-memory access serves both).  The remaining separation 1 pairs with r_max for
+// even r_max and is alone for odd r_max.
+//
+// Per output the arithmetic is that of insertion_contract_kernel<float> (the products of
+// the samples in order, blocks of kInsertionBlock folded into a compensated sum, the FP64
+// update of bsum), so both forms give the same bits.
+#pragma once
+
+namespace ul {
+
+// Block shape: at most kContractItems threads (a multiple of 32) and kContractSmem bytes of
+// shared memory, so that two blocks share an SM and one block's barriers and FP64 epilogue
+// overlap the other's contraction (measured faster than one block of 672 threads per SM).
+constexpr int kContractItems = 352, kContractSmem = 110 * 1024, kContractBlocksPerSM = 2;
+
+struct ContractTile {
+    int ny = 0, ndb = 0, rows = 0, bs = 0, tpad = 0;
+    int threads = 0, smem = 0;
+    int ytiles = 0, dsubs = 0, groups = 0;
+    bool ok = false;
+};
+
+// Tile plan of one launch with at most `max_items` threads and `max_smem` bytes of shared
+// memory per block; ok = false where a batch of kInsertionBlock samples does not fit (large
+// L with many offsets): the untiled kernel runs instead.
+// The second transporter plane of a sample starts tpad floats after the first, so that
+// the two lanes of a pair hit different banks (its byte offset is 64 modulo 128).
+inline ContractTile contract_tile(const Geo& g, int r_max, int nd, int max_items, int max_smem)
+{
+    ContractTile t;
+    const int L = g.L;
+    const int per_row = 2 * L; // threads per (y-row, offset): two separations x L
+    t.ndb = std::min(nd, std::max(1, max_items / per_row));
+    t.ny = std::max(1, std::min(L, max_items / (per_row * t.ndb)));
+    t.bs = kInsertionBlock;
+    auto tpad = [&](int ny) { return ((64 - 8 * L * ny) % 128 + 128) % 128 / 4; };
+    auto smem_for = [&](int ny) {
+        const long rows = std::min(L, ny + t.ndb - 1);
+        const long per_sample = (4L * L * ny + tpad(ny)) * sizeof(float) // T: (ra, rb) planes of L ny complex
+                                + rows * L * 8 * sizeof(float);          // O rows
+        return 2 * t.bs * per_sample;
+    };
+    while (t.ny > 1 && smem_for(t.ny) > max_smem) --t.ny; // fewer y-rows per tile to fit
+    t.tpad = tpad(t.ny);
+    t.rows = std::min(L, t.ny + t.ndb - 1);
+    const int items = per_row * t.ny * t.ndb;
+    t.threads = (items + 31) / 32 * 32;
+    t.smem = static_cast<int>(smem_for(t.ny));
+    t.ytiles = (L + t.ny - 1) / t.ny;
+    t.dsubs = (nd + t.ndb - 1) / t.ndb;
+    t.groups = (r_max + 1) / 2;
+    t.ok = items <= max_items && t.smem <= max_smem;
+    return t;
+}
+
+__device__ __forceinline__ void contract_group(int gi, int r_max, int& ra, int& rb)
+{
+    const int npairs = (r_max - 1) / 2;
+    if (gi < npairs) {
+        ra = 2 * gi + 2;
+        rb = 2 * gi + 3;
+    } else {
+        ra = 1;
+        rb = (r_max % 2 == 0) ? r_max : 0;
+    }
+}
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p)
+{
+    return static_cast<unsigned int>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// one arrival that also announces `bytes` of bulk copies completing on the barrier's phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned int bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity)
+{
+    unsigned int done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+// Waits for the phase `parity` of the barrier, at most about kCopyWaitCycles SM cycles
+// (about a second); false when the limit was reached.
+constexpr long long kCopyWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned int parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kCopyWaitCycles) return false;
+    return true;
+}
+
+// Bulk copy global -> shared memory of this CTA (16-byte aligned addresses, size a multiple
+// of 16), completing `bytes` on the barrier.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned int bytes,
+                                              unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// One sample of one output: the transporter (re, im) at t, the 8 channels of the shifted
+// site at o.
+__device__ __forceinline__ void contract_sample(const float* t, const float* o, InsertionAcc<float>* acc)
+{
+    const float2 tv = *reinterpret_cast<const float2*>(t);
+    const float4 lo = *reinterpret_cast<const float4*>(o);
+    const float4 hi = *reinterpret_cast<const float4*>(o + 4);
+    const Cx<float> T{tv.x, tv.y};
+    acc[0].add(T, lo.x);
+    acc[1].add(T, lo.y);
+    acc[2].add(T, lo.z);
+    acc[3].add(T, lo.w);
+    acc[4].add(T, hi.x);
+    acc[5].add(T, hi.y);
+    acc[6].add(T, hi.z);
+    acc[7].add(T, hi.w);
+}
+
+// The copies of one batch into buffer `buf`, issued by the 32 lanes of one warp (lane j:
+// sample k0 + j): per sample the transporter rows of the tile for each separation and the
+// staged channel rows (two copies where the rows wrap past L - 1); lane 0 first announces
+// the batch's bytes on the buffer's barrier.
+__device__ __forceinline__ void issue_batch(float* smem, unsigned long long* bars, int k0, int buf, int nb, int bufsz,
+                                            int tsz, int osz, int o_at, int tplane, int nr,
+                                            const Cx<float>* tsrc0, long t_db, long t_ks, unsigned int t_bytes,
+                                            const float* osrc0, long o_ks, int row0, int n1, int rows, int L,
+                                            unsigned int o_bytes)
+{
+    float* base = smem + buf * bufsz;
+    const int lane = static_cast<int>(threadIdx.x) & 31;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[buf], (nr * t_bytes + o_bytes) * nb);
+    __syncwarp();
+    for (int j = lane; j < nb; j += 32) {
+        const long k = k0 + j;
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const Cx<float>* ts = tsrc0 + k * t_ks;
+        bulk_copy_g2s(base + j * tsz, ts, t_bytes, &bars[buf]);
+        if (nr == 2) bulk_copy_g2s(base + j * tsz + tplane, ts + t_db, t_bytes, &bars[buf]);
+        const float* os = osrc0 + k * o_ks;
+        float* od = base + o_at + j * osz;
+        const unsigned int seg1 = static_cast<unsigned int>(n1 * L * 8 * sizeof(float));
+        bulk_copy_g2s(od, os + static_cast<long>(row0) * L * 8, seg1, &bars[buf]);
+        if (n1 < rows) bulk_copy_g2s(od + n1 * L * 8, os, o_bytes - seg1, &bars[buf]);
+    }
+}
+
+// Shared memory of one batch buffer (floats):
+//   T[j][ri][x0l] complex, j < kInsertionBlock, ri < 2, x0l < L ny   (4 L ny + tpad floats per
+//                          sample; plane ri = 1 starts 2 L ny + tpad floats after plane 0)
+//   O[j][rl][x][ch],       rl < rows, x < L, ch < 8                  (8 rows L floats per sample)
+// The two lanes of a pair read the same O site (one access); eight lanes read four sites 32
+// bytes apart, one 128-byte line, so the 128-bit loads need no swizzle.
+template <typename R>
+__global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
+    insertion_contract_tiled_kernel(Geo g, int S, int r_max, int nd, int count, ContractTile t,
+                                    const Cx<float>* __restrict__ tk, const float* __restrict__ ok,
+                                    double2* __restrict__ bsum, int* __restrict__ status)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ unsigned long long bars[2];
+    constexpr int BS = kInsertionBlock;
+    const int L = g.L, L2 = g.L * g.L;
+    // block -> (s, pz, ytile, group, dsub), dsub fastest: the blocks of one plane run together
+    int b = static_cast<int>(blockIdx.x);
+    const int dsub = b % t.dsubs;
+    b /= t.dsubs;
+    const int gi = b % t.groups;
+    b /= t.groups;
+    const int ytile = b % t.ytiles;
+    b /= t.ytiles;
+    const int pz = b % L;
+    const int s = b / L;
+    int ra, rb;
+    contract_group(gi, r_max, ra, rb);
+    const int nr = rb ? 2 : 1;
+    const int py0 = ytile * t.ny, d0 = dsub * t.ndb;
+    const int nyv = min(t.ny, L - py0);          // y-rows of this tile
+    const int XT = L * t.ny;                     // x0 slots per staged sample
+    const int row0 = (py0 + d0) % L;             // first staged channel row
+    const int tsz = XT * 4 + t.tpad, osz = t.rows * L * 8; // floats per staged sample
+    const int bufsz = BS * (tsz + osz);          // floats per batch buffer: T then O
+    const long plane = static_cast<long>(L2) * pz;
+
+    // this thread's output (x0, r, d): separation fastest, then x, y-row, offset
+    const int tid = static_cast<int>(threadIdx.x);
+    const int ri = tid & 1, item = tid >> 1;
+    const int px = item % L, pyl = (item / L) % t.ny, dl = item / (L * t.ny);
+    const int r = ri ? rb : ra;
+    const bool active = item < L * t.ny * t.ndb && r != 0 && pyl < nyv && d0 + dl < nd;
+    const int toff = ri * (2 * XT + t.tpad) + 2 * (px + L * pyl);         // transporter in a staged sample
+    const int ooff = (((pyl + dl) % L) * L + (px + r / 2) % L) * 8;      // shifted channel site
+
+    // batch copies, issued by the lanes of warp 0 (lane j: sample j of the batch)
+    const int n1 = min(t.rows, L - row0); // staged rows before the wrap to row 0
+    const unsigned int t_bytes = static_cast<unsigned int>(nyv * L * sizeof(Cx<float>));
+    const unsigned int o_bytes = static_cast<unsigned int>(t.rows * L * 8 * sizeof(float));
+    const Cx<float>* tsrc0 = tk + (static_cast<long>(s) * r_max + (ra - 1)) * g.L3 + plane + static_cast<long>(L) * py0;
+    const long t_db = static_cast<long>(rb - ra) * g.L3;         // second separation's plane
+    const long t_ks = static_cast<long>(S) * r_max * g.L3;       // per sample (complex)
+    const float* osrc0 = ok + (static_cast<long>(s) * g.L3 + plane) * 8;
+    const long o_ks = static_cast<long>(S) * g.L3 * 8;           // per sample (floats)
+    const int tplane = 2 * XT + t.tpad;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    InsertionAcc<float> acc[8];
+    const int nbatch = (count + BS - 1) / BS;
+    if (tid < 32)
+        issue_batch(smem, bars, 0, 0, min(BS, count), bufsz, tsz, osz, BS * tsz, tplane, nr, tsrc0, t_db, t_ks,
+                    t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes);
+    for (int bi = 0; bi < nbatch; ++bi) {
+        const int buf = bi & 1;
+        const int k0 = bi * BS;
+        const int nb = min(BS, count - k0);
+        // the other buffer was last read in batch bi - 1, which every thread has finished
+        if (bi + 1 < nbatch && tid < 32)
+            issue_batch(smem, bars, k0 + BS, buf ^ 1, min(BS, count - k0 - BS), bufsz, tsz, osz, BS * tsz, tplane, nr,
+                        tsrc0, t_db, t_ks, t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes);
+        const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1);
+        if (__syncthreads_or(!arrived)) {
+            // a copy did not complete in time: report it, give the copies in flight a bounded
+            // wait so that none lands after the block has left, and stop
+            if (tid == 0) {
+                atomicExch(status, 2);
+                mbar_wait_bounded(&bars[buf], (bi >> 1) & 1);
+                if (bi + 1 < nbatch) mbar_wait_bounded(&bars[buf ^ 1], ((bi + 1) >> 1) & 1);
+            }
+            return;
+        }
+        if (active) {
+            const float* sT = smem + buf * bufsz + toff;
+            const float* sO = smem + buf * bufsz + BS * tsz + ooff;
+            if (nb == BS) {
+                // a whole block of kInsertionBlock samples (k0 is a multiple of it): fold after it
+#pragma unroll
+                for (int j = 0; j < BS; ++j) contract_sample(sT + j * tsz, sO + j * osz, acc);
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
+            } else {
+                for (int j = 0; j < nb; ++j) contract_sample(sT + j * tsz, sO + j * osz, acc);
+            }
+        }
+        __syncthreads(); // the next batch overwrites this buffer
+    }
+    if (!active) return;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
+    const int x0 = px + L * (py0 + pyl) + L2 * pz;
+    const long base = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d0 + dl) * 8) * g.L3 + x0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+        double2 v = bsum[base + ch * g.L3];
+        v.x += acc[ch].total_re();
+        v.y += acc[ch].total_im();
+        bsum[base + ch * g.L3] = v;
+    }
+}
+
+template <typename R>
+cudaError_t prepare_insertion_contract()
+{
+    if constexpr (sizeof(R) == 4)
+        return cudaFuncSetAttribute(insertion_contract_tiled_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kContractSmem);
+    return cudaSuccess;
+}
+
+// Launches the tiled form for FP32 links; returns false (nothing launched) where it does
+// not apply, and the caller runs the untiled kernel.
+template <typename R>
+bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
+                           double2* bsum, int* status, cudaStream_t st, cudaError_t* err)
+{
+    if constexpr (sizeof(R) != 4) {
+        return false;
+    } else {
+        const ContractTile t = contract_tile(g, r_max, nd, kContractItems, kContractSmem);
+        if (!t.ok || count < 1) return false;
+        const long blocks = static_cast<long>(S) * g.L * t.ytiles * t.groups * t.dsubs;
+        insertion_contract_tiled_kernel<float><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
+            g, S, r_max, nd, count, t, static_cast<const Cx<float>*>(tk), static_cast<const float*>(ok), bsum,
+            status);
+        *err = cudaGetLastError();
+        return true;
+    }
+}
+
+} // namespace ul

@@ -73,10 +73,21 @@ template <typename R>
 cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* ubar, cudaStream_t st);
 
 // bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] += sum over the first `count` stored samples of
-// T(s,x0,r) O(s, x0 + floor(r/2) xhat + d yhat, ch).
+// T(s,x0,r) O(s, x0 + floor(r/2) xhat + d yhat, ch).  tiled: FP32 links use the
+// shared-memory tiled form where it applies (same bits as the untiled kernel); its bounded
+// waits for the staging copies write 2 to *status when they give up.
 template <typename R>
 cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
-                                      const void* ok, double2* bsum, cudaStream_t st);
+                                      const void* ok, double2* bsum, cudaStream_t st, bool tiled, int* status);
+
+// Raises the dynamic shared-memory limit of the tiled FP32 contraction (once per process,
+// before any launch or graph capture that may use it).
+template <typename R>
+cudaError_t prepare_insertion_contract();
+
+// Raises the dynamic shared-memory limit of the reduction that keeps the other-slab
+// weights in shared memory (up to 50 slabs; more slabs use a per-thread prefix array).
+cudaError_t prepare_ml_reduce();
 
 // Cross-slab products, x0 reduction and normalisation.  out_dev receives
 // 2*r_max doubles (correlator) followed by 2*r_max*nd*8 doubles (fields) and 8 (vacuum).

@@ -607,8 +607,9 @@ struct InsertionAcc<float> {
         bre = 0.f;
         bim = 0.f;
     }
-    __device__ __forceinline__ double total_re() const { return static_cast<double>(re) - static_cast<double>(re_c); }
-    __device__ __forceinline__ double total_im() const { return static_cast<double>(im) - static_cast<double>(im_c); }
+    // the compensated sum rounded once to FP32, then widened (one FP64-pipe conversion)
+    __device__ __forceinline__ double total_re() const { return static_cast<double>(__fsub_rn(re, re_c)); }
+    __device__ __forceinline__ double total_im() const { return static_cast<double>(__fsub_rn(im, im_c)); }
 };
 
 template <typename R>
@@ -1000,10 +1001,16 @@ cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* uba
 }
 
 template <typename R>
+bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
+                           double2* bsum, int* status, cudaStream_t st, cudaError_t* err);
+
+template <typename R>
 cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
-                                      const void* ok, double2* bsum, cudaStream_t st)
+                                      const void* ok, double2* bsum, cudaStream_t st, bool tiled, int* status)
 {
     const int S = g.Nt / slab_t;
+    cudaError_t err = cudaSuccess;
+    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk, ok, bsum, status, st, &err)) return err;
     const long total = static_cast<long>(S) * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
         g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk), static_cast<const R*>(ok), bsum);
@@ -1101,9 +1108,11 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
                                                  void*, double*, const void*, cudaStream_t);                        \
     template cudaError_t launch_multihit<R>(const Geo&, const void*, double, void*, cudaStream_t);                 \
     template cudaError_t launch_insertion_contract<R>(const Geo&, int, int, int, int, const void*, const void*,     \
-                                                      double2*, cudaStream_t);
+                                                      double2*, cudaStream_t, bool, int*);                         \
+    template cudaError_t prepare_insertion_contract<R>();
 
 } // namespace ul
 
 #include "ul_slab.cuh"
 #include "ul_sym.cuh"
+#include "ul_contract.cuh"

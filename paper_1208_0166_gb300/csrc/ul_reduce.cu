@@ -85,6 +85,79 @@ __global__ void __launch_bounds__(kT) ml_reduce_kernel(Geo g, int S, int n_sub, 
     }
 }
 
+// The same reduction with the other-slab weights W_s = (1/n_sub) prod_{s' != s} A_s'(x0, r)
+// formed once per (x0, r) and kept in shared memory (column tid of wsm[S][kT]: no thread
+// reads another's), so the offsets d reuse them; a term of the field sums is then four
+// FP64 fused multiply-adds, B_s W_s (the mean of B folded into W).  The correlator is
+// summed exactly as in ml_reduce_kernel.
+constexpr int kReduceSmemBytes = 200 * 1024;
+
+__global__ void __launch_bounds__(kT) ml_reduce_w_kernel(Geo g, int S, int n_sub, int r_max, int nd,
+                                                          const double2* __restrict__ asum,
+                                                          const double2* __restrict__ bsum_in,
+                                                          double* __restrict__ partials)
+{
+    extern __shared__ double2 wsm[];
+    __shared__ double smem[kT / 32];
+    const int chunks = gridDim.x, chunk = blockIdx.x, r = blockIdx.y;
+    const int tid = static_cast<int>(threadIdx.x);
+    const int x0 = chunk * kT + tid;
+    const bool valid = x0 < g.L3;
+    const int Q = 1 + nd * 8;
+    const double n = 1.0 / static_cast<double>(n_sub);
+    Cx<double> p{1.0, 0.0};
+    for (int s = 0; s < S; ++s) {
+        const Cx<double> A = valid ? mean_of(asum[static_cast<long>(s * r_max + r) * g.L3 + x0], n) : Cx<double>{0.0, 0.0};
+        wsm[s * kT + tid] = make_double2(p.re, p.im); // prefix prod_{s' < s} A_s'
+        p = cmul(p, A);
+    }
+    const Cx<double> c = valid ? p : Cx<double>{0.0, 0.0};
+    double re = bsum(c.re, smem);
+    double im = bsum(c.im, smem);
+    if (threadIdx.x == 0) {
+        const long o = ((static_cast<long>(r) * Q + 0) * chunks + chunk) * 2;
+        partials[o] = re;
+        partials[o + 1] = im;
+    }
+    if (nd == 0) return;
+    if (valid) {
+        Cx<double> suf{1.0, 0.0};
+        for (int s = S - 1; s >= 0; --s) {
+            const double2 pre = wsm[s * kT + tid];
+            const Cx<double> W = cmul(Cx<double>{pre.x, pre.y}, suf);
+            wsm[s * kT + tid] = make_double2(W.re * n, W.im * n);
+            suf = cmul(mean_of(asum[static_cast<long>(s * r_max + r) * g.L3 + x0], n), suf);
+        }
+    }
+    for (int d = 0; d < nd; ++d) {
+        double ar[8], ai[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) ar[ch] = ai[ch] = 0.0;
+        if (valid) {
+            for (int s = S - 1; s >= 0; --s) {
+                const double2 W = wsm[s * kT + tid];
+                const long base = ((static_cast<long>(s * r_max + r) * nd + d) * 8) * g.L3 + x0;
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    const double2 B = bsum_in[base + ch * g.L3];
+                    ar[ch] = fma(B.x, W.x, fma(-B.y, W.y, ar[ch]));
+                    ai[ch] = fma(B.x, W.y, fma(B.y, W.x, ai[ch]));
+                }
+            }
+        }
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+            re = bsum(ar[ch], smem);
+            im = bsum(ai[ch], smem);
+            if (threadIdx.x == 0) {
+                const long o = ((static_cast<long>(r) * Q + 1 + d * 8 + ch) * chunks + chunk) * 2;
+                partials[o] = re;
+                partials[o + 1] = im;
+            }
+        }
+    }
+}
+
 // One thread per output double: sum over chunks in order, then normalise.
 __global__ void ml_finalize_kernel(int r_max, int nd, int chunks, const double* __restrict__ partials, double L3,
                                    double V, double* __restrict__ out)
@@ -223,7 +296,11 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
     const int S = g.Nt / slab_t;
     if (S > kMaxSlabs) return cudaErrorInvalidValue;
     const int chunks = (g.L3 + kT - 1) / kT;
-    ml_reduce_kernel<<<dim3(chunks, r_max), kT, 0, st>>>(g, S, n_sub, r_max, nd, asum, bsum_in, partials);
+    const size_t wbytes = static_cast<size_t>(S) * kT * sizeof(double2);
+    if (wbytes <= kReduceSmemBytes)
+        ml_reduce_w_kernel<<<dim3(chunks, r_max), kT, wbytes, st>>>(g, S, n_sub, r_max, nd, asum, bsum_in, partials);
+    else
+        ml_reduce_kernel<<<dim3(chunks, r_max), kT, 0, st>>>(g, S, n_sub, r_max, nd, asum, bsum_in, partials);
     const int nout = r_max * (1 + nd * 8) * 2;
     ml_finalize_kernel<<<(nout + kT - 1) / kT, kT, 0, st>>>(r_max, nd, chunks, partials, static_cast<double>(g.L3),
                                                              static_cast<double>(g.V), out_dev);
@@ -231,6 +308,11 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
         ml_vacuum_kernel<<<8, kT, 0, st>>>(S * g.L3, osum, static_cast<double>(n_sub) * static_cast<double>(g.V),
                                            out_dev + 2 * r_max + 2 * r_max * nd * 8);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_ml_reduce()
+{
+    return cudaFuncSetAttribute(ml_reduce_w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kReduceSmemBytes);
 }
 
 cudaError_t launch_ml_vacuum(int SL3, const double* osum, int nch, double nV, double* out, cudaStream_t st)

@@ -33,7 +33,8 @@ def _same(g, c, gr, cr):
 
 @pytest.mark.parametrize("slab", [0, 1])
 @pytest.mark.parametrize("L,Nt,tau,n_sub,r_max,d_max", [(2, 2, 1, 2, 1, 1), (2, 2, 2, 1, 1, 1), (2, 4, 4, 2, 1, 1),
-                                                         (6, 4, 2, 1, 3, 5), (4, 6, 3, 2, 2, 3)])
+                                                         (6, 4, 2, 1, 3, 5), (4, 6, 3, 2, 2, 3),
+                                                         (2, 104, 2, 2, 1, 1)])  # 52 slabs: the other reduction form
 def test_one_level_degenerate_shapes(slab, L, Nt, tau, n_sub, r_max, d_max):
     g, c = _pair(L, Nt, 41, slab)
     _same(g, c, g.multilevel_fields(tau, n_sub, r_max, d_max), c.multilevel(tau, n_sub, r_max, d_max=d_max))
