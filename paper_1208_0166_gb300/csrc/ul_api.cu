@@ -321,14 +321,19 @@ int check_device_status(ul_lattice* h)
 }
 
 // Sub-samples per insertion contraction: a quarter of the level (so that the contraction of
-// one chunk can overlap the next chunk's updates), bounded so that two chunk buffers fit
-// into the option "insertion_chunk_mb".  The same chunks in every launch mode, so that the
+// one chunk can overlap the next chunk's updates), but at least kMinChunkSamples (a
+// contraction launch has a fixed cost, the FP64 read-modify-write of the field sums: with
+// fewer samples the overlapped contractions fall behind the slab-resident updates, and a
+// level of fewer samples is contracted once), bounded so that two chunk buffers fit into
+// the option "insertion_chunk_mb".  The same chunks in every launch mode, so that the
 // modes give the same sums.
+constexpr int kMinChunkSamples = 48;
+
 int chunk_samples(const ul_lattice* h, int n_sub, size_t per_sample)
 {
     const size_t cap = (static_cast<size_t>(h->chunk_mb) << 20) / 2;
-    const size_t quarter = (static_cast<size_t>(n_sub) + 3) / 4;
-    return static_cast<int>(std::max<size_t>(1, std::min<size_t>(quarter, cap / per_sample)));
+    const size_t quarter = std::max<size_t>((static_cast<size_t>(n_sub) + 3) / 4, kMinChunkSamples);
+    return static_cast<int>(std::max<size_t>(1, std::min<size_t>({quarter, static_cast<size_t>(n_sub), cap / per_sample})));
 }
 
 int compound_sweep(ul_lattice* h, int n_metro, int n_or)

@@ -447,6 +447,7 @@ int ul_batch_create(ul_batch** out, int precision, size_t hbm_budget_bytes, void
         b->stream = b->own_stream;
     }
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->base), hbm_budget_bytes);
+    if (e == cudaSuccess) e = ul::prepare_ml_reduce();
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (b->own_stream) cudaStreamDestroy(b->own_stream);

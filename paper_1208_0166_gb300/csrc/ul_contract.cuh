@@ -23,6 +23,7 @@
 // the samples in order, blocks of kInsertionBlock folded into a compensated sum, the FP64
 // update of bsum), so both forms give the same bits.
 #pragma once
+#include <atomic>
 
 namespace ul {
 
@@ -296,12 +297,19 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     }
 }
 
+// set once the shared-memory limit has been raised: until then a tile that needs more than
+// the default 48 KB runs as the untiled kernel
+inline std::atomic<bool> g_contract_prepared{false};
+
 template <typename R>
 cudaError_t prepare_insertion_contract()
 {
-    if constexpr (sizeof(R) == 4)
-        return cudaFuncSetAttribute(insertion_contract_tiled_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kContractSmem);
+    if constexpr (sizeof(R) == 4) {
+        const cudaError_t e = cudaFuncSetAttribute(insertion_contract_tiled_kernel<float>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
+        if (e == cudaSuccess) g_contract_prepared.store(true);
+        return e;
+    }
     return cudaSuccess;
 }
 
@@ -315,7 +323,7 @@ bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, co
         return false;
     } else {
         const ContractTile t = contract_tile(g, r_max, nd, kContractItems, kContractSmem);
-        if (!t.ok || count < 1) return false;
+        if (!t.ok || count < 1 || (t.smem > 48 * 1024 && !g_contract_prepared.load())) return false;
         const long blocks = static_cast<long>(S) * g.L * t.ytiles * t.groups * t.dsubs;
         insertion_contract_tiled_kernel<float><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
             g, S, r_max, nd, count, t, static_cast<const Cx<float>*>(tk), static_cast<const float*>(ok), bsum,

@@ -5,6 +5,7 @@
 //                                                                  B_s = <T O>_s
 // The product over the other slabs is prefix(s) * suffix(s+1) (no division).  All sums
 // run in a fixed order, so results are bitwise reproducible for a fixed lattice shape.
+#include <atomic>
 #include "ul_device.cuh"
 #include "ul_internal.h"
 #include "ul_math.cuh"
@@ -277,6 +278,10 @@ cudaError_t launch_fold_level2_fields(const Geo& g, int tau1, int tau2, int r_ma
     return cudaGetLastError();
 }
 
+// set once the shared-memory limit has been raised: until then a launch that needs more
+// than the default 48 KB takes the prefix-array form
+std::atomic<bool> g_reduce_prepared{false};
+
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st)
 {
     set_u64_kernel<<<1, 1, 0, st>>>(p, v);
@@ -297,7 +302,7 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
     if (S > kMaxSlabs) return cudaErrorInvalidValue;
     const int chunks = (g.L3 + kT - 1) / kT;
     const size_t wbytes = static_cast<size_t>(S) * kT * sizeof(double2);
-    if (wbytes <= kReduceSmemBytes)
+    if (wbytes <= 48 * 1024 || (wbytes <= kReduceSmemBytes && g_reduce_prepared.load()))
         ml_reduce_w_kernel<<<dim3(chunks, r_max), kT, wbytes, st>>>(g, S, n_sub, r_max, nd, asum, bsum_in, partials);
     else
         ml_reduce_kernel<<<dim3(chunks, r_max), kT, 0, st>>>(g, S, n_sub, r_max, nd, asum, bsum_in, partials);
@@ -312,7 +317,10 @@ cudaError_t launch_ml_reduce(const Geo& g, int slab_t, int n_sub, int r_max, int
 
 cudaError_t prepare_ml_reduce()
 {
-    return cudaFuncSetAttribute(ml_reduce_w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kReduceSmemBytes);
+    const cudaError_t e =
+        cudaFuncSetAttribute(ml_reduce_w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kReduceSmemBytes);
+    if (e == cudaSuccess) g_reduce_prepared.store(true);
+    return e;
 }
 
 cudaError_t launch_ml_vacuum(int SL3, const double* osum, int nch, double nV, double* out, cudaStream_t st)

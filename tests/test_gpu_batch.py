@@ -15,6 +15,7 @@ MIX = [  # (L, Nt, beta, seed, n_sweeps, slab_t, n_sub, r_max)
     (12, 12, 0.96, 13, 2, 2, 3, 4),
     (4, 6, 1.0, 14, 4, 3, 5, 2),
     (10, 8, 1.0, 15, 1, 4, 2, 5),
+    (4, 28, 1.0, 16, 1, 2, 2, 2),  # 14 slabs: the reduction's weights need 56 KB of shared memory
 ]
 
 
