@@ -404,6 +404,7 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
     for (int k = 0; k < n_sub;) {
         const int count = std::min(seq, n_sub - k);
         const int sm = h->sub_metro, so = h->sub_or;
+        const bool chunk_first = k == 0; // the first contraction writes the field sums
         if (slab_cl) {
             // chunk c fills buffer c % 2 on the handle's stream; its contraction runs on the
             // auxiliary stream (on the SMs the cluster grid leaves free) while chunk c + 1 runs
@@ -434,9 +435,11 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
                 UL_CK(h, cudaEventRecord(h->ev_slab[buf], h->stream));
                 UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_slab[buf], 0));
                 e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum,
-                                                                      h->aux_stream, h->contract_tiled, h->d_status)
+                                                                      chunk_first, h->aux_stream, h->contract_tiled,
+                                                                      h->d_status)
                               : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum,
-                                                                     h->aux_stream, h->contract_tiled, h->d_status);
+                                                                     chunk_first, h->aux_stream, h->contract_tiled,
+                                                                     h->d_status);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 UL_CK(h, cudaEventRecord(h->ev_contract[buf], h->aux_stream));
                 h->launches += 1;
@@ -448,7 +451,7 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
                 UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
             continue;
         }
-        const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
+        const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count, chunk_first ? 1 : 0,
                                             bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
                                             reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
                                             reinterpret_cast<long long>(tk), reinterpret_cast<long long>(ok),
@@ -468,10 +471,10 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             if (rc) return rc;
             if (fields) {
                 cudaError_t e = is_f64(h)
-                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream,
-                                                            h->contract_tiled, h->d_status)
-                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, h->stream,
-                                                           h->contract_tiled, h->d_status);
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first,
+                                                            h->stream, h->contract_tiled, h->d_status)
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first,
+                                                           h->stream, h->contract_tiled, h->d_status);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 h->launches += 1;
             }
@@ -500,9 +503,9 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             }
             if (fields) {
                 cudaError_t e = is_f64(h)
-                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, st,
+                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first, st,
                                                             h->contract_tiled, h->d_status)
-                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, st,
+                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first, st,
                                                            h->contract_tiled, h->d_status);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 ++n;
@@ -564,7 +567,6 @@ int level_begin(ul_lattice* h, int slab_t, int n_sub, int r_max, int d_max, bool
     double* dout = reinterpret_cast<double*>(base + off_out);
     UL_CK(h, cudaMemsetAsync(asum, 0, n_a * sizeof(double2), h->stream));
     if (fields) {
-        UL_CK(h, cudaMemsetAsync(bsum, 0, n_b * sizeof(double2), h->stream));
         UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
     }
 
@@ -1055,7 +1057,6 @@ int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int
         account_passes(h, sm, tau1);
         // level 2: n2 sub-samples with t = 0 mod tau2 frozen, measured into fresh accumulators
         UL_CK(h, cudaMemsetAsync(asum2, 0, n_a2 * sizeof(double2), h->stream));
-        UL_CK(h, cudaMemsetAsync(bsum2, 0, n_b2 * sizeof(double2), h->stream));
         rc = run_level(h, tau2, n2, r_max, nd, true, LevelBufs{asum2, bsum2, osum, tk, ok, nullptr, chunk});
         if (rc) return rc;
         cudaError_t e = ul::launch_fold_level2_fields(g, tau1, tau2, r_max, nd, n2, asum2, bsum2, asum1, bsum1,

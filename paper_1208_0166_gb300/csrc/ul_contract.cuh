@@ -191,7 +191,7 @@ template <typename R>
 __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     insertion_contract_tiled_kernel(Geo g, int S, int r_max, int nd, int count, ContractTile t,
                                     const Cx<float>* __restrict__ tk, const float* __restrict__ ok,
-                                    double2* __restrict__ bsum, int* __restrict__ status)
+                                    double2* __restrict__ bsum, bool first, int* __restrict__ status)
 {
     extern __shared__ __align__(16) float smem[];
     __shared__ unsigned long long bars[2];
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     const long base = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d0 + dl) * 8) * g.L3 + x0;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
-        double2 v = bsum[base + ch * g.L3];
+        double2 v = first ? make_double2(0.0, 0.0) : bsum[base + ch * g.L3];
         v.x += acc[ch].total_re();
         v.y += acc[ch].total_im();
         bsum[base + ch * g.L3] = v;
@@ -317,7 +317,7 @@ cudaError_t prepare_insertion_contract()
 // not apply, and the caller runs the untiled kernel.
 template <typename R>
 bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
-                           double2* bsum, int* status, cudaStream_t st, cudaError_t* err)
+                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err)
 {
     if constexpr (sizeof(R) != 4) {
         return false;
@@ -326,7 +326,7 @@ bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, co
         if (!t.ok || count < 1 || (t.smem > 48 * 1024 && !g_contract_prepared.load())) return false;
         const long blocks = static_cast<long>(S) * g.L * t.ytiles * t.groups * t.dsubs;
         insertion_contract_tiled_kernel<float><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
-            g, S, r_max, nd, count, t, static_cast<const Cx<float>*>(tk), static_cast<const float*>(ok), bsum,
+            g, S, r_max, nd, count, t, static_cast<const Cx<float>*>(tk), static_cast<const float*>(ok), bsum, first,
             status);
         *err = cudaGetLastError();
         return true;

@@ -73,12 +73,14 @@ template <typename R>
 cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* ubar, cudaStream_t st);
 
 // bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] += sum over the first `count` stored samples of
-// T(s,x0,r) O(s, x0 + floor(r/2) xhat + d yhat, ch).  tiled: FP32 links use the
+// T(s,x0,r) O(s, x0 + floor(r/2) xhat + d yhat, ch); with `first` bsum is written, not read
+// (the level's first chunk: no zeroing of the field sums needed).  tiled: FP32 links use the
 // shared-memory tiled form where it applies (same bits as the untiled kernel); its bounded
 // waits for the staging copies write 2 to *status when they give up.
 template <typename R>
 cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
-                                      const void* ok, double2* bsum, cudaStream_t st, bool tiled, int* status);
+                                      const void* ok, double2* bsum, bool first, cudaStream_t st, bool tiled,
+                                      int* status);
 
 // Raises the dynamic shared-memory limit of the tiled FP32 contraction (once per process,
 // before any launch or graph capture that may use it).

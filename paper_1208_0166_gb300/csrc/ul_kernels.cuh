@@ -639,6 +639,7 @@ struct Vec8<double> {
 
 // Deferred insertion contraction over the `count` samples stored in tk/ok:
 //   bsum[(((s*R + r-1)*nd + d)*8 + ch)*L3 + x0] += sum_k T_k(s,x0,r) O_k(s, x0 + floor(r/2) xhat + d yhat, ch)
+// (with `first`, the level's first chunk, bsum is not read: the sums start from 0)
 // thread per output (s, r, d, x0), one block per kThreads consecutive x0 of one (s, r, d);
 // the blocks of a tile of x0 are neighbours in the grid for all (r, d) (d fastest, then r),
 // so the transporters and channel rows they share are read from DRAM about once.  Each
@@ -649,7 +650,7 @@ constexpr int kContractMinBlocks = 3;
 template <typename R>
 __global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     insertion_contract_kernel(Geo g, int S, int r_max, int nd, int count, const Cx<R>* __restrict__ tk,
-                              const R* __restrict__ ok, double2* __restrict__ bsum)
+                              const R* __restrict__ ok, double2* __restrict__ bsum, bool first)
 {
     const int tiles = (g.L3 + kThreads - 1) / kThreads;
     int b = static_cast<int>(blockIdx.x);
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     const long base = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d) * 8) * g.L3 + x0;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
-        double2 b = bsum[base + ch * g.L3];
+        double2 b = first ? make_double2(0.0, 0.0) : bsum[base + ch * g.L3];
         b.x += acc[ch].total_re();
         b.y += acc[ch].total_im();
         bsum[base + ch * g.L3] = b;
@@ -1002,18 +1003,19 @@ cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* uba
 
 template <typename R>
 bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
-                           double2* bsum, int* status, cudaStream_t st, cudaError_t* err);
+                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err);
 
 template <typename R>
 cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
-                                      const void* ok, double2* bsum, cudaStream_t st, bool tiled, int* status)
+                                      const void* ok, double2* bsum, bool first, cudaStream_t st, bool tiled,
+                                      int* status)
 {
     const int S = g.Nt / slab_t;
     cudaError_t err = cudaSuccess;
-    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk, ok, bsum, status, st, &err)) return err;
+    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk, ok, bsum, first, status, st, &err)) return err;
     const long total = static_cast<long>(S) * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
-        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk), static_cast<const R*>(ok), bsum);
+        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk), static_cast<const R*>(ok), bsum, first);
     return cudaGetLastError();
 }
 
@@ -1108,7 +1110,7 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
                                                  void*, double*, const void*, cudaStream_t);                        \
     template cudaError_t launch_multihit<R>(const Geo&, const void*, double, void*, cudaStream_t);                 \
     template cudaError_t launch_insertion_contract<R>(const Geo&, int, int, int, int, const void*, const void*,     \
-                                                      double2*, cudaStream_t, bool, int*);                         \
+                                                      double2*, bool, cudaStream_t, bool, int*);                   \
     template cudaError_t prepare_insertion_contract<R>();
 
 } // namespace ul
