@@ -76,6 +76,9 @@ struct ul_lattice {
     size_t pinned_n = 0;
     cudaEvent_t ev_main = nullptr;
     cudaEvent_t ev_result = nullptr;
+    // two-level estimator with insertions: the fold of level-1 iteration k (second stream)
+    // has finished with the level-2 accumulators of parity k % 2
+    cudaEvent_t ev_fold[2] = {nullptr, nullptr};
 
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
@@ -138,6 +141,8 @@ void release(ul_lattice* h)
     if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     if (h->ev_main) cudaEventDestroy(h->ev_main);
     if (h->ev_result) cudaEventDestroy(h->ev_result);
+    for (int b = 0; b < 2; ++b)
+        if (h->ev_fold[b]) cudaEventDestroy(h->ev_fold[b]);
     if (h->pinned) cudaFreeHost(h->pinned);
     cudaFree(h->theta);
     cudaFree(h->cs);
@@ -372,7 +377,7 @@ struct LevelBufs {
 // chunk, added into the accumulators of b.  Slab-resident where the slab fits (and neither
 // multihit nor persistent mode is on), else persistent or per-class launches.
 int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fields, const LevelBufs& b,
-              bool wait_contraction = true)
+              bool wait_contraction = true, int buf0 = 0)
 {
     const ul::Geo& g = h->g;
     const int S = g.Nt / slab_t;
@@ -408,10 +413,11 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
         if (slab_cl) {
             // chunk c fills buffer c % 2 on the handle's stream; its contraction runs on the
             // auxiliary stream (on the SMs the cluster grid leaves free) while chunk c + 1 runs
-            const int buf = chunk_index % 2;
+            const int buf = (buf0 + chunk_index) % 2;
             void* tkb = static_cast<char*>(tk) + static_cast<size_t>(buf) * n_a * 2 * rs * chunk;
             void* okb = static_cast<char*>(ok) + static_cast<size_t>(buf) * 8ull * S * g.L3 * rs * chunk;
-            if (fields && chunk_index >= 2) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
+            // the buffer's previous contraction (of this level or an earlier one) has read it
+            if (fields) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
             ul::SlabArgs a{};
             a.u = persist_args(h, count, sm, so, slab_t).u;
             a.n_units = count;
@@ -686,6 +692,9 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
         return bail(e, "auxiliary stream");
     if ((e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
     if ((e = cudaEventCreateWithFlags(&h->ev_result, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaEventCreateWithFlags(&h->ev_fold[b], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e, "event");
     for (int b = 0; b < 2; ++b) {
         if ((e = cudaEventCreateWithFlags(&h->ev_slab[b], cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
         if ((e = cudaEventCreateWithFlags(&h->ev_contract[b], cudaEventDisableTiming)) != cudaSuccess)
@@ -1007,7 +1016,9 @@ int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int
     if (h->multihit) return fail(h, UL_EINVAL, "ul_multilevel2_fields: not available with the multihit option");
     const int S1 = g.Nt / tau1, S2 = g.Nt / tau2, nd = d_max + 1;
 
-    // Scratch: asum1 | bsum1 | asum2 | bsum2 | osum (level-2 layout) | tk | ok | partials | out
+    // Scratch: asum1 | bsum1 | asum2 x 2 | bsum2 x 2 | osum (level-2 layout) | tk | ok | partials | out
+    // (the level-2 accumulators are double-buffered by level-1 iteration: the fold of one
+    // iteration runs on the second stream while the next iteration updates and measures)
     const size_t rs = real_size(h);
     const size_t n_a1 = static_cast<size_t>(S1) * r_max * g.L3, n_a2 = static_cast<size_t>(S2) * r_max * g.L3;
     const size_t n_b1 = n_a1 * nd * 8, n_b2 = n_a2 * nd * 8;
@@ -1019,8 +1030,8 @@ int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int
     auto al = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
     const size_t off_b1 = al(n_a1 * sizeof(double2));
     const size_t off_a2 = off_b1 + al(n_b1 * sizeof(double2));
-    const size_t off_b2 = off_a2 + al(n_a2 * sizeof(double2));
-    const size_t off_o = off_b2 + al(n_b2 * sizeof(double2));
+    const size_t off_b2 = off_a2 + 2 * al(n_a2 * sizeof(double2));
+    const size_t off_o = off_b2 + 2 * al(n_b2 * sizeof(double2));
     const size_t off_t = off_o + al(n_o * sizeof(double));
     const size_t off_k = off_t + al(n_a2 * 2 * rs * chunk * 2);
     const size_t off_p = off_k + al(8ull * S2 * g.L3 * rs * chunk * 2);
@@ -1030,8 +1041,10 @@ int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int
     char* base = static_cast<char*>(h->ml_buf);
     double2* asum1 = reinterpret_cast<double2*>(base);
     double2* bsum1 = reinterpret_cast<double2*>(base + off_b1);
-    double2* asum2 = reinterpret_cast<double2*>(base + off_a2);
-    double2* bsum2 = reinterpret_cast<double2*>(base + off_b2);
+    double2* asum2[2] = {reinterpret_cast<double2*>(base + off_a2),
+                         reinterpret_cast<double2*>(base + off_a2 + al(n_a2 * sizeof(double2)))};
+    double2* bsum2[2] = {reinterpret_cast<double2*>(base + off_b2),
+                         reinterpret_cast<double2*>(base + off_b2 + al(n_b2 * sizeof(double2)))};
     double* osum = reinterpret_cast<double*>(base + off_o);
     void* tk = base + off_t;
     void* ok = base + off_k;
@@ -1042,6 +1055,7 @@ int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int
     UL_CK(h, cudaMemsetAsync(osum, 0, n_o * sizeof(double), h->stream));
     const int sm = h->sub_metro, so = h->sub_or;
     const long long kb = bits_of(h->beta), kw = bits_of(h->width), ks = static_cast<long long>(h->seed);
+    int buf0 = 0; // sample-buffer parity of the next level-2 chunk
 
     for (int k1 = 0; k1 < n1; ++k1) {
         // level-1 update: passes with the spatial links on t = 0 mod tau1 frozen
@@ -1056,14 +1070,30 @@ int ul_multilevel2_fields(ul_lattice* h, int tau1, int n1, int tau2, int n2, int
         if (rc) return rc;
         account_passes(h, sm, tau1);
         // level 2: n2 sub-samples with t = 0 mod tau2 frozen, measured into fresh accumulators
-        UL_CK(h, cudaMemsetAsync(asum2, 0, n_a2 * sizeof(double2), h->stream));
-        rc = run_level(h, tau2, n2, r_max, nd, true, LevelBufs{asum2, bsum2, osum, tk, ok, nullptr, chunk});
+        // of parity p, once the fold of iteration k1 - 2 has read them
+        const int p = k1 & 1;
+        UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_fold[p], 0));
+        UL_CK(h, cudaMemsetAsync(asum2[p], 0, n_a2 * sizeof(double2), h->stream));
+        rc = run_level(h, tau2, n2, r_max, nd, true, LevelBufs{asum2[p], bsum2[p], osum, tk, ok, nullptr, chunk},
+                       false, buf0);
         if (rc) return rc;
-        cudaError_t e = ul::launch_fold_level2_fields(g, tau1, tau2, r_max, nd, n2, asum2, bsum2, asum1, bsum1,
-                                                      h->stream);
+        buf0 = (buf0 + (n2 + chunk - 1) / chunk) % 2;
+        // the fold runs on the second stream after everything the iteration enqueued (in the
+        // slab-resident form its last contraction is already there), beside the next
+        // iteration; with persistent sweeps (grid barriers that need every block resident) it
+        // stays on the handle's stream
+        cudaStream_t fs = h->use_persistent ? h->stream : h->aux_stream;
+        if (fs != h->stream) {
+            UL_CK(h, cudaEventRecord(h->ev_main, h->stream));
+            UL_CK(h, cudaStreamWaitEvent(fs, h->ev_main, 0));
+        }
+        cudaError_t e = ul::launch_fold_level2_fields(g, tau1, tau2, r_max, nd, n2, asum2[p], bsum2[p], asum1, bsum1,
+                                                      fs);
         if (e != cudaSuccess) return cuda_fail(h, e, "level-2 fold launch");
+        UL_CK(h, cudaEventRecord(h->ev_fold[p], fs));
         h->launches += 1;
     }
+    UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_fold[(n1 - 1) & 1], 0));
     cudaError_t e = ul::launch_ml_reduce(g, tau1, n1, r_max, nd, asum1, bsum1, nullptr, partials, dout, h->stream);
     if (e == cudaSuccess)
         e = ul::launch_ml_vacuum(S2 * g.L3, osum, 8, static_cast<double>(n1) * n2 * static_cast<double>(g.V),

@@ -67,3 +67,45 @@ def test_two_level_fields_rejects_multihit_and_bad_arguments():
         g.multilevel2_fields(4, 1, 2, 1, 3, 1)
     with pytest.raises(_lib.ULError):
         g.multilevel2_fields(4, 0, 2, 1, 1, 1)
+
+
+def _two_level(prec, mode, seed, chunk_mb=None, args=(4, 4, 2, 3, 3, 2)):
+    g = _lib.Lattice(8, 8, 1.0, seed, prec)
+    g.set_option("slab_resident", 1 if mode == "slab" else 0)
+    g.set_option("persistent", 1 if mode == "persistent" else 0)
+    g.set_option("graphs", 0 if mode == "direct" else 1)
+    if chunk_mb:
+        g.set_option("insertion_chunk_mb", chunk_mb)
+    g.sweep(1, 3)
+    r = g.multilevel2_fields(*args)
+    links = g.get_links()
+    g.close()
+    return r, links
+
+
+@pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
+def test_two_level_fields_every_launch_form_equal(prec):
+    """Four level-1 iterations: the level-2 accumulators alternate between two buffers and
+    each iteration's fold runs beside the next iteration (on the second stream, except with
+    persistent sweeps); every launch form gives the same bits."""
+    ref, ref_links = _two_level(prec, "graphs", 37)
+    for mode in ("slab", "direct", "persistent"):
+        r, links = _two_level(prec, mode, 37)
+        assert np.array_equal(links, ref_links), mode
+        for key in ("corr", "fields", "vac"):
+            assert np.array_equal(r[key], ref[key]), (mode, key)
+
+
+def test_two_level_fields_odd_chunk_count_matches_oracle():
+    """Three insertion chunks per level-1 iteration (insertion_chunk_mb = 1): the sample
+    buffers' parity changes from one iteration to the next; FP64 against the oracle."""
+    args = (4, 3, 2, 5, 3, 2)
+    for mode in ("slab", "graphs"):
+        r, links = _two_level(_lib.UL_FP64, mode, 41, chunk_mb=1, args=args)
+        c = O.Lattice(8, 8, 1.0, 41)
+        c.sweep(1, 3)
+        cr = c.multilevel2_fields(*args)
+        d = np.abs(np.remainder(links - c.theta + np.pi, 2 * np.pi) - np.pi)
+        assert d.max() == 0.0, mode
+        for key in ("corr", "fields", "vac"):
+            assert np.max(np.abs(np.asarray(r[key]) - np.asarray(cr[key]))) < OBS_TOL, (mode, key)
