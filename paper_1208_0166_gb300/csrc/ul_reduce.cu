@@ -264,6 +264,65 @@ __global__ void __launch_bounds__(kT) fold_level2_fields_kernel(int L3, int S1, 
         }
 }
 
+// The same fold for a compile-time number M of level-2 slabs per level-1 slab: the weights
+// W_j = (1/n2) prod_{j' != j} A2(j') are formed once per (s1, r, x0) in registers, and a
+// term of the field sums is four FP64 fused multiply-adds, B_j W_j (the sample mean of B
+// folded into W).  The correlator product is formed exactly as in the generic kernel.
+template <int M>
+__global__ void __launch_bounds__(kT) fold_level2_fields_m_kernel(int L3, int S1, int r_max, int nd, int n2,
+                                                                  const double2* __restrict__ asum2,
+                                                                  const double2* __restrict__ bsum2,
+                                                                  double2* __restrict__ asum1,
+                                                                  double2* __restrict__ bsum1)
+{
+    const long k = static_cast<long>(blockIdx.x) * kT + threadIdx.x;
+    const long total = static_cast<long>(S1) * r_max * L3;
+    if (k >= total) return;
+    const int x0 = static_cast<int>(k % L3);
+    const long sr = k / L3;
+    const int r = static_cast<int>(sr % r_max);
+    const int s1 = static_cast<int>(sr / r_max);
+    const double n = 1.0 / static_cast<double>(n2);
+    Cx<double> A[M];
+    Cx<double> prod{1.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        A[j] = mean_of(asum2[(static_cast<long>(s1 * M + j) * r_max + r) * L3 + x0], n);
+        prod = cmul(prod, A[j]);
+    }
+    double2 a = asum1[k];
+    a.x += prod.re;
+    a.y += prod.im;
+    asum1[k] = a;
+    Cx<double> W[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        Cx<double> w{n, 0.0};
+#pragma unroll
+        for (int j2 = 0; j2 < M; ++j2)
+            if (j2 != j) w = cmul(w, A[j2]);
+        W[j] = w;
+    }
+    for (int d = 0; d < nd; ++d) {
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+            double br = 0.0, bi = 0.0;
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const long i2 = ((static_cast<long>(s1 * M + j) * r_max + r) * nd + d) * 8 + ch;
+                const double2 B = bsum2[i2 * L3 + x0];
+                br = fma(B.x, W[j].re, fma(-B.y, W[j].im, br));
+                bi = fma(B.x, W[j].im, fma(B.y, W[j].re, bi));
+            }
+            const long i1 = ((static_cast<long>(s1) * r_max + r) * nd + d) * 8 + ch;
+            double2 v = bsum1[i1 * L3 + x0];
+            v.x += br;
+            v.y += bi;
+            bsum1[i1 * L3 + x0] = v;
+        }
+    }
+}
+
 } // namespace
 
 cudaError_t launch_fold_level2_fields(const Geo& g, int tau1, int tau2, int r_max, int nd, int n2,
@@ -273,8 +332,15 @@ cudaError_t launch_fold_level2_fields(const Geo& g, int tau1, int tau2, int r_ma
     const int S1 = g.Nt / tau1, m = tau1 / tau2;
     if (m > kMaxFoldM) return cudaErrorInvalidValue;
     const long total = static_cast<long>(S1) * r_max * g.L3;
-    fold_level2_fields_kernel<<<static_cast<int>((total + kT - 1) / kT), kT, 0, st>>>(g.L3, S1, m, r_max, nd, n2,
-                                                                                      asum2, bsum2, asum1, bsum1);
+    const int nb = static_cast<int>((total + kT - 1) / kT);
+    switch (m) {
+    case 1: fold_level2_fields_m_kernel<1><<<nb, kT, 0, st>>>(g.L3, S1, r_max, nd, n2, asum2, bsum2, asum1, bsum1); break;
+    case 2: fold_level2_fields_m_kernel<2><<<nb, kT, 0, st>>>(g.L3, S1, r_max, nd, n2, asum2, bsum2, asum1, bsum1); break;
+    case 4: fold_level2_fields_m_kernel<4><<<nb, kT, 0, st>>>(g.L3, S1, r_max, nd, n2, asum2, bsum2, asum1, bsum1); break;
+    default:
+        fold_level2_fields_kernel<<<nb, kT, 0, st>>>(g.L3, S1, m, r_max, nd, n2, asum2, bsum2, asum1, bsum1);
+        break;
+    }
     return cudaGetLastError();
 }
 
