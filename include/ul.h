@@ -265,10 +265,10 @@ int ul_free(ul_lattice* h);
  *   "slab_cluster" CTAs per slab in the slab-resident form (a divisor of L, at most 16;
  *                  0, the default: the most CTAs up to 8 that keep every slab resident).
  *                  A size whose slab share does not fit falls back to one launch per class.
- *   "insertion_chunk_mb"  bound (MiB, default 4096) on the two buffers that hold the
+ *   "insertion_chunk_mb"  bound (MiB, default 16384) on the buffers that hold the
  *                  per-sample transporters and channel sums between insertion contractions
- *                  (a level is contracted in chunks of a quarter of its sub-samples, smaller
- *                  where the bound requires; in the slab-resident form one chunk's
+ *                  (a level is contracted in chunks of a quarter of its sub-samples but at
+ *                  least 48, smaller where the bound requires; in the slab-resident form one chunk's
  *                  contraction overlaps the next chunk's updates); fewer MiB means more,
  *                  smaller contractions (results change only by rounding)
  *   "contract_tiled"  1 (default): for UL_FP32_ACC64 the insertion contraction runs in a
