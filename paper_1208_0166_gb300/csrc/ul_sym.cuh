@@ -29,6 +29,20 @@ __device__ __forceinline__ int sym_shift(int L, int x0, int a, int n)
     return c[0] + L * (c[1] + L * c[2]);
 }
 
+// Spatial coordinates of a site, moved along one axis without integer division.
+struct SymSite {
+    int c1, c2, c3; // coordinates along the spatial axes 1, 2, 3 (x, y, z)
+    __device__ __forceinline__ SymSite moved(int L, int axis, int n) const // |n| < L
+    {
+        SymSite q = *this;
+        int& v = axis == 1 ? q.c1 : (axis == 2 ? q.c2 : q.c3);
+        v += n;
+        v = v >= L ? v - L : (v < 0 ? v + L : v);
+        return q;
+    }
+    __device__ __forceinline__ int lex(int L) const { return c1 + L * (c2 + L * c3); }
+};
+
 // Measurement after one sub-sample, thread per (s, x0):
 //   T_a(s, x0, r) = W*(s, x0) W(s, x0 + r e_a)  (W the slab line),
 //   asum3[(a-1) nA + (s R + r-1) L3 + x0] += T,  tk3[(((slot*3 + a-1) S + s) R + r-1) L3 + x0] = T,
@@ -48,9 +62,10 @@ __global__ void __launch_bounds__(kThreads)
     const int t0 = s * slab_t;
     const long nA = static_cast<long>(S) * r_max * g.L3;
     const Cx<R> w0 = cconj(slab_line<R>(g, cs, x0, t0, slab_t));
+    const SymSite p0{x0 % g.L, (x0 / g.L) % g.L, x0 / (g.L * g.L)};
     for (int a = 1; a <= 3; ++a)
         for (int r = 1; r <= r_max; ++r) {
-            const Cx<R> T = cmul_rn(w0, slab_line<R>(g, cs, sym_shift(g.L, x0, a, r), t0, slab_t));
+            const Cx<R> T = cmul_rn(w0, slab_line<R>(g, cs, p0.moved(g.L, a, r).lex(g.L), t0, slab_t));
             const long ai = (a - 1) * nA + static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0;
             double2 av = asum3[ai];
             av.x += static_cast<double>(T.re);
@@ -108,6 +123,7 @@ __global__ void __launch_bounds__(kThreads)
     const int d = static_cast<int>(rest % nd);
     const int s = static_cast<int>(rest / nd);
     const int L = g.L;
+    const SymSite pm{m % L, (m / L) % L, m / (L * L)};
     const int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
     const long SL3 = static_cast<long>(S) * g.L3;
     const R* O = o12 + static_cast<long>(s) * g.L3; // channel ch of site y: O[ch SL3 + y]
@@ -123,8 +139,9 @@ __global__ void __launch_bounds__(kThreads)
         const R ori = b < c ? R(1) : R(-1); // Im of P_{bc} = ori Im of the stored plane
 #pragma unroll
         for (int sbi = 0; sbi < 2; ++sbi) {
-            const int y = sym_shift(L, m, b, sbi == 0 ? d : -d);
-            const int yb = sym_shift(L, y, b, -1), yc = sym_shift(L, y, c, -1), ybc = sym_shift(L, yb, c, -1);
+            const SymSite py = pm.moved(L, b, sbi == 0 ? d : -d);
+            const SymSite pyb = py.moved(L, b, -1);
+            const int y = py.lex(L), yb = pyb.lex(L), yc = py.moved(L, c, -1).lex(L), ybc = pyb.moved(L, c, -1).lex(L);
 #pragma unroll
             for (int sci = 0; sci < 2; ++sci) {
                 // (0, +a)
