@@ -807,13 +807,12 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
     double* partials = reinterpret_cast<double*>(base + off_p);
     double* dout = reinterpret_cast<double*>(base + off_out);
     UL_CK(h, cudaMemsetAsync(asum3, 0, 3 * n_a * sizeof(double2), h->stream));
-    UL_CK(h, cudaMemsetAsync(bsum3, 0, 3 * n_b * sizeof(double2), h->stream));
     UL_CK(h, cudaMemsetAsync(osum12, 0, n_o * sizeof(double), h->stream));
 
     for (int k = 0; k < n_sub;) {
         const int count = std::min(chunk, n_sub - k);
         const int sm = h->sub_metro, so = h->sub_or;
-        const std::vector<long long> key = {kGraphSym, slab_t, sm, so, r_max, nd, count,
+        const std::vector<long long> key = {kGraphSym, slab_t, sm, so, r_max, nd, count, k == 0 ? 1 : 0,
                                             bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
                                             reinterpret_cast<long long>(asum3), reinterpret_cast<long long>(bsum3),
                                             reinterpret_cast<long long>(osum12), reinterpret_cast<long long>(tk3),
@@ -831,8 +830,10 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
                 n += 2;
             }
             cudaError_t e = is_f64(h)
-                ? ul::launch_insertion_contract_sym<double>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, st)
-                : ul::launch_insertion_contract_sym<float>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, st);
+                ? ul::launch_insertion_contract_sym<double>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, k == 0, st,
+                                                            h->contract_tiled, h->d_status)
+                : ul::launch_insertion_contract_sym<float>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, k == 0, st,
+                                                           h->contract_tiled, h->d_status);
             if (e != cudaSuccess) return cuda_fail(h, e, "symmetrised contraction launch");
             return n + 1;
         });

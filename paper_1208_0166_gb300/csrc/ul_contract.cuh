@@ -44,7 +44,7 @@ struct ContractTile {
 // L with many offsets): the untiled kernel runs instead.
 // The second transporter plane of a sample starts tpad floats after the first, so that
 // the two lanes of a pair hit different banks (its byte offset is 64 modulo 128).
-inline ContractTile contract_tile(const Geo& g, int r_max, int nd, int max_items, int max_smem)
+inline ContractTile contract_tile(const Geo& g, int r_max, int nd, int max_items, int max_smem, bool sym = false)
 {
     ContractTile t;
     const int L = g.L;
@@ -53,15 +53,18 @@ inline ContractTile contract_tile(const Geo& g, int r_max, int nd, int max_items
     t.ny = std::max(1, std::min(L, max_items / (per_row * t.ndb)));
     t.bs = kInsertionBlock;
     auto tpad = [&](int ny) { return ((64 - 8 * L * ny) % 128 + 128) % 128 / 4; };
+    // staged channel rows: the rows the offsets reach (single frame), or the tile's rows once
+    // per offset (24-frame sums, which are stored per offset)
+    auto rows_for = [&](int ny) { return sym ? ny * t.ndb : std::min(L, ny + t.ndb - 1); };
     auto smem_for = [&](int ny) {
-        const long rows = std::min(L, ny + t.ndb - 1);
+        const long rows = rows_for(ny);
         const long per_sample = (4L * L * ny + tpad(ny)) * sizeof(float) // T: (ra, rb) planes of L ny complex
                                 + rows * L * 8 * sizeof(float);          // O rows
         return 2 * t.bs * per_sample;
     };
     while (t.ny > 1 && smem_for(t.ny) > max_smem) --t.ny; // fewer y-rows per tile to fit
     t.tpad = tpad(t.ny);
-    t.rows = std::min(L, t.ny + t.ndb - 1);
+    t.rows = rows_for(t.ny);
     const int items = per_row * t.ny * t.ndb;
     t.threads = (items + 31) / 32 * 32;
     t.smem = static_cast<int>(smem_for(t.ny));
@@ -157,11 +160,14 @@ __device__ __forceinline__ void contract_sample(const float* t, const float* o, 
 // sample k0 + j): per sample the transporter rows of the tile for each separation and the
 // staged channel rows (two copies where the rows wrap past L - 1); lane 0 first announces
 // the batch's bytes on the buffer's barrier.
+// For the 24-frame sums (SYM) the channel part is one copy per offset d of the tile (ndv
+// offsets, o_ds floats apart in global memory, blk floats apart in shared memory).
+template <bool SYM>
 __device__ __forceinline__ void issue_batch(float* smem, unsigned long long* bars, int k0, int buf, int nb, int bufsz,
                                             int tsz, int osz, int o_at, int tplane, int nr,
                                             const Cx<float>* tsrc0, long t_db, long t_ks, unsigned int t_bytes,
                                             const float* osrc0, long o_ks, int row0, int n1, int rows, int L,
-                                            unsigned int o_bytes)
+                                            unsigned int o_bytes, int ndv, long o_ds, int blk)
 {
     float* base = smem + buf * bufsz;
     const int lane = static_cast<int>(threadIdx.x) & 31;
@@ -175,9 +181,13 @@ __device__ __forceinline__ void issue_batch(float* smem, unsigned long long* bar
         if (nr == 2) bulk_copy_g2s(base + j * tsz + tplane, ts + t_db, t_bytes, &bars[buf]);
         const float* os = osrc0 + k * o_ks;
         float* od = base + o_at + j * osz;
-        const unsigned int seg1 = static_cast<unsigned int>(n1 * L * 8 * sizeof(float));
-        bulk_copy_g2s(od, os + static_cast<long>(row0) * L * 8, seg1, &bars[buf]);
-        if (n1 < rows) bulk_copy_g2s(od + n1 * L * 8, os, o_bytes - seg1, &bars[buf]);
+        if constexpr (SYM) {
+            for (int q = 0; q < ndv; ++q) bulk_copy_g2s(od + q * blk, os + q * o_ds, o_bytes / ndv, &bars[buf]);
+        } else {
+            const unsigned int seg1 = static_cast<unsigned int>(n1 * L * 8 * sizeof(float));
+            bulk_copy_g2s(od, os + static_cast<long>(row0) * L * 8, seg1, &bars[buf]);
+            if (n1 < rows) bulk_copy_g2s(od + n1 * L * 8, os, o_bytes - seg1, &bars[buf]);
+        }
     }
 }
 
@@ -187,7 +197,11 @@ __device__ __forceinline__ void issue_batch(float* smem, unsigned long long* bar
 //   O[j][rl][x][ch],       rl < rows, x < L, ch < 8                  (8 rows L floats per sample)
 // The two lanes of a pair read the same O site (one access); eight lanes read four sites 32
 // bytes apart, one 128-byte line, so the 128-bit loads need no swizzle.
-template <typename R>
+// SYM: the 24-frame estimator.  Sites of one separation axis a are in that axis's
+// axis-major order (the midpoint shift runs along the rows, "x" below), the channel part is
+// the frame sums of each offset d of the tile (O[j][dl][y-row][x][ch], ny rows per offset),
+// tk and ok hold the three axes per sample, and the grid has the axis slowest.
+template <typename R, bool SYM>
 __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     insertion_contract_tiled_kernel(Geo g, int S, int r_max, int nd, int count, ContractTile t,
                                     const Cx<float>* __restrict__ tk, const float* __restrict__ ok,
@@ -197,8 +211,11 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     __shared__ unsigned long long bars[2];
     constexpr int BS = kInsertionBlock;
     const int L = g.L, L2 = g.L * g.L;
-    // block -> (s, pz, ytile, group, dsub), dsub fastest: the blocks of one plane run together
+    // block -> (axis, s, pz, ytile, group, dsub), dsub fastest: the blocks of one plane run together
     int b = static_cast<int>(blockIdx.x);
+    const int blocks_per_axis = S * L * t.ytiles * t.groups * t.dsubs;
+    const int ax = SYM ? b / blocks_per_axis : 0; // separation axis - 1
+    b -= ax * blocks_per_axis;
     const int dsub = b % t.dsubs;
     b /= t.dsubs;
     const int gi = b % t.groups;
@@ -225,17 +242,23 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     const int r = ri ? rb : ra;
     const bool active = item < L * t.ny * t.ndb && r != 0 && pyl < nyv && d0 + dl < nd;
     const int toff = ri * (2 * XT + t.tpad) + 2 * (px + L * pyl);         // transporter in a staged sample
-    const int ooff = (((pyl + dl) % L) * L + (px + r / 2) % L) * 8;      // shifted channel site
+    const int ooff = SYM ? ((dl * t.ny + pyl) * L + (px + r / 2) % L) * 8    // frame sums of offset dl
+                         : (((pyl + dl) % L) * L + (px + r / 2) % L) * 8; // shifted channel site
 
     // batch copies, issued by the lanes of warp 0 (lane j: sample j of the batch)
     const int n1 = min(t.rows, L - row0); // staged rows before the wrap to row 0
     const unsigned int t_bytes = static_cast<unsigned int>(nyv * L * sizeof(Cx<float>));
-    const unsigned int o_bytes = static_cast<unsigned int>(t.rows * L * 8 * sizeof(float));
-    const Cx<float>* tsrc0 = tk + (static_cast<long>(s) * r_max + (ra - 1)) * g.L3 + plane + static_cast<long>(L) * py0;
+    const int ndv = min(t.ndb, nd - d0); // offsets of this block (SYM)
+    const unsigned int o_bytes = static_cast<unsigned int>((SYM ? ndv * nyv : t.rows) * L * 8 * sizeof(float));
+    const int na = SYM ? 3 : 1;             // separation axes per stored sample
+    const long sa = static_cast<long>(ax) * S + s;
+    const Cx<float>* tsrc0 = tk + (sa * r_max + (ra - 1)) * g.L3 + plane + static_cast<long>(L) * py0;
     const long t_db = static_cast<long>(rb - ra) * g.L3;         // second separation's plane
-    const long t_ks = static_cast<long>(S) * r_max * g.L3;       // per sample (complex)
-    const float* osrc0 = ok + (static_cast<long>(s) * g.L3 + plane) * 8;
-    const long o_ks = static_cast<long>(S) * g.L3 * 8;           // per sample (floats)
+    const long t_ks = static_cast<long>(na) * S * r_max * g.L3;  // per sample (complex)
+    const float* osrc0 = SYM ? ok + ((sa * nd + d0) * g.L3 + plane + static_cast<long>(L) * py0) * 8
+                             : ok + (static_cast<long>(s) * g.L3 + plane) * 8;
+    const long o_ks = static_cast<long>(na) * S * (SYM ? nd : 1) * g.L3 * 8; // per sample (floats)
+    const long o_ds = static_cast<long>(g.L3) * 8;                          // per offset (SYM)
     const int tplane = 2 * XT + t.tpad;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -244,19 +267,22 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     }
     __syncthreads();
 
+    // this thread's outputs bsum[out + ch L3]
+    const long out = (((sa * r_max + (r - 1)) * nd + d0 + dl) * 8) * g.L3 + px + L * (py0 + pyl) + plane;
     InsertionAcc<float> acc[8];
     const int nbatch = (count + BS - 1) / BS;
     if (tid < 32)
-        issue_batch(smem, bars, 0, 0, min(BS, count), bufsz, tsz, osz, BS * tsz, tplane, nr, tsrc0, t_db, t_ks,
-                    t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes);
+        issue_batch<SYM>(smem, bars, 0, 0, min(BS, count), bufsz, tsz, osz, BS * tsz, tplane, nr, tsrc0, t_db, t_ks,
+                         t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes, ndv, o_ds, t.ny * L * 8);
     for (int bi = 0; bi < nbatch; ++bi) {
         const int buf = bi & 1;
         const int k0 = bi * BS;
         const int nb = min(BS, count - k0);
         // the other buffer was last read in batch bi - 1, which every thread has finished
         if (bi + 1 < nbatch && tid < 32)
-            issue_batch(smem, bars, k0 + BS, buf ^ 1, min(BS, count - k0 - BS), bufsz, tsz, osz, BS * tsz, tplane, nr,
-                        tsrc0, t_db, t_ks, t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes);
+            issue_batch<SYM>(smem, bars, k0 + BS, buf ^ 1, min(BS, count - k0 - BS), bufsz, tsz, osz, BS * tsz, tplane,
+                             nr, tsrc0, t_db, t_ks, t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes, ndv, o_ds,
+                             t.ny * L * 8);
         const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1);
         if (__syncthreads_or(!arrived)) {
             // a copy did not complete in time: report it, give the copies in flight a bounded
@@ -286,14 +312,12 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     if (!active) return;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
-    const int x0 = px + L * (py0 + pyl) + L2 * pz;
-    const long base = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d0 + dl) * 8) * g.L3 + x0;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
-        double2 v = first ? make_double2(0.0, 0.0) : bsum[base + ch * g.L3];
+        double2 v = first ? make_double2(0.0, 0.0) : bsum[out + ch * g.L3];
         v.x += acc[ch].total_re();
         v.y += acc[ch].total_im();
-        bsum[base + ch * g.L3] = v;
+        bsum[out + ch * g.L3] = v;
     }
 }
 
@@ -305,29 +329,37 @@ template <typename R>
 cudaError_t prepare_insertion_contract()
 {
     if constexpr (sizeof(R) == 4) {
-        const cudaError_t e = cudaFuncSetAttribute(insertion_contract_tiled_kernel<float>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
+        cudaError_t e = cudaFuncSetAttribute(insertion_contract_tiled_kernel<float, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(insertion_contract_tiled_kernel<float, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
         if (e == cudaSuccess) g_contract_prepared.store(true);
         return e;
     }
     return cudaSuccess;
 }
 
-// Launches the tiled form for FP32 links; returns false (nothing launched) where it does
-// not apply, and the caller runs the untiled kernel.
+// Launches the tiled form for FP32 links (sym: the 24-frame sums of three axes); returns
+// false (nothing launched) where it does not apply, and the caller runs the untiled kernel.
 template <typename R>
 bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
-                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err)
+                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err, bool sym)
 {
     if constexpr (sizeof(R) != 4) {
         return false;
     } else {
-        const ContractTile t = contract_tile(g, r_max, nd, kContractItems, kContractSmem);
+        const ContractTile t = contract_tile(g, r_max, nd, kContractItems, kContractSmem, sym);
         if (!t.ok || count < 1 || (t.smem > 48 * 1024 && !g_contract_prepared.load())) return false;
-        const long blocks = static_cast<long>(S) * g.L * t.ytiles * t.groups * t.dsubs;
-        insertion_contract_tiled_kernel<float><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
-            g, S, r_max, nd, count, t, static_cast<const Cx<float>*>(tk), static_cast<const float*>(ok), bsum, first,
-            status);
+        const long blocks = static_cast<long>(sym ? 3 : 1) * S * g.L * t.ytiles * t.groups * t.dsubs;
+        const auto* tkf = static_cast<const Cx<float>*>(tk);
+        const auto* okf = static_cast<const float*>(ok);
+        if (sym)
+            insertion_contract_tiled_kernel<float, true><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
+                g, S, r_max, nd, count, t, tkf, okf, bsum, first, status);
+        else
+            insertion_contract_tiled_kernel<float, false><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
+                g, S, r_max, nd, count, t, tkf, okf, bsum, first, status);
         *err = cudaGetLastError();
         return true;
     }

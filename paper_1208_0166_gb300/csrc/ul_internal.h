@@ -66,7 +66,8 @@ cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_m
                                void* tk3, void* o12, void* csym, double* osum12, cudaStream_t st);
 template <typename R>
 cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
-                                          const void* csym, double2* bsum3, cudaStream_t st);
+                                          const void* csym, double2* bsum3, bool first, cudaStream_t st, bool tiled,
+                                          int* status);
 
 // Multihit temporal links ubar[i] (lexicographic site i, complex in precision R).
 template <typename R>

@@ -1003,7 +1003,7 @@ cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* uba
 
 template <typename R>
 bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
-                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err);
+                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err, bool sym);
 
 template <typename R>
 cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
@@ -1012,7 +1012,8 @@ cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int n
 {
     const int S = g.Nt / slab_t;
     cudaError_t err = cudaSuccess;
-    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk, ok, bsum, first, status, st, &err)) return err;
+    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk, ok, bsum, first, status, st, &err, false))
+        return err;
     const long total = static_cast<long>(S) * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
         g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk), static_cast<const R*>(ok), bsum, first);
@@ -1091,7 +1092,7 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
     template cudaError_t launch_measure_sym<R>(const Geo&, const void*, int, int, int, int, double2*, void*,       \
                                                void*, void*, double*, cudaStream_t);                              \
     template cudaError_t launch_insertion_contract_sym<R>(const Geo&, int, int, int, int, const void*,             \
-                                                          const void*, double2*, cudaStream_t);                   \
+                                                          const void*, double2*, bool, cudaStream_t, bool, int*); \
     template cudaError_t launch_rng_uniforms<R>(uint64_t, uint64_t, uint64_t, int, double*, cudaStream_t);        \
     template cudaError_t slab_plan<R>(const Geo&, int, int, int*, int*);                                           \
     template cudaError_t launch_slab<R>(const Geo&, R*, void*, const SlabArgs&, int, cudaStream_t);               \

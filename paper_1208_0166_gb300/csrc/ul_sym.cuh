@@ -13,21 +13,19 @@
 // so the measurement stores the six planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3) once per site,
 // a second kernel sums every axis's 8 frames per insertion midpoint, and the contraction
 // multiplies those sums by the axis's transporters.
+//
+// Everything indexed by a site for one axis a (the accumulators asum3 / bsum3, the stored
+// transporters tk3 and the frame sums csym) uses the axis-major site order of a: position
+// along e_a fastest, then the other two axes in increasing order.  The midpoint shift
+// x0 + floor(r/2) e_a then stays inside a row of L consecutive entries, as the shift along
+// x does for the single-frame estimator; the reduction over x0 takes the entries in this
+// order.  The frame sums of a midpoint are stored as 8 consecutive channels.
 #pragma once
 
 namespace ul {
 
 __device__ __constant__ static const int kSymPlaneMu[6] = {0, 0, 0, 1, 1, 2};
 __device__ __constant__ static const int kSymPlaneNu[6] = {1, 2, 3, 2, 3, 3};
-
-// Spatial lexicographic index of x0 moved by n (any sign) along spatial axis a.
-__device__ __forceinline__ int sym_shift(int L, int x0, int a, int n)
-{
-    int c[3] = {x0 % L, (x0 / L) % L, x0 / (L * L)};
-    int v = (c[a - 1] + n) % L;
-    c[a - 1] = v < 0 ? v + L : v;
-    return c[0] + L * (c[1] + L * c[2]);
-}
 
 // Spatial coordinates of a site, moved along one axis without integer division.
 struct SymSite {
@@ -41,11 +39,32 @@ struct SymSite {
         return q;
     }
     __device__ __forceinline__ int lex(int L) const { return c1 + L * (c2 + L * c3); }
+    // index in the axis-major order of axis a
+    __device__ __forceinline__ int axis_major(int L, int a) const
+    {
+        return a == 1 ? c1 + L * (c2 + L * c3) : (a == 2 ? c2 + L * (c1 + L * c3) : c3 + L * (c1 + L * c2));
+    }
+    // the site at index i of the axis-major order of axis a
+    static __device__ __forceinline__ SymSite from_axis_major(int L, int a, int i)
+    {
+        const int u = i % L, v = (i / L) % L, w = i / (L * L);
+        return a == 1 ? SymSite{u, v, w} : (a == 2 ? SymSite{v, u, w} : SymSite{v, w, u});
+    }
 };
 
-// Measurement after one sub-sample, thread per (s, x0):
+// Index reached from axis-major index i of axis a by n (0 <= n < L) steps along e_a.
+__device__ __forceinline__ int axis_major_step(int L, int i, int n)
+{
+    const int u = i % L;
+    const int v = u + n;
+    return i - u + (v >= L ? v - L : v);
+}
+
+// Measurement after one sub-sample, one launch of 4 S L3 threads:
+// threads [0, 3 S L3), one per (a, s, i) with i the axis-major index of site x0:
 //   T_a(s, x0, r) = W*(s, x0) W(s, x0 + r e_a)  (W the slab line),
-//   asum3[(a-1) nA + (s R + r-1) L3 + x0] += T,  tk3[(((slot*3 + a-1) S + s) R + r-1) L3 + x0] = T,
+//   asum3[(a-1) nA + (s R + r-1) L3 + i] += T,  tk3[(((slot*3 + a-1) S + s) R + r-1) L3 + i] = T;
+// threads [3 S L3, 4 S L3), one per (s, x0) in lexicographic order:
 //   O(s, x0, 2p + part) = sum_{t in slab} {Im, Re} P_p(x0, t)  (the six planes p),
 //   o12[ch SL3 + s L3 + x0] = O (this sample only),  osum12[ch SL3 + s L3 + x0] += O.
 template <typename R>
@@ -55,24 +74,33 @@ __global__ void __launch_bounds__(kThreads)
                        double* __restrict__ osum12)
 {
     const int S = g.Nt / slab_t;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + x0
-    if (k >= S * g.L3) return;
-    const int s = k / g.L3;
-    const int x0 = k - s * g.L3;
-    const int t0 = s * slab_t;
-    const long nA = static_cast<long>(S) * r_max * g.L3;
-    const Cx<R> w0 = cconj(slab_line<R>(g, cs, x0, t0, slab_t));
-    const SymSite p0{x0 % g.L, (x0 / g.L) % g.L, x0 / (g.L * g.L)};
-    for (int a = 1; a <= 3; ++a)
+    const long SL3 = static_cast<long>(S) * g.L3;
+    long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= 4 * SL3) return;
+    if (idx < 3 * SL3) {
+        const int a = static_cast<int>(idx / SL3) + 1;
+        const long rem = idx - (a - 1) * SL3;
+        const int s = static_cast<int>(rem / g.L3);
+        const int i = static_cast<int>(rem - static_cast<long>(s) * g.L3);
+        const int t0 = s * slab_t;
+        const SymSite p0 = SymSite::from_axis_major(g.L, a, i);
+        const Cx<R> w0 = cconj(slab_line<R>(g, cs, p0.lex(g.L), t0, slab_t));
+        const long nA = SL3 * r_max;
         for (int r = 1; r <= r_max; ++r) {
             const Cx<R> T = cmul_rn(w0, slab_line<R>(g, cs, p0.moved(g.L, a, r).lex(g.L), t0, slab_t));
-            const long ai = (a - 1) * nA + static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0;
+            const long ai = (a - 1) * nA + static_cast<long>(s * r_max + (r - 1)) * g.L3 + i;
             double2 av = asum3[ai];
             av.x += static_cast<double>(T.re);
             av.y += static_cast<double>(T.im);
             asum3[ai] = av;
-            tk3[((static_cast<long>(slot * 3 + a - 1) * S + s) * r_max + (r - 1)) * g.L3 + x0] = T;
+            tk3[((static_cast<long>(slot * 3 + a - 1) * S + s) * r_max + (r - 1)) * g.L3 + i] = T;
         }
+        return;
+    }
+    const int k = static_cast<int>(idx - 3 * SL3); // s*L3 + x0
+    const int s = k / g.L3;
+    const int x0 = k - s * g.L3;
+    const int t0 = s * slab_t;
     R acc[12];
 #pragma unroll
     for (int ch = 0; ch < 12; ++ch) acc[ch] = R(0);
@@ -89,7 +117,6 @@ __global__ void __launch_bounds__(kThreads)
             acc[2 * p + 1] += P.re;
         }
     }
-    const long SL3 = static_cast<long>(S) * g.L3;
 #pragma unroll
     for (int ch = 0; ch < 12; ++ch) {
         o12[ch * SL3 + k] = acc[ch];
@@ -103,10 +130,12 @@ __device__ __forceinline__ int sym_plane(int mu, int nu)
     return mu == 0 ? nu - 1 : (mu == 1 ? (nu == 2 ? 3 : 4) : 5);
 }
 
-// Frame sums of one sub-sample, thread per (a, s, d, m), m fastest: the 8 frames (b, c, sb,
-// sc) of axis a put their channels at y = m + d sb e_b; their sum does not depend on how the
-// midpoint m = x0 + floor(r/2) e_a was reached, so it is formed once per (a, s, d, m):
-//   csym[((((slot*3 + a-1) S + s) nd + d) 8 + ch) L3 + m] = sum over the frames of channel ch,
+// Frame sums of one sub-sample, thread per (a, s, d, m), m fastest in lexicographic order (the
+// channel loads of neighbouring threads are neighbours); the 8 frames (b, c, sb, sc) of axis a
+// put their channels at y = m + d sb e_b; their sum does not depend on how the midpoint
+// m = x0 + floor(r/2) e_a was reached, so it is formed once per (a, s, d, m) and stored at
+// the axis-major index i(m) of a as 8 consecutive channels (one 32-byte sector in FP32):
+//   csym[(((((slot*3 + a-1) S + s) nd + d) L3 + i(m)) 8 + ch] = sum over the frames of channel ch,
 // the frames taken in the order (b, c) = (o1, o2), (o2, o1) (o1 < o2 the axes other than a),
 // sb = +, -, sc = +, -, summed in precision R.
 template <typename R>
@@ -124,6 +153,7 @@ __global__ void __launch_bounds__(kThreads)
     const int s = static_cast<int>(rest / nd);
     const int L = g.L;
     const SymSite pm{m % L, (m / L) % L, m / (L * L)};
+    const int i = pm.axis_major(L, a);
     const int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
     const long SL3 = static_cast<long>(S) * g.L3;
     const R* O = o12 + static_cast<long>(s) * g.L3; // channel ch of site y: O[ch SL3 + y]
@@ -171,19 +201,21 @@ __global__ void __launch_bounds__(kThreads)
             }
         }
     }
-    R* out = csym + ((static_cast<long>(slot * 3 + a - 1) * S + s) * nd + d) * 8 * g.L3 + m;
+    R* out = csym + (((static_cast<long>(slot * 3 + a - 1) * S + s) * nd + d) * g.L3 + i) * 8;
 #pragma unroll
-    for (int ch = 0; ch < 8; ++ch) out[ch * g.L3] = C[ch];
+    for (int ch = 0; ch < 8; ++ch) out[ch] = C[ch];
 }
 
-// Symmetrised contraction over the `count` stored samples, m = x0 + floor(r/2) e_a:
+// Symmetrised contraction over the `count` stored samples, m = x0 + floor(r/2) e_a, sites in
+// the axis-major order of a:
 //   bsum3[(a-1) nB + (((s R + r-1) nd + d) 8 + ch) L3 + x0] += sum_k T_a,k(s, x0, r) csym_k(a, s, d, m, ch),
 // thread per output (a, s, r, d, x0) summing over k in order, blocks ordered as in
-// insertion_contract_kernel (a tile of x0 for all (r, d) together).
+// insertion_contract_kernel (a tile of x0 for all (r, d) together); with `first` (the
+// level's first chunk) bsum3 is written, not read.
 template <typename R>
 __global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     insertion_contract_sym_kernel(Geo g, int S, int r_max, int nd, int count, const Cx<R>* __restrict__ tk3,
-                                  const R* __restrict__ csym, double2* __restrict__ bsum3)
+                                  const R* __restrict__ csym, double2* __restrict__ bsum3, bool first)
 {
     const long per_axis = static_cast<long>(S) * r_max * nd * g.L3;
     const int tiles = (g.L3 + kThreads - 1) / kThreads;
@@ -198,13 +230,14 @@ __global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     const int a = b / S + 1;
     const int x0 = tile * kThreads + static_cast<int>(threadIdx.x);
     if (x0 >= g.L3) return;
-    const int m = sym_shift(g.L, x0, a, r / 2);
+    const int m = axis_major_step(g.L, x0, r / 2);
     InsertionAcc<R> acc[8];
     for (int k = 0; k < count; ++k) {
         const Cx<R> T = tk3[((static_cast<long>(k * 3 + a - 1) * S + s) * r_max + (r - 1)) * g.L3 + x0];
-        const R* C = csym + ((static_cast<long>(k * 3 + a - 1) * S + s) * nd + d) * 8 * g.L3 + m;
+        R C[8];
+        Vec8<R>::load(csym + (((static_cast<long>(k * 3 + a - 1) * S + s) * nd + d) * g.L3 + m) * 8, C);
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, C[ch * g.L3]);
+        for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, C[ch]);
         if (k % kInsertionBlock == kInsertionBlock - 1)
 #pragma unroll
             for (int ch = 0; ch < 8; ++ch) acc[ch].fold();
@@ -214,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     const long base = (a - 1) * (per_axis * 8) + (((static_cast<long>(s) * r_max + (r - 1)) * nd + d) * 8) * g.L3 + x0;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
-        double2 bv = bsum3[base + ch * g.L3];
+        double2 bv = first ? make_double2(0.0, 0.0) : bsum3[base + ch * g.L3];
         bv.x += acc[ch].total_re();
         bv.y += acc[ch].total_im();
         bsum3[base + ch * g.L3] = bv;
@@ -226,7 +259,7 @@ cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_m
                                void* tk3, void* o12, void* csym, double* osum12, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
-    measure_sym_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
+    measure_sym_kernel<R><<<blocks_for(4L * S * g.L3), kThreads, 0, st>>>(
         g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, slot, asum3, static_cast<Cx<R>*>(tk3),
         static_cast<R*>(o12), osum12);
     combine_sym_kernel<R><<<blocks_for(3L * S * nd * g.L3), kThreads, 0, st>>>(
@@ -236,12 +269,16 @@ cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_m
 
 template <typename R>
 cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
-                                          const void* csym, double2* bsum3, cudaStream_t st)
+                                          const void* csym, double2* bsum3, bool first, cudaStream_t st, bool tiled,
+                                          int* status)
 {
     const int S = g.Nt / slab_t;
+    cudaError_t err = cudaSuccess;
+    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk3, csym, bsum3, first, status, st, &err, true))
+        return err;
     const long total = 3L * S * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_sym_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
-        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk3), static_cast<const R*>(csym), bsum3);
+        g, S, r_max, nd, count, static_cast<const Cx<R>*>(tk3), static_cast<const R*>(csym), bsum3, first);
     return cudaGetLastError();
 }
 

@@ -99,3 +99,38 @@ def test_symmetrised_rejects_multihit_and_bad_arguments():
         g.multilevel_fields_sym(2, 1, 3, 1)
     with pytest.raises(_lib.ULError):
         g.multilevel_fields_sym(2, 1, 1, 4)
+
+
+def _sym_level(L, Nt, tau, n_sub, r_max, d_max, tiled, chunk_mb=None, seed=83):
+    g = _lib.Lattice(L, Nt, 1.0, seed, _lib.UL_FP32_ACC64)
+    g.set_option("contract_tiled", tiled)
+    if chunk_mb:
+        g.set_option("insertion_chunk_mb", chunk_mb)
+    g.sweep(1, 3)
+    r = g.multilevel_fields_sym(tau, n_sub, r_max, d_max)
+    g.close()
+    return r
+
+
+@pytest.mark.parametrize("L,Nt,tau,n_sub,r_max,d_max", [
+    (2, 2, 1, 3, 1, 1),
+    (4, 4, 2, 9, 2, 3),
+    (6, 4, 2, 5, 3, 5),     # odd r_max: separation 1 alone
+    (8, 4, 2, 3, 4, 7),
+    (12, 2, 1, 2, 6, 11),   # offsets in several blocks
+    (24, 2, 2, 2, 8, 6),    # the benchmark's tile
+])
+def test_symmetrised_tiled_contraction_equals_untiled(L, Nt, tau, n_sub, r_max, d_max):
+    """The 24-frame contraction in the tiled form (sites of each axis in its axis-major
+    order, the frame sums of each offset staged per tile) gives the untiled kernel's bits."""
+    a = _sym_level(L, Nt, tau, n_sub, r_max, d_max, 1)
+    b = _sym_level(L, Nt, tau, n_sub, r_max, d_max, 0)
+    for key in ("corr", "fields", "vac"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_symmetrised_tiled_contraction_several_chunks():
+    a = _sym_level(8, 8, 2, 11, 3, 4, 1, chunk_mb=8)
+    b = _sym_level(8, 8, 2, 11, 3, 4, 0, chunk_mb=8)
+    for key in ("corr", "fields", "vac"):
+        assert np.array_equal(a[key], b[key]), key
