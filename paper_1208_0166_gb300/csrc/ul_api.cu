@@ -808,11 +808,20 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
     double* dout = reinterpret_cast<double*>(base + off_out);
     UL_CK(h, cudaMemsetAsync(asum3, 0, 3 * n_a * sizeof(double2), h->stream));
     UL_CK(h, cudaMemsetAsync(osum12, 0, n_o * sizeof(double), h->stream));
+    // the sub-sample passes in the slab-resident form where it applies (one cluster launch per
+    // sub-sample without its own measurement), else one launch per class
+    int slab_cl = 0, slab_threads = 0;
+    if (h->slab_mode && !h->use_persistent) {
+        cudaError_t e = is_f64(h) ? ul::slab_plan<double>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads)
+                                  : ul::slab_plan<float>(g, slab_t, h->slab_cluster, &slab_cl, &slab_threads);
+        if (e != cudaSuccess) return cuda_fail(h, e, "slab plan");
+    }
 
     for (int k = 0; k < n_sub;) {
         const int count = std::min(chunk, n_sub - k);
         const int sm = h->sub_metro, so = h->sub_or;
-        const std::vector<long long> key = {kGraphSym, slab_t, sm, so, r_max, nd, count, k == 0 ? 1 : 0,
+        const std::vector<long long> key = {kGraphSym, slab_t, sm, so, r_max, nd, count, k == 0 ? 1 : 0, slab_cl,
+                                            slab_threads,
                                             bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
                                             reinterpret_cast<long long>(asum3), reinterpret_cast<long long>(bsum3),
                                             reinterpret_cast<long long>(osum12), reinterpret_cast<long long>(tk3),
@@ -820,9 +829,28 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
         rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* pb) -> long {
             long n = 0;
             for (int j = 0; j < count; ++j) {
-                const long m = enqueue_passes(h, st, sm, so, slab_t, first + static_cast<uint64_t>(j) * sm, pb);
-                if (m < 0) return m;
-                n += m;
+                if (slab_cl) {
+                    ul::SlabArgs a{};
+                    a.u = persist_args(h, 1, sm, so, slab_t).u;
+                    a.u.pass = first + static_cast<uint64_t>(j) * sm;
+                    a.u.pass_base = pb;
+                    a.n_units = 1;
+                    a.n_metro = sm;
+                    a.n_or = so;
+                    a.cluster = slab_cl;
+                    a.nz = g.L / slab_cl;
+                    a.skip_measure = 1;
+                    cudaError_t e =
+                        is_f64(h)
+                            ? ul::launch_slab<double>(g, static_cast<double*>(h->theta), h->cs, a, slab_threads, st)
+                            : ul::launch_slab<float>(g, static_cast<float*>(h->theta), h->cs, a, slab_threads, st);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "slab-resident launch");
+                    n += 1;
+                } else {
+                    const long m = enqueue_passes(h, st, sm, so, slab_t, first + static_cast<uint64_t>(j) * sm, pb);
+                    if (m < 0) return m;
+                    n += m;
+                }
                 cudaError_t e = is_f64(h)
                     ? ul::launch_measure_sym<double>(g, h->cs, slab_t, r_max, nd, j, asum3, tk3, o12, csym, osum12, st)
                     : ul::launch_measure_sym<float>(g, h->cs, slab_t, r_max, nd, j, asum3, tk3, o12, csym, osum12, st);

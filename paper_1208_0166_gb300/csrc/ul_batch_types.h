@@ -44,6 +44,7 @@ struct SlabArgs {
     int n_metro, n_or;        // passes per sub-sample
     int cluster, nz;          // CTAs per slab (one cluster), z planes per CTA
     int r_max, fields, slot0; // measurement as in PersistArgs
+    int skip_measure;         // 1: passes only (the caller measures after the launch)
     double2* asum;
     void* tk;
     void* ok;

@@ -304,7 +304,9 @@ __global__ void __launch_bounds__(1024, 1) slab_kernel(Geo g, R* __restrict__ th
     }
     cl.sync();
 
-    uint64_t pass = a.u.pass;
+    // first Metropolis pass: an offset plus a device-side base where the launch is replayed
+    // from a CUDA graph (as for the one-class-per-launch kernel)
+    uint64_t pass = a.u.pass + (a.u.pass_base ? *a.u.pass_base : 0ull);
     for (int unit = 0; unit < a.n_units; ++unit) {
         for (int k = 0; k < a.n_metro + a.n_or; ++k) {
             const bool metro = k < a.n_metro;
@@ -329,8 +331,10 @@ __global__ void __launch_bounds__(1024, 1) slab_kernel(Geo g, R* __restrict__ th
             }
             if (metro) pass += 1;
         }
-        slab_measure<R, LC>(S, g, L, z0, t0, s, a.slot0 + unit, a);
-        cl.sync(); // the next updates may change links that other CTAs just measured
+        if (!a.skip_measure) {
+            slab_measure<R, LC>(S, g, L, z0, t0, s, a.slot0 + unit, a);
+            cl.sync(); // the next updates may change links that other CTAs just measured
+        }
     }
 
     for (int e = tid; e < NT * P; e += nthr) {

@@ -134,3 +134,27 @@ def test_symmetrised_tiled_contraction_several_chunks():
     b = _sym_level(8, 8, 2, 11, 3, 4, 0, chunk_mb=8)
     for key in ("corr", "fields", "vac"):
         assert np.array_equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_symmetrised_slab_resident_passes_equal_per_class(prec, graphs):
+    """The sub-sample passes of the 24-frame estimator as one slab-resident launch per
+    sub-sample (measurement skipped inside, the 24-frame measurement after it): links,
+    acceptance counts and observables equal those of the one-launch-per-class form."""
+    out = []
+    for slab in (1, 0):
+        g = _lib.Lattice(8, 8, 1.0, 89, prec)
+        g.set_option("slab_resident", slab)
+        g.set_option("graphs", graphs)
+        g.sweep(1, 3)
+        n0 = g.launch_count()
+        r = g.multilevel_fields_sym(2, 5, 3, 2)
+        r2 = g.multilevel_fields_sym(2, 3, 3, 2)  # replayed graphs: later Metropolis passes
+        out.append((g.get_links(), g.stats(), r, r2, g.launch_count() - n0))
+        g.close()
+    assert out[0][4] < out[1][4], "the slab-resident form did not run"
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    for key in ("corr", "fields", "vac"):
+        assert np.array_equal(out[0][2][key], out[1][2][key]), key
+        assert np.array_equal(out[0][3][key], out[1][3][key]), key
