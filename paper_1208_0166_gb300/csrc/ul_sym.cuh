@@ -138,27 +138,13 @@ __device__ __forceinline__ int sym_plane(int mu, int nu)
 //   csym[(((((slot*3 + a-1) S + s) nd + d) L3 + i(m)) 8 + ch] = sum over the frames of channel ch,
 // the frames taken in the order (b, c) = (o1, o2), (o2, o1) (o1 < o2 the axes other than a),
 // sb = +, -, sc = +, -, summed in precision R.
+// The 8 channel sums over the frames of axis a at midpoint pm and offset d (channel ch of site
+// y of the slab: O[ch SL3 + y]), in the order stated above.
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-    combine_sym_kernel(Geo g, int S, int nd, int slot, const R* __restrict__ o12, R* __restrict__ csym)
+__device__ __forceinline__ void frame_sums(int L, long SL3, const R* __restrict__ O, int a, int d, SymSite pm, R C[8])
 {
-    const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const long per_axis = static_cast<long>(S) * nd * g.L3;
-    if (idx >= 3 * per_axis) return;
-    const int a = static_cast<int>(idx / per_axis) + 1;
-    long rest = idx - (a - 1) * per_axis;
-    const int m = static_cast<int>(rest % g.L3);
-    rest /= g.L3;
-    const int d = static_cast<int>(rest % nd);
-    const int s = static_cast<int>(rest / nd);
-    const int L = g.L;
-    const SymSite pm{m % L, (m / L) % L, m / (L * L)};
-    const int i = pm.axis_major(L, a);
     const int o1 = a == 1 ? 2 : 1, o2 = a == 3 ? 2 : 3;
-    const long SL3 = static_cast<long>(S) * g.L3;
-    const R* O = o12 + static_cast<long>(s) * g.L3; // channel ch of site y: O[ch SL3 + y]
     const int pa = a - 1;
-    R C[8];
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) C[ch] = R(0);
 #pragma unroll
@@ -201,9 +187,61 @@ __global__ void __launch_bounds__(kThreads)
             }
         }
     }
-    R* out = csym + (((static_cast<long>(slot * 3 + a - 1) * S + s) * nd + d) * g.L3 + i) * 8;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    combine_sym_kernel(Geo g, int S, int nd, int slot, const R* __restrict__ o12, R* __restrict__ csym)
+{
+    const long idx = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const long per_axis = static_cast<long>(S) * nd * g.L3;
+    if (idx >= 3 * per_axis) return;
+    const int a = static_cast<int>(idx / per_axis) + 1;
+    long rest = idx - (a - 1) * per_axis;
+    const int m = static_cast<int>(rest % g.L3);
+    rest /= g.L3;
+    const int d = static_cast<int>(rest % nd);
+    const int s = static_cast<int>(rest / nd);
+    const int L = g.L;
+    const SymSite pm{m % L, (m / L) % L, m / (L * L)};
+    R C[8];
+    frame_sums<R>(L, static_cast<long>(S) * g.L3, o12 + static_cast<long>(s) * g.L3, a, d, pm, C);
+    R* out = csym + (((static_cast<long>(slot * 3 + a - 1) * S + s) * nd + d) * g.L3 + pm.axis_major(L, a)) * 8;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) out[ch] = C[ch];
+}
+
+// The same frame sums, one block of L^2 threads per (a, s, d, plane): the plane holds the
+// axis-major indices [L^2 w, L^2 (w + 1)) of axis a (z = w for a = 1, 2; y = w for a = 3).
+// Thread t takes the site with x = t mod L (the channel loads of neighbouring threads are
+// neighbours) and v = t / L as its other in-plane coordinate (y for a = 1, the coordinate
+// along e_a for a = 2, 3); the block stages the plane's sums in shared memory in axis-major
+// order and writes them as one contiguous run of 8 L^2 values.
+template <typename R>
+__global__ void __launch_bounds__(1024)
+    combine_sym_plane_kernel(Geo g, int S, int nd, int slot, const R* __restrict__ o12, R* __restrict__ csym)
+{
+    extern __shared__ __align__(16) unsigned char tile_raw[];
+    R* tile = reinterpret_cast<R*>(tile_raw);
+    const int L = g.L, L2 = g.L * g.L;
+    int b = static_cast<int>(blockIdx.x); // ((a - 1) S + s) nd + d) L + w
+    const int w = b % L;
+    b /= L;
+    const int d = b % nd;
+    b /= nd;
+    const int s = b % S;
+    const int a = b / S + 1;
+    const int t = static_cast<int>(threadIdx.x);
+    const int x = t % L, v = t / L;
+    const SymSite pm = a == 3 ? SymSite{x, w, v} : SymSite{x, v, w};
+    const int il = a == 1 ? x + L * v : v + L * x; // axis-major index within the plane
+    R C[8];
+    frame_sums<R>(L, static_cast<long>(S) * g.L3, o12 + static_cast<long>(s) * g.L3, a, d, pm, C);
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) tile[il * 8 + ch] = C[ch];
+    __syncthreads();
+    R* out = csym + (((static_cast<long>(slot * 3 + a - 1) * S + s) * nd + d) * g.L3 + static_cast<long>(L2) * w) * 8;
+    for (int e = t; e < 8 * L2; e += blockDim.x) out[e] = tile[e];
 }
 
 // Symmetrised contraction over the `count` stored samples, m = x0 + floor(r/2) e_a, sites in
@@ -262,8 +300,13 @@ cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_m
     measure_sym_kernel<R><<<blocks_for(4L * S * g.L3), kThreads, 0, st>>>(
         g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, slot, asum3, static_cast<Cx<R>*>(tk3),
         static_cast<R*>(o12), osum12);
-    combine_sym_kernel<R><<<blocks_for(3L * S * nd * g.L3), kThreads, 0, st>>>(
-        g, S, nd, slot, static_cast<const R*>(o12), static_cast<R*>(csym));
+    const size_t tile_bytes = static_cast<size_t>(g.L) * g.L * 8 * sizeof(R);
+    if (g.L * g.L <= 1024 && tile_bytes <= 48 * 1024)
+        combine_sym_plane_kernel<R><<<static_cast<unsigned int>(3L * S * nd * g.L), g.L * g.L, tile_bytes, st>>>(
+            g, S, nd, slot, static_cast<const R*>(o12), static_cast<R*>(csym));
+    else
+        combine_sym_kernel<R><<<blocks_for(3L * S * nd * g.L3), kThreads, 0, st>>>(
+            g, S, nd, slot, static_cast<const R*>(o12), static_cast<R*>(csym));
     return cudaGetLastError();
 }
 
