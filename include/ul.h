@@ -15,11 +15,13 @@
  *     valid after an error (except UL_ENOMEM from ul_init, which sets *h = NULL).
  *   - The library owns all device memory and the handle; the caller owns every host
  *     buffer it passes (outputs are written before the call returns).
- *   - Calls on one handle are serialised on the handle's CUDA stream.  Calls that return
- *     results (ul_multilevel*, ul_plaquette, ul_get_*) block until the results are on
- *     the host.  ul_sweep and ul_set_state only enqueue work and return; an execution
- *     error of enqueued work is reported by the next blocking call.  Different handles
- *     may be used from different host threads.
+ *   - Calls on one handle are serialised on the handle's CUDA stream (the insertion
+ *     contractions and a begun level's reduction run on a second, library-owned stream,
+ *     ordered by events).  Calls that return results (ul_multilevel*, except
+ *     ul_multilevel_fields_begin, ul_plaquette, ul_get_*) block until the results are on
+ *     the host.  ul_sweep, ul_set_state and ul_multilevel_fields_begin only enqueue work
+ *     and return; an execution error of enqueued work is reported by the next blocking
+ *     call.  Different handles may be used from different host threads.
  */
 #ifndef UL_H
 #define UL_H
