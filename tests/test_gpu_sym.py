@@ -158,3 +158,37 @@ def test_symmetrised_slab_resident_passes_equal_per_class(prec, graphs):
     for key in ("corr", "fields", "vac"):
         assert np.array_equal(out[0][2][key], out[1][2][key]), key
         assert np.array_equal(out[0][3][key], out[1][3][key]), key
+
+
+def test_symmetrised_largest_separation_and_offset_match_oracle_fp64():
+    """r_max = L/2 and d_max = L - 1 (every midpoint shift and offset wraps around) with
+    updates between the measurements, against the oracle."""
+    L, Nt, tau, n_sub, r_max, d_max = 8, 4, 2, 2, 4, 7
+    g = _lib.Lattice(L, Nt, 1.0, 97)
+    c = O.Lattice(L, Nt, 1.0, 97)
+    g.sweep(1, 3)
+    c.sweep(1, 3)
+    gr = g.multilevel_fields_sym(tau, n_sub, r_max, d_max)
+    cr = c.multilevel_sym(tau, n_sub, r_max, d_max)
+    assert angle_diff(g.get_links(), c.theta).max() == 0.0
+    for key in ("corr", "fields", "vac"):
+        assert np.max(np.abs(np.asarray(gr[key]) - np.asarray(cr[key]))) < OBS_TOL, key
+
+
+def test_symmetrised_full_size_fp32_tiled_close_to_fp64():
+    """24^4 (the benchmark's lattice and launch shapes: slab-resident passes, plane blocks of
+    frame sums, the tiled contraction of three axes) on a frozen configuration: FP32 links
+    and products against the FP64 path (whose kernels are pinned to the oracle above)."""
+    g64 = _lib.Lattice(24, 24, 1.0, 5, _lib.UL_FP64)
+    g64.sweep(1, 3)
+    th = g64.get_links()
+    g32 = _lib.Lattice(24, 24, 1.0, 5, _lib.UL_FP32_ACC64)
+    g32.set_links(th)
+    res = []
+    for g in (g64, g32):
+        g.set_option("sub_metro", 0)
+        g.set_option("sub_or", 0)
+        res.append(g.multilevel_fields_sym(2, 2, 8, 6))
+        g.close()
+    for key in ("corr", "fields", "vac"):
+        assert np.max(np.abs(np.asarray(res[0][key]) - np.asarray(res[1][key]))) < 2e-6, key
