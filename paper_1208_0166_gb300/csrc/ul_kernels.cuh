@@ -1007,7 +1007,9 @@ cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r
                                  double2* asum, void* tk, void* ok, double* osum, const void* ubar, cudaStream_t st)
 {
     const int S = g.Nt / slab_t;
-    measure_store_kernel<R><<<blocks_for(static_cast<long>(S) * g.L3), kThreads, 0, st>>>(
+    const long n = static_cast<long>(S) * g.L3;
+    const int threads = update_block_threads(n); // balanced over the SMs, as the class updates
+    measure_store_kernel<R><<<static_cast<unsigned int>((n + threads - 1) / threads), threads, 0, st>>>(
         g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, fields ? 1 : 0, slot, asum, static_cast<Cx<R>*>(tk),
         static_cast<R*>(ok), osum, static_cast<const Cx<R>*>(ubar));
     return cudaGetLastError();
