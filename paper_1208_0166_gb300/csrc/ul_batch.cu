@@ -11,6 +11,7 @@
 // (first-fit arena) and a parameter-table slot is free, and leave when their results
 // are on the host: continuous batching.  A job only ever touches its own memory and its
 // own random numbers, so its results are bit for bit the same alone or in any mix.
+#include <atomic>
 #include <algorithm>
 #include <cstring>
 #include <deque>
@@ -127,7 +128,7 @@ Layout layout_of(const Job& j, size_t rs)
 
 // Block sizes tried by the batched update kernel's autotuner, and the choice per precision.
 const int kTuneCandidates[3] = {64, 96, 128};
-int g_tuned_threads[2] = {0, 0};
+std::atomic<int> g_tuned_threads[2]; // 0 until tuned; written by any thread
 
 } // namespace
 

@@ -7,6 +7,7 @@
 // transporters T, insertion operator, multilevel field estimator).
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <cooperative_groups.h>
 #include "ul_device.cuh"
 #include "ul_batch_types.h"
@@ -284,20 +285,20 @@ constexpr int kUpdateThreads = 256;
 // against 36 with 4), a masked spatial class (2,592 warps) 6 warps (18 against 20).
 inline int update_block_threads(long work)
 {
-    static int sms[16] = {0};
+    static std::atomic<int> sms_of[16]; // SM count per device, queried once (any thread)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
-    if (!sms[dev]) {
-        int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
-        sms[dev] = n;
+    int sms = sms_of[dev].load(std::memory_order_relaxed);
+    if (!sms) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+        sms_of[dev].store(sms, std::memory_order_relaxed);
     }
     const long warps = (work + 31) / 32;
     int best_k = 4;
     long best = -1;
     for (int k = 2; k <= kUpdateThreads / 32; ++k) {
         const long blocks = (warps + k - 1) / k;
-        const long busiest = (blocks + sms[dev] - 1) / sms[dev] * k;
+        const long busiest = (blocks + sms - 1) / sms * k;
         if (best < 0 || busiest < best || (busiest == best && k > best_k)) {
             best = busiest;
             best_k = k;
@@ -1079,17 +1080,21 @@ cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaS
 template <typename R, int LC>
 cudaError_t launch_persistent_lc(const Geo& g, R* theta, void* cs, const PersistArgs& in, int threads, cudaStream_t st)
 {
-    static int blocks_per_sm = 0;
-    static int n_sm = 0;
+    // occupancy of this instantiation and SM count, queried once (any thread; one GPU model)
+    static std::atomic<int> cached_blocks_per_sm{0}, cached_n_sm{0};
     auto fn = persistent_kernel<R, LC>;
     threads = 256;
-    if (!blocks_per_sm) {
+    int blocks_per_sm = cached_blocks_per_sm.load(std::memory_order_relaxed);
+    int n_sm = cached_n_sm.load(std::memory_order_relaxed);
+    if (!blocks_per_sm || !n_sm) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, threads, 0);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+        cached_n_sm.store(n_sm, std::memory_order_relaxed);
+        cached_blocks_per_sm.store(blocks_per_sm, std::memory_order_relaxed);
     }
     const int work = in.measure ? std::max(g.Vh, (g.Nt / in.u.slab_t) * g.L3) : g.Vh;
     int grid = blocks_per_sm * n_sm;
