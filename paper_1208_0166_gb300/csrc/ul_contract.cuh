@@ -283,6 +283,12 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
             issue_batch<SYM>(smem, bars, k0 + BS, buf ^ 1, min(BS, count - k0 - BS), bufsz, tsz, osz, BS * tsz, tplane,
                              nr, tsrc0, t_db, t_ks, t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes, ndv, o_ds,
                              t.ny * L * 8);
+        // the last batch: bring this thread's FP64 sums into L2 for the epilogue
+        if (bi + 1 == nbatch && active && !first) {
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch)
+                asm volatile("prefetch.global.L2 [%0];\n" ::"l"(bsum + out + ch * g.L3));
+        }
         const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1);
         if (__syncthreads_or(!arrived)) {
             // a copy did not complete in time: report it, give the copies in flight a bounded
