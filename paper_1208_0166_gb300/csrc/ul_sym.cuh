@@ -60,6 +60,18 @@ __device__ __forceinline__ int axis_major_step(int L, int i, int n)
     return i - u + (v >= L ? v - L : v);
 }
 
+// slab_line of the spatial site with lexicographic index x0 and coordinate sum csum (x+y+z):
+// the same loads and products, the temporal link offsets formed without decoding the site.
+template <typename R>
+__device__ __forceinline__ Cx<R> slab_line_at(const Geo& g, const cs_t<R>* __restrict__ cs, int x0, int csum, int t0,
+                                              int slab_t)
+{
+    Cx<R> w = link_at<R>(cs, ((csum + t0) & 1) * g.Vh + ((x0 + g.L3 * t0) >> 1));
+    for (int t = t0 + 1; t < t0 + slab_t; ++t)
+        w = cmul_rn(w, link_at<R>(cs, ((csum + t) & 1) * g.Vh + ((x0 + g.L3 * t) >> 1)));
+    return w;
+}
+
 // Measurement after one sub-sample, one launch of 4 S L3 threads:
 // threads [0, 3 S L3), one per (a, s, i) with i the axis-major index of site x0:
 //   T_a(s, x0, r) = W*(s, x0) W(s, x0 + r e_a)  (W the slab line),
@@ -84,10 +96,11 @@ __global__ void __launch_bounds__(kThreads)
         const int i = static_cast<int>(rem - static_cast<long>(s) * g.L3);
         const int t0 = s * slab_t;
         const SymSite p0 = SymSite::from_axis_major(g.L, a, i);
-        const Cx<R> w0 = cconj(slab_line<R>(g, cs, p0.lex(g.L), t0, slab_t));
+        const Cx<R> w0 = cconj(slab_line_at<R>(g, cs, p0.lex(g.L), p0.c1 + p0.c2 + p0.c3, t0, slab_t));
         const long nA = SL3 * r_max;
         for (int r = 1; r <= r_max; ++r) {
-            const Cx<R> T = cmul_rn(w0, slab_line<R>(g, cs, p0.moved(g.L, a, r).lex(g.L), t0, slab_t));
+            const SymSite p = p0.moved(g.L, a, r);
+            const Cx<R> T = cmul_rn(w0, slab_line_at<R>(g, cs, p.lex(g.L), p.c1 + p.c2 + p.c3, t0, slab_t));
             const long ai = (a - 1) * nA + static_cast<long>(s * r_max + (r - 1)) * g.L3 + i;
             double2 av = asum3[ai];
             av.x += static_cast<double>(T.re);
