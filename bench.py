@@ -87,8 +87,9 @@ def _peaks():
 # DRAM bytes per launch of the dominant kernel from the committed ncu capture, keyed by
 # the hash of the kernel source it was taken on (null when the source has changed).
 TRAFFIC = {
-    # profiles/update_class_f64_24x24.md: mean DRAM bytes of the two captured launches (ncu
-    # replays with cold caches; the lattice is L2-resident in the bench)
+    # mean DRAM bytes of two captured launches of the FP64 update kernel at 24^4 (launches 8
+    # and 9 of the profiled step; ncu replays with cold caches, while in the bench the
+    # lattice is L2-resident)
     ("update_class_kernel<double>", "3bc68a4c11a4ef4c"): 21.30e6,
 }
 

@@ -7,8 +7,7 @@
  * calls this code; only the test suite, the smoke check and the CPU-baseline
  * leg of the benchmark do.  It shares no source with the CUDA path.
  *
- * Conventions (the paper leaves them open; each reading is listed with its
- * reason in the design notes):
+ * Conventions (the paper leaves them open; these are the readings taken):
  *   - direction mu = 0 is time, mu = 1,2,3 are x,y,z;
  *   - site index i = x + L*(y + L*(z + L*t)), V = L^3 * Nt;
  *   - link angles are stored canonically as theta[mu*V + i], in [-pi, pi);
