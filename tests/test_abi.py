@@ -53,6 +53,16 @@ def test_null_handle_is_rejected_without_gpu(lib):
     assert lib.ul_free(None) == _lib.UL_OK
     out = ctypes.c_double()
     assert lib.ul_plaquette(None, ctypes.byref(out)) == _lib.UL_EINVAL
+    buf = (ctypes.c_double * 64)()
+    for call in (lambda: lib.ul_multilevel(None, 2, 1, 1, buf),
+                 lambda: lib.ul_multilevel_fields(None, 2, 1, 1, 0, buf, buf, buf),
+                 lambda: lib.ul_multilevel_fields_begin(None, 2, 1, 1, 0),
+                 lambda: lib.ul_multilevel_fields_end(None, buf, buf, buf),
+                 lambda: lib.ul_multilevel_fields_sym(None, 2, 1, 1, 0, buf, buf, buf),
+                 lambda: lib.ul_multilevel2(None, 4, 1, 2, 1, 1, buf),
+                 lambda: lib.ul_multilevel2_fields(None, 4, 1, 2, 1, 1, 0, buf, buf, buf)):
+        assert call() == _lib.UL_EINVAL
+    assert b"NULL handle" in lib.ul_last_error(None)
 
 
 def test_invalid_shapes_rejected_before_touching_the_device(lib):
