@@ -64,33 +64,72 @@ FLOP_STAPLE = 6 * (6 + 8)
 FLOP_METRO = FLOP_STAPLE + 2 + 4 + 5 + 42 + 6 + 33
 FLOP_OR = FLOP_STAPLE + 30 + 2 + 5 + 42
 
-# Peaks.  HBM from MEASURED_PEAKS.json; ALU peaks derived from unit counts and the
-# maximum SM clock: FP64 4 flop/clk/SM (nominal 1.25 TFLOP/s), FP32 256 flop/clk/SM.
-N_SM = 152
+# Algorithmic bytes per link update: one (mu, parity) class reads its own V/2 angles, the
+# 3V angles of the other directions and the V/2 angles of the opposite parity of its own
+# direction, and writes V/2: 9 angles per update, 36 B in FP32, 72 B in FP64.
+BYTES_PER_UPDATE = {"fp64": 72, "fp32": 36}
+UPDATES_PER_CLASS_LAUNCH = UPDATES_PER_PASS_FULL // 8
+CLASS_LAUNCHES_PER_STEP = W.therm_sweeps * (W.sweep_metro + W.sweep_or) * 8
 
 
-def _peaks():
-    p = {"hbm_gbs": 6792.4, "sm_max_mhz": 2070.0, "source": "fallback"}
+def _measured_peaks():
+    """HBM copy bandwidth from MEASURED_PEAKS.json (fallback 6800 GB/s if absent)."""
+    p = {"hbm_gbs": 6800.0, "hbm_source": "fallback (MEASURED_PEAKS.json absent)"}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             m = json.load(f)
-        p.update({"hbm_gbs": float(m["hbm_gbs"]), "sm_max_mhz": float(m.get("sm_max_mhz", 2070.0)),
-                  "source": "measured"})
+        p = {"hbm_gbs": float(m["hbm_gbs"]), "hbm_source": "MEASURED_PEAKS.json (copy, read + write bytes)"}
     except Exception:
         pass
-    clk = p["sm_max_mhz"] * 1e6
-    p["fp64_tflops"] = N_SM * 4 * clk / 1e12
-    p["fp32_tflops"] = N_SM * 256 * clk / 1e12
     return p
 
 
-# DRAM bytes per launch of the dominant kernel from the committed ncu capture, keyed by
-# the hash of the kernel source it was taken on (null when the source has changed).
+def probe_peaks(lib, stream_handle):
+    """Measured on this GPU at the start of the run (ul_probe_*): L2-resident read bandwidth
+    (32 MiB, the FP64 24^4 lattice with its phase cache, read 64 times) and the FP64 / FP32
+    fused multiply-add rates; the HBM figure is MEASURED_PEAKS.json's."""
+    p = _measured_peaks()
+    p["l2_read_gbs"] = lib.probe_l2_read(32 << 20, 64, stream_handle)
+    p["fp64_fma_tflops"] = lib.probe_fma(lib.UL_FP64, stream_handle)
+    p["fp32_fma_tflops"] = lib.probe_fma(lib.UL_FP32_ACC64, stream_handle)
+    p["source"] = "ul_probe_l2_read(32 MiB, 64 reads), ul_probe_fma (include/ul_probe.h), best of 5"
+    return p
+
+
+def roofline_block(prec_name, sweep_ms_per_step, peaks, traffic=None):
+    """Roofline of the dominant kernel, the one-class update launch of the sweep phase:
+    achieved = algorithmic bytes per launch (updates per launch x bytes per update) over the
+    average launch time (the sweep phase's CUDA-event time on the launching stream over its
+    class launches), as a fraction of the HBM and of the probed L2 read bandwidth; the FP
+    operation rate against the probed FMA rate beside it."""
+    bpu = BYTES_PER_UPDATE[prec_name]
+    avg_s = sweep_ms_per_step / 1e3 / CLASS_LAUNCHES_PER_STEP
+    achieved = UPDATES_PER_CLASS_LAUNCH * bpu / avg_s / 1e9
+    flop_per_update = (W.sweep_metro * FLOP_METRO + W.sweep_or * FLOP_OR) / (W.sweep_metro + W.sweep_or)
+    alu_achieved = UPDATES_PER_CLASS_LAUNCH * flop_per_update / avg_s / 1e12
+    alu_peak = peaks["fp64_fma_tflops"] if prec_name == "fp64" else peaks["fp32_fma_tflops"]
+    fr = {"hbm": achieved / peaks["hbm_gbs"], "l2": achieved / peaks["l2_read_gbs"],
+          "alu": alu_achieved / alu_peak}
+    binding = max(fr, key=fr.get)
+    return {"bound": "hbm", "kernel": "update_class_kernel<%s>" % ("double" if prec_name == "fp64" else "float"),
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": fr["hbm"],
+            "traffic": traffic, "bytes_per_update": bpu, "updates_per_launch": UPDATES_PER_CLASS_LAUNCH,
+            "avg_launch_us": avg_s * 1e6, "launches_per_step": CLASS_LAUNCHES_PER_STEP,
+            "l2": {"achieved": achieved, "peak": peaks["l2_read_gbs"], "unit": "GB/s", "frac": fr["l2"],
+                   "note": "the lattice (and its phase cache) is L2-resident across the sweep phase"},
+            "alu": {"achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": fr["alu"],
+                    "flop_per_update": flop_per_update,
+                    "note": "%s fused multiply-add rate measured by ul_probe_fma" % prec_name.upper()},
+            "closest_roof": binding}
+
+
+# DRAM bytes per launch of the dominant kernel from a committed ncu capture, keyed by the
+# hash of the kernel sources it was taken on (null once the sources have changed).
 TRAFFIC = {
     # mean DRAM bytes of two captured launches of the FP64 update kernel at 24^4 (launches 8
     # and 9 of the profiled step; ncu replays with cold caches, while in the bench the
     # lattice is L2-resident)
-    ("update_class_kernel<double>", "3bc68a4c11a4ef4c"): 21.30e6,
+    ("fp64", "3bc68a4c11a4ef4c"): 21.30e6,
 }
 
 
@@ -178,8 +217,10 @@ def _measure(lat, args):
 def fp32_error_vs_fp64(lib):
     """Error of the FP32+FP64-accumulation estimators against the FP64 path on one frozen
     24^4 configuration (the same angles in both precisions, sub-samples without updates, so
-    the difference is the FP32 arithmetic alone; the FP64 path equals the oracle bit for bit).
-    Max absolute difference per observable, and relative to the largest FP64 value."""
+    the difference is the FP32 arithmetic alone; the FP64 path equals the oracle within its
+    rounding bound).  Relative errors element by element: per r for C(r) (|dC(r)| / |C(r)|),
+    per channel the median and maximum over (r, d) of |dN| / |N| for the insertions, per
+    channel for the vacuum terms, and for the plaquette."""
     import numpy as np
 
     g64 = lib.Lattice(W.L, W.Nt, W.beta, 77, lib.UL_FP64)
@@ -188,20 +229,38 @@ def fp32_error_vs_fp64(lib):
     th = g64.get_links()
     g32 = lib.Lattice(W.L, W.Nt, W.beta, 77, lib.UL_FP32_ACC64)
     g32.set_links(th)
-    out = {}
     res = []
     for g in (g64, g32):
         g.set_option("sub_metro", 0)
         g.set_option("sub_or", 0)
         res.append(g.multilevel_fields(SLAB_T, 16, W.r_max, W.d_max))
         res[-1]["plaquette"] = np.array([g.plaquette()])
-    for key in ("corr", "fields", "vac", "plaquette"):
-        a, b = np.asarray(res[0][key]), np.asarray(res[1][key])
-        err = float(np.max(np.abs(a - b)))
-        out[key] = {"max_abs": err, "rel_to_max": err / max(float(np.max(np.abs(a))), 1e-300)}
     g64.close()
     g32.close()
-    out["workload"] = "24^4 after 5 FP64 sweeps, frozen (16 sub-samples without updates), both precisions"
+    a, b = res
+
+    def rel(x, y):
+        x, y = np.asarray(x), np.asarray(y)
+        return np.abs(y - x) / np.maximum(np.abs(x), 1e-300)
+
+    rc = rel(a["corr"], b["corr"])
+    rf = rel(a["fields"], b["fields"])          # [r, d, ch]
+    names = ["Im E_x", "Re E_x", "Im E_y", "Re E_y", "Im E_z", "Re E_z", "Im B_x", "Re B_x"]
+    out = {
+        "corr_rel_per_r": [float(v) for v in rc],
+        "corr_max_abs": float(np.max(np.abs(np.asarray(a["corr"]) - np.asarray(b["corr"])))),
+        "fields_rel_per_channel": {n: {"median": float(np.median(rf[..., k])), "max": float(np.max(rf[..., k]))}
+                                   for k, n in enumerate(names)},
+        "fields_rel_median": float(np.median(rf)),
+        "vac_rel_per_channel": {n: float(v) for n, v in zip(names, rel(a["vac"], b["vac"]))},
+        "plaquette_rel": float(rel(a["plaquette"], b["plaquette"])[0]),
+        "workload": "24^4 after 5 FP64 sweeps, frozen (16 sub-samples without updates), both precisions",
+    }
+    out["summary"] = ("FP32 links + FP64 accumulation vs FP64 on a frozen 24^4 configuration: C(r) relative "
+                      "error <= %.1e for every r = 1..%d; insertion sums median %.1e (largest %.1e on the "
+                      "smallest elements); plaquette %.1e"
+                      % (max(out["corr_rel_per_r"]), W.r_max, out["fields_rel_median"], float(np.max(rf)),
+                         out["plaquette_rel"]))
     return out
 
 
@@ -238,20 +297,51 @@ def _config(args):
             "parallelism": f"replicas x{args.gpus}"}
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline_sample():
-    """The oracle on a bounded sample of the workload: one full compound sweep plus one
-    masked sub-sample (1 + 3 passes) and its transporter measurement at 24^4."""
+    """The oracle timed on this machine's host cores, on bounded samples of the workload:
+    all cores (the oracle's OpenMP timing build: the links of one class on every thread)
+    on the reduced run of 10 compound sweeps then a level of 10 sub-samples at 24^4, and
+    one thread (the default build) on 1 compound sweep + 1 masked sub-sample."""
     import oracle as O
 
-    lat = O.Lattice(W.L, W.Nt, W.beta, 1)
+    O.build()
+    n_thr = O.threads(openmp=True)
+    lat = O.Lattice(W.L, W.Nt, W.beta, 1, openmp=True)
     t0 = time.perf_counter()
-    lat.sweep(W.sweep_metro, W.sweep_or)
-    lat.multilevel(SLAB_T, 1, W.r_max, sub_metro=W.sweep_metro, sub_or=W.sweep_or)
+    for _ in range(10):
+        lat.sweep(W.sweep_metro, W.sweep_or)
+    lat.multilevel(SLAB_T, 10, W.r_max, sub_metro=W.sweep_metro, sub_or=W.sweep_or)
     dt = time.perf_counter() - t0
-    updates = (W.sweep_metro + W.sweep_or) * (UPDATES_PER_PASS_FULL + UPDATES_PER_PASS_SUB)
-    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"24^4: 1 compound sweep + 1 masked sub-sample with T measurement "
-                      f"({updates} link updates, {dt:.1f} s, single thread)"}
+    per = W.sweep_metro + W.sweep_or
+    updates = 10 * per * UPDATES_PER_PASS_FULL + 10 * per * UPDATES_PER_PASS_SUB
+    samples = 10 * S * L3 * W.r_max
+    lat1 = O.Lattice(W.L, W.Nt, W.beta, 1)
+    t1 = time.perf_counter()
+    lat1.sweep(W.sweep_metro, W.sweep_or)
+    lat1.multilevel(SLAB_T, 1, W.r_max, sub_metro=W.sweep_metro, sub_or=W.sweep_or)
+    dt1 = time.perf_counter() - t1
+    updates1 = per * (UPDATES_PER_PASS_FULL + UPDATES_PER_PASS_SUB)
+    return {"value": updates / dt, "unit": UNIT, "cores": n_thr, "kind": "oracle",
+            "cpu_model": _cpu_model(), "host_cpus": os.cpu_count(),
+            "sample": f"24^4 beta=1: 10 compound sweeps, then a level of 10 masked sub-samples with the "
+                      f"transporter measurement ({updates} link updates, {dt:.1f} s, {n_thr} OpenMP threads)",
+            "correlator_samples_per_s": samples / dt,
+            "single_thread": {"value": updates1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"24^4: 1 compound sweep + 1 masked sub-sample with T measurement "
+                                        f"({updates1} link updates, {dt1:.1f} s)"}}
 
 
 def run_reference(args):
@@ -261,7 +351,8 @@ def run_reference(args):
     import oracle as O
 
     O.build()
-    lat = O.Lattice(W.L, W.Nt, W.beta, 1)
+    n_thr = O.threads(openmp=True)
+    lat = O.Lattice(W.L, W.Nt, W.beta, 1, openmp=True)
     per_step = (W.sweep_metro + W.sweep_or) * UPDATES_PER_PASS_SUB
 
     def step():
@@ -275,12 +366,14 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = per_step * args.steps / dt
     sample = (f"24^4 beta=1: per step one masked sub-sample (1 Metropolis + 3 OR over the "
-              f"{UPDATES_PER_PASS_SUB} unfrozen links) and its slab-transporter measurement, single thread")
+              f"{UPDATES_PER_PASS_SUB} unfrozen links) and its slab-transporter measurement, "
+              f"{n_thr} OpenMP threads (the oracle's timing build)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_thr, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -422,17 +515,14 @@ def _torch_setup():
     return torch, dist, ws, rank, local
 
 
-def run_batch(args):
+def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000):
     """32 independent configurations of uneven sizes (8 each of 12^4, 16^4, 20^4, 24^4,
     beta from {0.96, 0.98, 1.0}) advanced together by the batch engine; a step is the
     whole batch run to completion (100 sweeps + one 200-sample level + reduction each)."""
-    torch, dist, ws, rank, local = _torch_setup()
-    from paper_1208_0166_gb300 import _lib as lib
     from paper_1208_0166_gb300.serving import job_from
     from paper_1208_0166_gb300.workloads import batch_jobs_uneven
 
-    prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
-    specs = batch_jobs_uneven(1000 + 100 * rank)
+    specs = batch_jobs_uneven(seed_base + 100 * rank)
     stream = torch.cuda.Stream()
     b = lib.Batch(prec, 8 << 30, stream.cuda_stream)
 
@@ -440,7 +530,7 @@ def run_batch(args):
         ids = [b.submit(job_from(sp)) for sp in specs]
         return b.run_to_completion(ids, passes_per_step=32)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     stream.synchronize()
     if dist:
@@ -448,70 +538,91 @@ def run_batch(args):
     u0, l0 = b.stats()["link_updates"], b.stats()["launches"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    clocks.start()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         res = step()
     e1.record(stream)
     stream.synchronize()
-    clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     st = b.stats()
-    updates, launches = st["link_updates"] - u0, st["launches"] - l0
-    samples = sum(sp["n_sub"] * (sp["Nt"] // sp["slab_t"]) * sp["L"] ** 3 * sp["r_max"] for sp in specs) * args.steps
+    b.close()
+    samples = sum(sp["n_sub"] * (sp["Nt"] // sp["slab_t"]) * sp["L"] ** 3 * sp["r_max"] for sp in specs) * steps
+    return {"ms": ms, "updates": st["link_updates"] - u0, "launches": st["launches"] - l0, "samples": samples,
+            "block_threads": st["block_threads"], "jobs": len(specs),
+            "C_r_first_job": [[z.real, z.imag] for z in res[min(res)]["corr"][:3]]}
+
+
+def serve_result(lib, prec, n_jobs, rate_hz, rank, torch):
+    """Poisson stream of correlator jobs (L in {12,16,20,24,32}, beta ~ U[0.95,1.005],
+    r_max in [4, L/3], n_sub in [50, 400]) served by continuous batching."""
+    from paper_1208_0166_gb300.serving import Server
+    from paper_1208_0166_gb300.workloads import serving_stream
+
+    stream = torch.cuda.Stream()
+    warm = serving_stream(4, rate_hz=1000.0, seed=99, sizes=(12,), n_sweeps=2, n_sub_range=(2, 4))
+    srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
+    srv.run(warm)
+    srv.close()
+    reqs = serving_stream(n_jobs, rate_hz=rate_hz, seed=7 + rank)
+    srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
+    results, summary = srv.run(reqs)
+    srv.close()
+    return {"jobs_per_s": summary["jobs_per_s"], "p50_latency_s": summary["p50_latency_s"],
+            "p99_latency_s": summary["p99_latency_s"], "jobs": summary["jobs"], "wall_s": summary["wall_s"],
+            "link_updates_per_s": summary["stats"]["link_updates"] / summary["wall_s"],
+            "gpu_launches": summary["stats"]["launches"], "block_threads": summary["stats"]["block_threads"],
+            "max_resident": summary.get("max_resident"),
+            "workload": f"Poisson stream, {n_jobs} jobs at {rate_hz} Hz, L in {{12,16,20,24,32}}, "
+                        "beta~U[0.95,1.005], r_max in [4,L/3], n_sub in [50,400], 100 sweeps, slab_t=2, "
+                        "HBM budget 16 GiB"}
+
+
+BATCH_WORKLOAD = ("batch: 32 configurations, 8 each of 12^4/16^4/20^4/24^4, beta in {0.96,0.98,1.0}, "
+                  "100 sweeps + slab_t=2 n_sub=200 r<=L/3 each")
+
+
+def run_batch(args):
+    torch, dist, ws, rank, local = _torch_setup()
+    from paper_1208_0166_gb300 import _lib as lib
+
+    prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
+    clocks = ClockSampler(local)
+    clocks.start()
+    r = batch_result(lib, prec, args.steps, args.warmup, rank, dist, torch)
+    clk = clocks.stop()
     from paper_1208_0166_gb300.replicas import aggregate
 
-    t, total_updates = aggregate(ms / 1e3, updates, dist, "cuda")
-    b.close()
+    t, total_updates = aggregate(r["ms"] / 1e3, r["updates"], dist, "cuda")
     if rank != 0:
         return 0
     line = {"metric": METRIC, "workload_mode": "batch", "value": total_updates / t, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
-            "config": {"workload": "batch: 32 configurations, 8 each of 12^4/16^4/20^4/24^4, beta in "
-                                   "{0.96,0.98,1.0}, 100 sweeps + slab_t=2 n_sub=200 r<=L/3, one launch per class",
-                       "jobs": len(specs), "block_threads": st["block_threads"]},
-            "correlator_samples_per_s": samples * ws / t, "gpu_launches": launches, "clocks": clk,
-            "C_r_first_job": [[z.real, z.imag] for z in res[min(res)]["corr"][:3]]}
+            "config": {"workload": BATCH_WORKLOAD, "jobs": r["jobs"], "block_threads": r["block_threads"]},
+            "correlator_samples_per_s": r["samples"] * ws / t, "gpu_launches": r["launches"], "clocks": clk,
+            "C_r_first_job": r["C_r_first_job"]}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_serve(args):
-    """Poisson stream of correlator jobs (L in {12,16,20,24,32}, beta ~ U[0.95,1.005],
-    r_max in [4, L/3], n_sub in [50, 400]) served by continuous batching."""
     torch, dist, ws, rank, local = _torch_setup()
     from paper_1208_0166_gb300 import _lib as lib
-    from paper_1208_0166_gb300.serving import Server
-    from paper_1208_0166_gb300.workloads import serving_stream
 
     prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
-    stream = torch.cuda.Stream()
-    warm = serving_stream(4, rate_hz=1000.0, seed=99, sizes=(12,), n_sweeps=2, n_sub_range=(2, 4))
-    srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
-    srv.run(warm)
-    srv.close()
-    reqs = serving_stream(args.serve_jobs, rate_hz=args.serve_rate, seed=7 + rank)
-    srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
     clocks = ClockSampler(local)
     clocks.start()
-    results, summary = srv.run(reqs)
+    r = serve_result(lib, prec, args.serve_jobs, args.serve_rate, rank, torch)
     clk = clocks.stop()
-    srv.close()
     if rank != 0:
         return 0
     line = {"metric": "served multilevel correlator jobs/s and p50/p99 latency", "workload_mode": "serve",
-            "value": summary["jobs_per_s"], "unit": "jobs/s", "n_gpus": ws, "higher_is_better": True,
-            "p50_latency_s": summary["p50_latency_s"], "p99_latency_s": summary["p99_latency_s"],
+            "value": r["jobs_per_s"], "unit": "jobs/s", "n_gpus": ws, "higher_is_better": True,
+            "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"],
             "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
-            "config": {"workload": f"Poisson stream, {args.serve_jobs} jobs at {args.serve_rate} Hz, L in "
-                                   "{12,16,20,24,32}, beta~U[0.95,1.005], r_max in [4,L/3], n_sub in [50,400], "
-                                   "100 sweeps, slab_t=2, HBM budget 16 GiB",
-                       "block_threads": summary["stats"]["block_threads"]},
-            "link_updates_per_s": summary["stats"]["link_updates"] / summary["wall_s"],
-            "gpu_launches": summary["stats"]["launches"], "clocks": clk}
+            "config": {"workload": r["workload"], "block_threads": r["block_threads"]},
+            "link_updates_per_s": r["link_updates_per_s"], "gpu_launches": r["gpu_launches"], "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -574,49 +685,68 @@ def run_ours(args):
     value = total_updates / total_s
     samples = SAMPLES_PER_STEP * K * ws / total_s
 
+    peaks = probe_peaks(lib, None)
+    prec_name = "fp64" if prec == lib.UL_FP64 else "fp32"
+    roofline = roofline_block(prec_name, main["sweep_ms"] / K, peaks, TRAFFIC.get((prec_name, _kernel_hash())))
+
     compare = None
     if not args.no_compare:
         other = lib.UL_FP32_ACC64 if prec == lib.UL_FP64 else lib.UL_FP64
         o = _run_gpu(args, other, K, Wm, rank, ws, dist, torch, lib, e2e=False)
         o_s = gmax(o["total_ms"]) / 1e3
+        other_name = "fp32" if other == lib.UL_FP32_ACC64 else "fp64"
         compare = {"precision": "fp32_acc64" if other == lib.UL_FP32_ACC64 else "fp64",
                    "value": ups * K * ws / o_s, "unit": UNIT,
                    "sweep_ms_per_step": o["sweep_ms"] / K, "multilevel_ms_per_step": o["ml_ms"] / K,
                    "correlator_samples_per_s": SAMPLES_PER_STEP * K * ws / o_s,
                    "ms_per_step": o_s / K * 1e3, "gpu_launches": o["launches"],
                    "C_r": [[z.real, z.imag] for z in o["corr"][:4]],
+                   "roofline": roofline_block(other_name, o["sweep_ms"] / K, peaks,
+                                              TRAFFIC.get((other_name, _kernel_hash()))),
                    "fp32_error_vs_fp64": fp32_error_vs_fp64(lib)}
 
-    peaks = _peaks()
-    update_launches = W.therm_sweeps * (W.sweep_metro + W.sweep_or) * 8
-    avg_launch_s = main["sweep_ms"] / 1e3 / (K * update_launches)
-    flops_per_launch = (UPDATES_PER_PASS_FULL / 8) * (
-        W.sweep_metro * FLOP_METRO + W.sweep_or * FLOP_OR) / (W.sweep_metro + W.sweep_or)
-    achieved = flops_per_launch / avg_launch_s / 1e12
-    peak = peaks["fp64_tflops"] if prec == lib.UL_FP64 else peaks["fp32_tflops"]
-    kname = "update_class_kernel<%s>" % ("double" if prec == lib.UL_FP64 else "float")
-    traffic = TRAFFIC.get((kname, _kernel_hash()))
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x %s flop/clk x %.0f MHz" % (
-                    "4 FP64" if prec == lib.UL_FP64 else "256 FP32", peaks["sm_max_mhz"]),
-                "avg_launch_us": avg_launch_s * 1e6, "flop_per_launch": flops_per_launch,
-                "l2_equiv_gbs": (UPDATES_PER_PASS_FULL / 8) * (72 if prec == lib.UL_FP64 else 36)
-                / avg_launch_s / 1e9}
+    # the batched (configuration 3) and served (configuration 4) forms, FP32 links with FP64
+    # accumulation, each timed on its own (one GPU only: replicas would repeat them)
+    batch = serve = None
+    if not args.no_batch and ws == 1:
+        r = batch_result(lib, lib.UL_FP32_ACC64, 2, 1, rank, dist, torch)
+        batch = {"value": r["updates"] / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"] / 2,
+                 "steps": 2, "warmup": 1, "correlator_samples_per_s": r["samples"] / (r["ms"] / 1e3),
+                 "gpu_launches": r["launches"], "block_threads": r["block_threads"],
+                 "dtype": "f32 (FP64 accumulation)", "workload": BATCH_WORKLOAD,
+                 "roofline_step": {"achieved": r["updates"] * 36 / (r["ms"] / 1e3) / 1e9, "unit": "GB/s",
+                                   "bytes_per_update": 36, "peak_hbm": peaks["hbm_gbs"],
+                                   "frac_hbm": r["updates"] * 36 / (r["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                   "peak_l2": peaks["l2_read_gbs"],
+                                   "frac_l2": r["updates"] * 36 / (r["ms"] / 1e3) / 1e9 / peaks["l2_read_gbs"],
+                                   "note": "whole batch step (every launch: updates, measurements, reductions)"}}
+    if not args.no_serve and ws == 1:
+        r = serve_result(lib, lib.UL_FP32_ACC64, args.serve_jobs, args.serve_rate, rank, torch)
+        serve = {**r, "dtype": "f32 (FP64 accumulation)"}
 
     if rank != 0:
         return 0
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline_sample()
+    accuracy = compare["fp32_error_vs_fp64"]["summary"] if compare else None
+    fp32_vs_fp64 = None
+    if compare:
+        v64, v32 = (value, compare["value"]) if prec == lib.UL_FP64 else (compare["value"], value)
+        fp32_vs_fp64 = {"fp64_link_updates_per_s": v64, "fp32_acc64_link_updates_per_s": v32, "speedup": v32 / v64}
+        if batch:
+            fp32_vs_fp64["batch_fp32_acc64_link_updates_per_s"] = batch["value"]
+            fp32_vs_fp64["batch_speedup_over_fp64"] = batch["value"] / v64
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
             "ms_per_step": total_s / K * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)",
             "data": "synthetic", "config": _config(args),
             "correlator_samples_per_s": samples,
-            "phases_ms_per_step": {"sweeps": main["sweep_ms"] / K, "multilevel": main["ml_ms"] / K}, "insertion_samples_per_s": INSERTION_SAMPLES_PER_STEP * K * ws / total_s,
-            "link_updates_per_step": ups, "compare": compare,
-            "roofline": roofline, "cpu_baseline": cpu,
+            "phases_ms_per_step": {"sweeps": main["sweep_ms"] / K, "multilevel": main["ml_ms"] / K},
+            "insertion_samples_per_s": INSERTION_SAMPLES_PER_STEP * K * ws / total_s,
+            "link_updates_per_step": ups, "compare": compare, "accuracy": accuracy,
+            "fp32_vs_fp64": fp32_vs_fp64, "batch": batch, "serve": serve,
+            "roofline": roofline, "peaks": peaks, "cpu_baseline": cpu,
             "e2e": {"value": ups * K * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": H2D_BYTES,
                     "d2h_bytes_per_step": D2H_BYTES},
             "gpu_launches": main["launches"], "clocks": clk,
@@ -636,6 +766,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched form (configuration 3)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served form (configuration 4)")
     ap.add_argument("--pipeline", type=int, default=0, choices=[0, 1],
                     help="1: collect each configuration's level after queueing the next one's sweeps "
                          "(ul_multilevel_fields_begin/_end; one-level estimator only)")

@@ -188,6 +188,27 @@ int ul_multilevel2(ul_lattice* h, int tau1, int n1, int tau2, int n2, int r_max,
 int ul_plaquette(ul_lattice* h, double* out);
 
 /*
+ * ul_check_enabled — 1 if this library is the bounds-checked build (libul_check.so,
+ * compiled with -DUL_CHECK), else 0.  The paper has no counterpart: the checked build
+ * stands in for a memory sanitizer.  In it, every link offset, neighbour site index and
+ * accumulator index the update, measurement, plaquette and slab-resident kernels form is
+ * compared with the extent of its array before the access; an index out of range is
+ * recorded (first one only) and replaced by 0, so the kernel never faults or traps.
+ */
+int ul_check_enabled(void);
+
+/*
+ * ul_check_status — *first_failure = 0 if no checked index has been out of range since the
+ * last clear, else the first failure: bit 63 set, bits 48..55 a tag naming the access
+ * (1 link offset, 2 neighbour site, 3 neighbour link, 4 updated link, 5 slab-kernel global
+ * offset, 6 transporter accumulator, 7 stored sample, 8 channel sums), bits 0..47 the index.
+ * clear != 0 resets the record.  Always 0 in the default build.  Synchronises with the
+ * device (reads device memory); call it between kernels, not during stream capture.
+ * UL_EINVAL for a NULL pointer, UL_ECUDA if the read fails.
+ */
+int ul_check_status(unsigned long long* first_failure, int clear);
+
+/*
  * ul_plaquette_noalloc — the mean plaquette <Re U_p> of link angles that already live in
  * device memory, computed without allocating any device memory.  The paper has no
  * counterpart: this exists for callers that cannot let a library allocate, such as a host
@@ -201,7 +222,9 @@ int ul_plaquette(ul_lattice* h, double* out);
  * Scratch: one partial sum per block of 256 sites, kept in a fixed array inside the library
  * (512 KiB per GPU that loads it, held until the process exits).  Lattices larger than
  * 2^24 sites (e.g. beyond 64^4) are rejected with UL_EINVAL, as are NULL pointers and
- * L or Nt < 2; UL_ECUDA means a CUDA call failed.  The first call on each device looks up
+ * L or Nt < 2; UL_ECUDA means a CUDA call of this entry point failed (an error left pending
+ * on the calling thread by earlier work is cleared on entry, not reported here).  The first
+ * call on each device looks up
  * the array's device address (with that device current); make that first call before any
  * stream capture.  All calls share the one array and each call overwrites every slot it
  * reads, so nothing carries over between calls, but two calls that overlap on the GPU
@@ -368,6 +391,15 @@ int ul_batch_step(ul_batch* b, int max_passes, int* n_active);
  * and the Metropolis acceptance rate, and the job is released (a second poll of the same
  * id is UL_EINVAL). */
 int ul_batch_poll(ul_batch* b, uint64_t job_id, double* out, int* state);
+
+/* ul_batch_job_info — progress of a job that has not been collected yet: *state as in
+ * ul_batch_poll (a finished job whose results are not yet collected reads UL_JOB_DONE),
+ * *passes_done = update passes the engine has enqueued for it so far (each lockstep step
+ * advances every resident job by one pass), *passes_total = its whole program (n_sweeps
+ * compound sweeps and n_sub sub-samples).  Serving loops use it to show that jobs admitted
+ * at different times advance in the same steps.  Any output may be NULL.  UL_EINVAL for
+ * an unknown or already collected job. */
+int ul_batch_job_info(ul_batch* b, uint64_t job_id, int* state, uint64_t* passes_done, uint64_t* passes_total);
 
 /* ul_batch_stats — link updates and kernel launches issued so far, the block size the
  * autotuner chose for the batched update kernel (128, 256 or 512 threads, timed on the

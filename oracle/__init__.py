@@ -27,26 +27,51 @@ N_CHANNELS = 8
 CHANNEL_NAMES = ["Im E_x", "Re E_x", "Im E_y", "Re E_y", "Im E_z", "Re E_z", "Im B_x", "Re B_x"]
 
 
-def build(force: bool = False) -> str:
-    """Compile ul_oracle.c into liboracle.so beside it (gcc, -ffp-contract=off)."""
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(os.path.join(_HERE, "ul_oracle.h"))):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
+_lib_omp = None
+
+
+def _build_one(path: str, extra, force: bool) -> str:
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(path) >= os.path.getmtime(os.path.join(_HERE, "ul_oracle.h"))):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-Wall", *extra, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-def _load():
-    global _lib
+def build(force: bool = False) -> str:
+    """Compile ul_oracle.c into liboracle.so beside it (gcc, -ffp-contract=off), and the
+    timing build liboracle_omp.so (the same source with -fopenmp: the links of one class
+    on OpenMP threads, same values)."""
+    _build_one(_OMP_PATH, ["-fopenmp"], force)
+    return _build_one(_LIB_PATH, [], force)
+
+
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _bind(ctypes.CDLL(_OMP_PATH))
+        return _lib_omp
     if _lib is not None:
         return _lib
     build()
-    lib = ctypes.CDLL(_LIB_PATH)
+    _lib = _bind(ctypes.CDLL(_LIB_PATH))
+    return _lib
+
+
+def threads(openmp: bool = True) -> int:
+    """Threads the timing build's class loop uses (OMP_NUM_THREADS or all cores)."""
+    return _load(openmp).ulo_threads()
+
+
+def _bind(lib):
     d, i, l, u64 = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_uint64
     dp = ctypes.POINTER(ctypes.c_double)
     up = ctypes.POINTER(ctypes.c_uint64)
@@ -93,7 +118,7 @@ def _load():
     lib.ulo_multilevel2_fields.restype = i
     lib.ulo_multilevel_sym.restype = i
     lib.ulo_symmetry_transform.argtypes = [i, i, dp, ip, ip, dp]
-    _lib = lib
+    lib.ulo_threads.restype = i
     return lib
 
 
@@ -154,57 +179,62 @@ class Lattice:
     """A lattice state in the oracle: angles in canonical layout plus the RNG state."""
 
     def __init__(self, L: int, Nt: int, beta: float, seed: int, width: float = 1.0,
-                 theta: np.ndarray | None = None, metro_pass: int = 0):
+                 theta: np.ndarray | None = None, metro_pass: int = 0, openmp: bool = False):
+        """openmp=True runs sweeps through the timing build (class loop on OpenMP threads)."""
+        self.openmp = bool(openmp)
         self.L, self.Nt, self.beta, self.seed, self.width = int(L), int(Nt), float(beta), int(seed), float(width)
         self.V = self.L ** 3 * self.Nt
         self.metro_pass = ctypes.c_uint64(int(metro_pass))
         if theta is None:
             self.theta = np.empty(4 * self.V, dtype=np.float64)
-            _load().ulo_hot_start(self.L, self.Nt, self.seed, _dp(self.theta))
+            self._lib().ulo_hot_start(self.L, self.Nt, self.seed, _dp(self.theta))
         else:
             self.theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(4 * self.V).copy()
+
+    def _lib(self):
+        return _load(self.openmp)
 
     def copy(self) -> "Lattice":
         return Lattice(self.L, self.Nt, self.beta, self.seed, self.width, self.theta, self.metro_pass.value)
 
     def sweep(self, n_metro: int, n_or: int, slab_t: int = 0) -> int:
-        return _load().ulo_sweep(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+        return self._lib().ulo_sweep(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
                                  ctypes.byref(self.metro_pass), int(n_metro), int(n_or), int(slab_t))
 
     def plaquette(self) -> float:
-        return _load().ulo_plaquette(self.L, self.Nt, _dp(self.theta))
+        return self._lib().ulo_plaquette(self.L, self.Nt, _dp(self.theta))
 
     def plaquette_at(self, mu: int, nu: int, i: int) -> complex:
         re, im = ctypes.c_double(), ctypes.c_double()
-        _load().ulo_plaquette_at(self.L, self.Nt, _dp(self.theta), mu, nu, int(i), ctypes.byref(re), ctypes.byref(im))
+        self._lib().ulo_plaquette_at(self.L, self.Nt, _dp(self.theta), mu, nu, int(i), ctypes.byref(re), ctypes.byref(im))
         return complex(re.value, im.value)
 
     def staple(self, mu: int, i: int) -> complex:
         re, im = ctypes.c_double(), ctypes.c_double()
-        _load().ulo_staple(self.L, self.Nt, _dp(self.theta), mu, int(i), ctypes.byref(re), ctypes.byref(im))
+        self._lib().ulo_staple(self.L, self.Nt, _dp(self.theta), mu, int(i), ctypes.byref(re), ctypes.byref(im))
         return complex(re.value, im.value)
 
     def local_action(self, mu: int, i: int) -> float:
-        return _load().ulo_local_action(self.L, self.Nt, self.beta, _dp(self.theta), mu, int(i))
+        return self._lib().ulo_local_action(self.L, self.Nt, self.beta, _dp(self.theta), mu, int(i))
 
     def polyakov(self) -> np.ndarray:
         out = np.empty(2 * self.L ** 3, dtype=np.float64)
-        _load().ulo_polyakov(self.L, self.Nt, _dp(self.theta), _dp(out))
+        self._lib().ulo_polyakov(self.L, self.Nt, _dp(self.theta), _dp(out))
         return _cplx(out.reshape(-1, 2))
 
     def polyakov_correlator(self, r_max: int) -> np.ndarray:
         out = np.empty(2 * r_max, dtype=np.float64)
-        _load().ulo_polyakov_correlator(self.L, self.Nt, _dp(self.theta), int(r_max), _dp(out))
+        self._lib().ulo_polyakov_correlator(self.L, self.Nt, _dp(self.theta), int(r_max), _dp(out))
         return _cplx(out.reshape(-1, 2))
 
     def field_correlator(self, r_max: int, d_max: int) -> np.ndarray:
         out = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64)
-        _load().ulo_field_correlator(self.L, self.Nt, _dp(self.theta), int(r_max), int(d_max), _dp(out))
+        self._lib().ulo_field_correlator(self.L, self.Nt, _dp(self.theta), int(r_max), int(d_max), _dp(out))
         return _cplx(out.reshape(r_max, d_max + 1, N_CHANNELS, 2))
 
     def field_correlator_one(self, r: int, d: int, ch: int) -> complex:
         re, im = ctypes.c_double(), ctypes.c_double()
-        _load().ulo_field_correlator_one(self.L, self.Nt, _dp(self.theta), int(r), int(d), int(ch),
+        self._lib().ulo_field_correlator_one(self.L, self.Nt, _dp(self.theta), int(r), int(d), int(ch),
                                          ctypes.byref(re), ctypes.byref(im))
         return complex(re.value, im.value)
 
@@ -212,7 +242,7 @@ class Lattice:
                     sub_or: int = 3, multihit: bool = False) -> np.ndarray:
         """Two-level multilevel correlator."""
         corr = np.empty(2 * r_max, dtype=np.float64)
-        rc = _load().ulo_multilevel2(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+        rc = self._lib().ulo_multilevel2(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
                                      ctypes.byref(self.metro_pass), int(tau1), int(n1), int(tau2), int(n2),
                                      int(sub_metro), int(sub_or), int(r_max), _dp(corr), 1 if multihit else 0)
         if rc != 0:
@@ -221,12 +251,12 @@ class Lattice:
 
     def multihit_link(self, i: int) -> complex:
         re, im = ctypes.c_double(), ctypes.c_double()
-        _load().ulo_multihit_link(self.L, self.Nt, self.beta, _dp(self.theta), int(i), ctypes.byref(re),
+        self._lib().ulo_multihit_link(self.L, self.Nt, self.beta, _dp(self.theta), int(i), ctypes.byref(re),
                                   ctypes.byref(im))
         return complex(re.value, im.value)
 
     def gauge_transform(self, seed: int) -> None:
-        _load().ulo_gauge_transform(self.L, self.Nt, int(seed), _dp(self.theta))
+        self._lib().ulo_gauge_transform(self.L, self.Nt, int(seed), _dp(self.theta))
 
     def multilevel(self, slab_t: int, n_sub: int, r_max: int, d_max: int = -1,
                    sub_metro: int = 1, sub_or: int = 3, record_samples: bool = False, multihit: bool = False):
@@ -237,7 +267,7 @@ class Lattice:
         vac = np.empty(N_CHANNELS, dtype=np.float64) if d_max >= 0 else None
         samples = (np.empty(n_sub * S * self.L ** 3 * r_max * 2, dtype=np.float64)
                    if record_samples else None)
-        rc = _load().ulo_multilevel(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+        rc = self._lib().ulo_multilevel(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
                                     ctypes.byref(self.metro_pass), int(slab_t), int(n_sub), int(sub_metro),
                                     int(sub_or), int(r_max), int(max(d_max, 0)), _dp(corr),
                                     _dp_or_null(fields), _dp_or_null(vac), _dp_or_null(samples),
@@ -259,7 +289,7 @@ class Lattice:
         corr = np.empty(2 * r_max, dtype=np.float64)
         fields = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64)
         vac = np.empty(N_CHANNELS, dtype=np.float64)
-        rc = _load().ulo_multilevel_sym(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+        rc = self._lib().ulo_multilevel_sym(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
                                         ctypes.byref(self.metro_pass), int(slab_t), int(n_sub), int(sub_metro),
                                         int(sub_or), int(r_max), int(d_max), _dp(corr), _dp(fields), _dp(vac))
         if rc != 0:
@@ -273,7 +303,7 @@ class Lattice:
         corr = np.empty(2 * r_max, dtype=np.float64)
         fields = np.empty(2 * r_max * (d_max + 1) * N_CHANNELS, dtype=np.float64)
         vac = np.empty(N_CHANNELS, dtype=np.float64)
-        rc = _load().ulo_multilevel2_fields(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
+        rc = self._lib().ulo_multilevel2_fields(self.L, self.Nt, self.beta, self.seed, self.width, _dp(self.theta),
                                             ctypes.byref(self.metro_pass), int(tau1), int(n1), int(tau2), int(n2),
                                             int(sub_metro), int(sub_or), int(r_max), int(d_max), _dp(corr),
                                             _dp(fields), _dp(vac))
@@ -288,7 +318,7 @@ class Lattice:
         ax = (ctypes.c_int * 4)(0, *[int(v) for v in axis_of])
         sg = (ctypes.c_int * 4)(1, *[int(v) for v in sign_of])
         out = np.empty_like(self.theta)
-        _load().ulo_symmetry_transform(self.L, self.Nt, _dp(self.theta), ax, sg, _dp(out))
+        self._lib().ulo_symmetry_transform(self.L, self.Nt, _dp(self.theta), ax, sg, _dp(out))
         return Lattice(self.L, self.Nt, self.beta, self.seed, self.width, out, self.metro_pass.value)
 
 

@@ -22,6 +22,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* Elementary functions with a fixed operation sequence.                     */
@@ -412,6 +415,12 @@ long ulo_sweep(int L, int Nt, double beta, uint64_t seed, double width, double* 
         int metropolis = pass < n_metro;
         for (int mu = 0; mu < 4; mu++) {
             for (int p = 0; p < 2; p++) {
+                /* The links of one (mu, parity) class share no staple (checkerboard), so the
+                 * timing build (-fopenmp) may update them on several threads; the default
+                 * build ignores the pragma.  Either way each link gets the same value. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : accepted_total)
+#endif
                 for (long i = 0; i < g.V; i++) {
                     if (parity_of(&g, i) != p) continue;
                     if (is_frozen(&g, mu, i, slab_t)) continue;
@@ -435,6 +444,15 @@ long ulo_sweep(int L, int Nt, double beta, uint64_t seed, double width, double* 
         if (metropolis) (*metro_pass)++;
     }
     return accepted_total;
+}
+
+int ulo_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 void ulo_hot_start(int L, int Nt, uint64_t seed, double* theta)

@@ -150,6 +150,11 @@ int ulo_multilevel2_fields(int L, int Nt, double beta, uint64_t seed, double wid
                            uint64_t* metro_pass, int tau1, int n1, int tau2, int n2, int sub_metro, int sub_or,
                            int r_max, int d_max, double* corr, double* fields, double* vac);
 
+/* Threads the class loop of ulo_sweep runs on: 1 in the default build; the timing build
+ * (compiled with -fopenmp) updates the links of one (mu, parity) class on OpenMP threads,
+ * with the same result for every link. */
+int ulo_threads(void);
+
 /* I1(x)/I0(x), x >= 0 (power series; asymptotic series beyond x = 600). */
 double ulo_bessel_ratio(double x);
 

@@ -17,7 +17,8 @@ UL_FP64, UL_FP32_ACC64 = 0, 1
 N_CHANNELS = 8
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libul.so")
+# UL_LIBRARY=check selects the bounds-checked build libul_check.so (same ABI)
+LIB_PATH = os.path.join(_PKG, "libul_check.so" if os.environ.get("UL_LIBRARY") == "check" else "libul.so")
 
 _lib = None
 
@@ -68,9 +69,14 @@ SIGNATURES = [
     ("ul_batch_submit", _I, [_P, ctypes.POINTER(Job), _U64P]),
     ("ul_batch_step", _I, [_P, _I, ctypes.POINTER(_I)]),
     ("ul_batch_poll", _I, [_P, _U64, _DP, ctypes.POINTER(_I)]),
+    ("ul_batch_job_info", _I, [_P, _U64, ctypes.POINTER(_I), _U64P, _U64P]),
     ("ul_batch_stats", _I, [_P, _U64P, _U64P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
     ("ul_batch_free", _I, [_P]),
     ("ul_batch_last_error", ctypes.c_char_p, [_P]),
+    ("ul_check_enabled", _I, []),
+    ("ul_check_status", _I, [ctypes.POINTER(ctypes.c_ulonglong), _I]),
+    ("ul_probe_l2_read", _I, [ctypes.c_size_t, _I, _DP, _P]),
+    ("ul_probe_fma", _I, [_I, _DP, _P]),
 ]
 
 
@@ -301,6 +307,12 @@ class Batch:
         self._check(load().ul_batch_poll(self._b, int(job_id), _dp(out), ctypes.byref(st)))
         return st.value
 
+    def job_info(self, job_id: int):
+        """(state, passes_done, passes_total) of a job not yet collected."""
+        st, d, t = ctypes.c_int(), ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(load().ul_batch_job_info(self._b, int(job_id), ctypes.byref(st), ctypes.byref(d), ctypes.byref(t)))
+        return st.value, d.value, t.value
+
     def stats(self):
         u, l, t, m = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int(), ctypes.c_size_t()
         self._check(load().ul_batch_stats(self._b, ctypes.byref(u), ctypes.byref(l), ctypes.byref(t), ctypes.byref(m)))
@@ -335,3 +347,24 @@ def rng_uniforms(precision: int, seed: int, pass_: int, link0: int, n: int) -> n
     out = np.zeros(2 * n)
     _check(load().ul_rng_uniforms(int(precision), int(seed), int(pass_), int(link0), int(n), _dp(out)))
     return out.reshape(n, 2)
+
+
+def check_status(clear: bool = False) -> int:
+    """ul_check_status: 0, or the first out-of-range index of the bounds-checked build."""
+    w = ctypes.c_ulonglong()
+    _check(load().ul_check_status(ctypes.byref(w), 1 if clear else 0))
+    return w.value
+
+
+def probe_l2_read(nbytes: int = 32 << 20, reps: int = 64, cuda_stream=None) -> float:
+    """ul_probe_l2_read: read bandwidth (GB/s) of an L2-resident buffer of nbytes."""
+    out = ctypes.c_double()
+    _check(load().ul_probe_l2_read(int(nbytes), int(reps), ctypes.byref(out), cuda_stream))
+    return out.value
+
+
+def probe_fma(precision: int, cuda_stream=None) -> float:
+    """ul_probe_fma: FP64 (UL_FP64) or FP32 (UL_FP32_ACC64) fused multiply-add TFLOP/s."""
+    out = ctypes.c_double()
+    _check(load().ul_probe_fma(int(precision), ctypes.byref(out), cuda_stream))
+    return out.value

@@ -1315,6 +1315,25 @@ int ul_rng_uniforms(int precision, uint64_t seed, uint64_t pass, uint64_t link0,
     return UL_OK;
 }
 
+int ul_check_enabled(void)
+{
+#ifdef UL_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int ul_check_status(unsigned long long* first_failure, int clear)
+{
+    if (!first_failure) return UL_EINVAL;
+    unsigned long long w64 = 0, w32 = 0;
+    if (ul::check_word<double>(&w64, clear != 0) != cudaSuccess) return UL_ECUDA;
+    if (ul::check_word<float>(&w32, clear != 0) != cudaSuccess) return UL_ECUDA;
+    *first_failure = w64 ? w64 : w32;
+    return UL_OK;
+}
+
 const char* ul_last_error(const ul_lattice* h) { return h ? h->err.c_str() : g_init_error.c_str(); }
 
 int ul_precision(const ul_lattice* h) { return h ? h->precision : UL_EINVAL; }

@@ -557,6 +557,19 @@ int ul_batch_poll(ul_batch* b, uint64_t job_id, double* out, int* state)
     return UL_OK;
 }
 
+int ul_batch_job_info(ul_batch* b, uint64_t job_id, int* state, uint64_t* passes_done, uint64_t* passes_total)
+{
+    if (!b) return UL_EINVAL;
+    auto it = b->jobs.find(job_id);
+    if (it == b->jobs.end()) return bfail(b, UL_EINVAL, "ul_batch_job_info: unknown or already collected job");
+    const Job* j = it->second;
+    if (state)
+        *state = j->state == kQueued ? UL_JOB_QUEUED : (j->state == kFinished ? UL_JOB_DONE : UL_JOB_RUNNING);
+    if (passes_done) *passes_done = static_cast<uint64_t>(j->pos);
+    if (passes_total) *passes_total = static_cast<uint64_t>(j->total_passes);
+    return UL_OK;
+}
+
 int ul_batch_stats(ul_batch* b, uint64_t* link_updates, uint64_t* launches, int* block_threads, size_t* bytes_in_use)
 {
     if (!b) return UL_EINVAL;

@@ -10,6 +10,40 @@
 
 namespace ul {
 
+// ---------------------------------------------------------------------------
+// Bounds-checked build (compiled with -DUL_CHECK, library libul_check.so).  Every index
+// passed through UL_IDX is compared with the extent of the array it addresses; an index
+// out of range is recorded in this translation unit's check word (the first one only:
+// bit 63 set, bits 48..55 the site's tag, bits 0..47 the index) and replaced by 0, so
+// the access stays inside the array and the kernel runs on: no trap, no fault.  The host
+// reads the words with ul_check_status.  In the default build UL_IDX is the index itself.
+// ---------------------------------------------------------------------------
+enum : unsigned {
+    kChkLinkOffset = 1,  // link_offset: (mu, site) of a link array
+    kChkNeighbour = 2,   // a staple's neighbour site index
+    kChkStaple = 3,      // a staple's neighbour link offset
+    kChkOwnLink = 4,     // the updated link's own offset
+    kChkSlabGlobal = 5,  // slab kernel: global link offset
+    kChkAsum = 6,        // measurement: transporter accumulator
+    kChkSample = 7,      // measurement: stored sample (slab, separation, site)
+    kChkOsum = 8,        // measurement: channel sums
+};
+
+#ifdef UL_CHECK
+static __device__ unsigned long long g_ul_check_word; // one per translation unit
+__device__ __forceinline__ long long ul_checked_index(long long idx, long long n, unsigned tag)
+{
+    if (idx >= 0 && idx < n) return idx;
+    atomicCAS(&g_ul_check_word, 0ull,
+              (1ull << 63) | (static_cast<unsigned long long>(tag & 0xffu) << 48) |
+                  (static_cast<unsigned long long>(idx) & 0xffffffffffffull));
+    return 0;
+}
+#define UL_IDX(idx, n, tag) ::ul::ul_checked_index((idx), (n), (tag))
+#else
+#define UL_IDX(idx, n, tag) (idx)
+#endif
+
 struct Geo {
     int L, Nt;  // extent of x, y, z and of t
     int Lh;     // L / 2
@@ -58,7 +92,8 @@ __device__ __forceinline__ Site site_step(const Geo& g, Site s, int d, int delta
 // Offset of link (mu, s) in a [mu][parity][h] array.
 __device__ __forceinline__ int link_offset(const Geo& g, int mu, const Site& s)
 {
-    return (mu * 2 + site_parity(s)) * g.Vh + (lex_index(g, s) >> 1);
+    return static_cast<int>(UL_IDX((mu * 2 + site_parity(s)) * g.Vh + (lex_index(g, s) >> 1), 8LL * g.Vh,
+                                   kChkLinkOffset));
 }
 
 // Site from a lexicographic index.

@@ -14,6 +14,11 @@ struct Geo;
 // Largest number of time slabs one multilevel level may have.
 constexpr int kMaxSlabs = 256;
 
+// Check word of the FP64 (R = double) or FP32 (R = float) kernel unit in the
+// bounds-checked build (see UL_IDX in ul_device.cuh); 0 in the default build.
+template <typename R>
+cudaError_t check_word(unsigned long long* out, bool clear);
+
 template <typename R>
 cudaError_t launch_hot_start(const Geo& g, R* theta, void* cs, uint64_t seed, cudaStream_t st);
 

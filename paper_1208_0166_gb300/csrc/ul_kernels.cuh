@@ -132,7 +132,12 @@ __device__ __forceinline__ T ld_link(const T* p)
 template <typename R, bool CG = false>
 __device__ __forceinline__ Cx<R> load_link(const cs_t<R>* __restrict__ cs, int Vh, int dir, int par, int j)
 {
+#ifdef UL_CHECK
+    j = static_cast<int>(UL_IDX(j, 2LL * Vh, kChkNeighbour));
+    const cs_t<R> v = ld_link<cs_t<R>, CG>(cs + UL_IDX((dir * 2 + par) * Vh + (j >> 1), 8LL * Vh, kChkStaple));
+#else
     const cs_t<R> v = ld_link<cs_t<R>, CG>(cs + (dir * 2 + par) * Vh + (j >> 1));
+#endif
     return Cx<R>{v.x, v.y};
 }
 
@@ -232,7 +237,7 @@ __device__ __forceinline__ bool update_link(const Geo& g, R* __restrict__ theta,
     if (MU != 1) staple_term<R, MU, (MU == 1 ? 2 : 1), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
     if (MU != 2) staple_term<R, MU, (MU == 2 ? 3 : 2), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
     if (MU != 3) staple_term<R, MU, (MU == 3 ? 0 : 3), CG>(A, cs, Vh, p, i, c, L, Nt, up_mu);
-    const int off = (MU * 2 + p) * Vh + h;
+    const int off = static_cast<int>(UL_IDX((MU * 2 + p) * Vh + h, 8LL * Vh, kChkOwnLink));
     const R th = ld_link<R, CG>(theta + off);
     R nth;
     cs_t<R> ncs;
@@ -500,11 +505,15 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
         const int x1 = (px + r) % g.L + pyz;
         const Cx<R> T = cmul_rn(w0, slab_line<R, CG>(g, cs, x1, t0, slab_t));
         const Cx<R> Tc = (ubar && r >= 2) ? cmul_rn(w0m, slab_line_mh<R, CG>(g, ubar, x1, t0, slab_t)) : T;
-        const long ai = static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0;
+        const long ai = UL_IDX(static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0,
+                               static_cast<long long>(S) * r_max * g.L3, kChkAsum);
         double2 av = ld_link<double2, CG>(asum + ai);
         av.x += static_cast<double>(Tc.re);
         av.y += static_cast<double>(Tc.im);
         asum[ai] = av;
+#ifdef UL_CHECK
+        if (fields && (slot < 0 || x1 < 0 || x1 >= g.L3)) (void)UL_IDX(-1, 0, kChkSample);
+#endif
         if (fields) tk[(static_cast<long>(slot * S + s) * r_max + (r - 1)) * g.L3 + x0] = T;
     }
     if (!fields) return;
@@ -531,7 +540,12 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
         o[ch] = acc[ch];
+#ifdef UL_CHECK
+        const long oi = UL_IDX(static_cast<long>(ch) * SL3 + k, 8LL * SL3, kChkOsum);
+        osum[oi] = ld_link<double, CG>(osum + oi) + static_cast<double>(acc[ch]);
+#else
         osum[ch * SL3 + k] = ld_link<double, CG>(osum + ch * SL3 + k) + static_cast<double>(acc[ch]);
+#endif
     }
 }
 
@@ -1125,7 +1139,27 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
     }
 }
 
+// Check word of this translation unit (bounds-checked build; 0 and nothing to clear in the
+// default build).  The template parameter only selects the FP64 or FP32 unit.
+template <typename R>
+cudaError_t check_word(unsigned long long* out, bool clear)
+{
+#ifdef UL_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_ul_check_word, sizeof(unsigned long long));
+    if (e == cudaSuccess && clear) {
+        const unsigned long long zero = 0;
+        e = cudaMemcpyToSymbol(g_ul_check_word, &zero, sizeof zero);
+    }
+    return e;
+#else
+    (void)clear;
+    *out = 0;
+    return cudaSuccess;
+#endif
+}
+
 #define UL_INSTANTIATE_KERNELS(R)                                                                                  \
+    template cudaError_t check_word<R>(unsigned long long*, bool);                                                 \
     template cudaError_t launch_measure_sym<R>(const Geo&, const void*, int, int, int, int, double2*, void*,       \
                                                void*, void*, double*, cudaStream_t);                              \
     template cudaError_t launch_insertion_contract_sym<R>(const Geo&, int, int, int, int, const void*,             \

@@ -117,6 +117,9 @@ int ul_plaquette_noalloc(const double* theta_dev, int L, int Nt, double* out_dev
     if (partials_for_current_device(&partials) != cudaSuccess) return UL_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int nb = static_cast<int>((V + kNoAllocThreads - 1) / kNoAllocThreads);
+    // An error left pending on this thread by earlier, unrelated work is cleared here, so
+    // that only this call's own launch errors are reported below.
+    (void)cudaGetLastError();
     noalloc_plaquette_partials<<<nb, kNoAllocThreads, 0, st>>>(theta_dev, L, Nt, partials);
     noalloc_plaquette_finish<<<1, kNoAllocThreads, 0, st>>>(partials, nb, 1.0 / (6.0 * static_cast<double>(V)),
                                                              out_dev);

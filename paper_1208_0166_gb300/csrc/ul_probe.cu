@@ -1,0 +1,157 @@
+// ul_probe.cu — measured ceilings for the roofline of the update and measurement kernels:
+// the read bandwidth of data resident in L2, and the FP64 and FP32 fused multiply-add
+// rates.  The paper has no counterpart; these are the denominators against which the
+// link-update kernels are reported (a 24^4 lattice with its phase cache is 16 MB in FP32
+// and 32 MB in FP64, resident in the 129 MB L2 across a sweep; the FP64 update is bound by
+// the FP64 pipe).
+#include <cstdint>
+
+#include "../../include/ul_probe.h"
+#include "../../include/ul.h"
+
+namespace {
+
+constexpr int kProbeThreads = 512;
+
+// Every thread reads 16-byte words of the buffer with a grid stride, reps times, through L2
+// only (ld.global.cg, so the repeated passes cannot be served by L1).  The XOR of the words
+// is stored only if it equals a value it cannot take for the buffer's contents (zeros), so
+// the loads stay live.
+__global__ void __launch_bounds__(kProbeThreads) l2_read_kernel(const uint4* __restrict__ buf, long long n16, int reps,
+                                                               uint4* __restrict__ sink)
+{
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    uint4 acc = make_uint4(0, 0, 0, 0);
+    for (int r = 0; r < reps; ++r) {
+        for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n16; k += stride) {
+            const uint4 v = __ldcg(buf + k);
+            acc.x ^= v.x;
+            acc.y ^= v.y;
+            acc.z ^= v.z;
+            acc.w ^= v.w;
+        }
+    }
+    if (acc.x == 0x9e3779b9u && acc.y == 0x7f4a7c15u) sink[blockIdx.x] = acc;
+}
+
+// kChains independent multiply-add chains per thread, kIters steps each: 2 kChains kIters
+// floating-point operations per thread.  a <- a * b + c with b slightly below 1 keeps every
+// value finite; the result is stored only if it is NaN (never), so the chains stay live.
+constexpr int kChains = 8;
+constexpr int kIters = 2048;
+
+template <typename R>
+__global__ void __launch_bounds__(256) fma_kernel(R b, R c, R* __restrict__ sink)
+{
+    R a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) a[j] = static_cast<R>(threadIdx.x + j);
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int j = 0; j < kChains; ++j) a[j] = fma(a[j], b, c);
+    }
+    R s = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) s += a[j];
+    if (s != s) sink[blockIdx.x] = s;
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+// Best of `trials` timings of launch() on stream st, in milliseconds (CUDA events).
+template <class F>
+cudaError_t best_time(cudaStream_t st, int trials, F launch, float* best_ms)
+{
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    *best_ms = 1e30f;
+    for (int t = 0; t < trials && e == cudaSuccess; ++t) {
+        cudaEventRecord(e0, st);
+        launch();
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < *best_ms) *best_ms = ms;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+} // namespace
+
+extern "C" {
+
+int ul_probe_l2_read(size_t bytes, int reps, double* gbs, void* cuda_stream)
+{
+    if (!gbs || bytes < (1u << 20) || bytes > (size_t(1) << 30) || reps < 1 || reps > 4096) return UL_EINVAL;
+    const int sms = sm_count();
+    if (sms <= 0) return UL_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long n16 = static_cast<long long>(bytes / 16);
+    const int blocks = sms * 4;
+    void* buf = nullptr;
+    void* sink = nullptr;
+    if (cudaMalloc(&buf, n16 * 16) != cudaSuccess) return UL_ENOMEM;
+    if (cudaMalloc(&sink, blocks * sizeof(uint4)) != cudaSuccess) {
+        cudaFree(buf);
+        return UL_ENOMEM;
+    }
+    int rc = UL_OK;
+    float ms = 0.f;
+    if (cudaMemsetAsync(buf, 0, n16 * 16, st) != cudaSuccess) rc = UL_ECUDA;
+    if (rc == UL_OK) {
+        // one pass first brings the buffer into L2
+        l2_read_kernel<<<blocks, kProbeThreads, 0, st>>>(static_cast<const uint4*>(buf), n16, 1,
+                                                         static_cast<uint4*>(sink));
+        const cudaError_t e = best_time(st, 5, [&] {
+            l2_read_kernel<<<blocks, kProbeThreads, 0, st>>>(static_cast<const uint4*>(buf), n16, reps,
+                                                             static_cast<uint4*>(sink));
+        }, &ms);
+        if (e != cudaSuccess) rc = UL_ECUDA;
+    }
+    if (rc == UL_OK) *gbs = static_cast<double>(n16) * 16.0 * reps / (ms * 1e-3) / 1e9;
+    cudaFree(buf);
+    cudaFree(sink);
+    return rc;
+}
+
+int ul_probe_fma(int precision, double* tflops, void* cuda_stream)
+{
+    if (!tflops || (precision != UL_FP64 && precision != UL_FP32_ACC64)) return UL_EINVAL;
+    const int sms = sm_count();
+    if (sms <= 0) return UL_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int blocks = sms * 8;
+    void* sink = nullptr;
+    if (cudaMalloc(&sink, blocks * sizeof(double)) != cudaSuccess) return UL_ENOMEM;
+    float ms = 0.f;
+    cudaError_t e;
+    if (precision == UL_FP64)
+        e = best_time(st, 5, [&] { fma_kernel<double><<<blocks, 256, 0, st>>>(0.9999999, 1e-7, static_cast<double*>(sink)); },
+                      &ms);
+    else
+        e = best_time(st, 5, [&] { fma_kernel<float><<<blocks, 256, 0, st>>>(0.9999f, 1e-4f, static_cast<float*>(sink)); },
+                      &ms);
+    cudaFree(sink);
+    if (e != cudaSuccess) return UL_ECUDA;
+    const double flop = 2.0 * kChains * kIters * static_cast<double>(blocks) * 256.0;
+    *tflops = flop / (ms * 1e-3) / 1e12;
+    return UL_OK;
+}
+
+} // extern "C"

@@ -116,7 +116,8 @@ __device__ __forceinline__ void slab_staple_term(Cx<R>& A, const SlabLinks<R, LC
 __device__ __forceinline__ int slab_global_offset(const Geo& g, int dir, int x, int y, int zg, int tg)
 {
     const int i = x + g.L * (y + g.L * (zg + g.L * tg));
-    return (dir * 2 + ((x + y + zg + tg) & 1)) * g.Vh + (i >> 1);
+    return static_cast<int>(UL_IDX((dir * 2 + ((x + y + zg + tg) & 1)) * g.Vh + (i >> 1), 8LL * g.Vh,
+                                   kChkSlabGlobal));
 }
 
 // Class (MU, p) of this CTA: thread tid updates the links at half index hl = tid (+ nthr ...)

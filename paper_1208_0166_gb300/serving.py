@@ -25,19 +25,38 @@ def job_from(spec: dict) -> _lib.Job:
 
 
 class Server:
+    """record=True keeps, per tick, the update passes enqueued so far for every job in
+    flight (ul_batch_job_info), so that a caller can check which jobs advanced together."""
+
     def __init__(self, precision: int = _lib.UL_FP32_ACC64, hbm_budget_bytes: int = 8 << 30,
-                 passes_per_tick: int = 4, cuda_stream: int | None = None):
+                 passes_per_tick: int = 4, cuda_stream: int | None = None, record: bool = False):
         self.batch = _lib.Batch(precision, hbm_budget_bytes, cuda_stream)
         self.passes_per_tick = passes_per_tick
         self.inflight = {}   # job id -> (request index, arrival time)
         self.done = {}       # request index -> result dict with latency
+        self.record = record
+        self.trace = []      # per tick: {request index: passes enqueued so far}
+        self.submitted_at_tick = {}  # request index -> number of ticks run before its submission
+        self.ticks = 0
+        self.max_resident = 0
 
     def submit(self, index: int, spec: dict, arrival: float) -> None:
         jid = self.batch.submit(job_from(spec))
         self.inflight[jid] = (index, arrival)
+        self.submitted_at_tick[index] = self.ticks
 
     def tick(self) -> None:
         self.batch.step(self.passes_per_tick)
+        self.ticks += 1
+        running = 0
+        progress = {}
+        for jid, (index, _) in self.inflight.items():
+            st, done, _total = self.batch.job_info(jid)
+            running += st == _lib.UL_JOB_RUNNING
+            progress[index] = done
+        self.max_resident = max(self.max_resident, running)
+        if self.record:
+            self.trace.append(progress)
         now = time.perf_counter()
         for jid in list(self.inflight):
             r = self.batch.poll(jid)
@@ -68,7 +87,7 @@ class Server:
         summary = {"jobs": len(self.done), "wall_s": wall, "jobs_per_s": len(self.done) / wall,
                    "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
                    "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
-                   "stats": self.batch.stats()}
+                   "max_resident": self.max_resident, "stats": self.batch.stats()}
         return self.done, summary
 
     def close(self):

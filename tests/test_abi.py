@@ -71,3 +71,16 @@ def test_invalid_shapes_rejected_before_touching_the_device(lib):
     assert b"even" in lib.ul_last_error(None)
     assert lib.ul_init_ex(ctypes.byref(h), 4, 4, 1.0, 1, 7) == _lib.UL_EINVAL
     assert h.value is None
+
+
+def test_checked_build_loads_and_says_so():
+    """libul_check.so exports the same entry points; ul_check_enabled needs no GPU."""
+    from paper_1208_0166_gb300 import build
+
+    build.build(check=True)
+    lib_default = ctypes.CDLL(build.LIB)
+    lib_check = ctypes.CDLL(build.LIB_CHECK)
+    assert lib_default.ul_check_enabled() == 0
+    assert lib_check.ul_check_enabled() == 1
+    missing = [n for n in declared_functions() if not hasattr(lib_check, n)]
+    assert not missing, missing

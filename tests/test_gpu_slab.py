@@ -10,11 +10,11 @@ import pytest
 
 import oracle as O
 from paper_1208_0166_gb300 import _lib
+from tests.tolerances import compare64
 
 pytestmark = pytest.mark.gpu
 
 ANGLE_TOL = 1e-10
-OBS_TOL = 1e-12
 
 
 def angle_diff(a, b):
@@ -45,9 +45,7 @@ def test_slab_resident_matches_oracle_fp64(L, Nt, tau, cluster):
         c.sweep(1, 3)
     cr = c.multilevel(tau, n_sub, r_max, d_max=d_max)
     assert angle_diff(g.get_links(), c.theta).max() <= ANGLE_TOL
-    assert np.max(np.abs(gr["corr"] - cr["corr"])) < OBS_TOL
-    assert np.max(np.abs(gr["fields"] - cr["fields"])) < OBS_TOL
-    assert np.max(np.abs(gr["vac"] - cr["vac"])) < OBS_TOL
+    compare64(gr, cr, L, Nt, tau, n_sub)
 
 
 @pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])

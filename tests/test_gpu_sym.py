@@ -1,5 +1,7 @@
 """Symmetrised insertions (ul_multilevel_fields_sym) against the oracle's symmetrised
-estimator: the same trajectory (FP64 links bit for bit) and observables within 1e-12."""
+estimator: the same trajectory (FP64 links bit for bit) and observables element by element
+within 1e-12 relative plus the rounding bound of a reordered sum; FP32 against FP64 on frozen
+configurations within the FP32 rounding bound (tests/tolerances.py)."""
 from __future__ import annotations
 
 import numpy as np
@@ -7,10 +9,9 @@ import pytest
 
 import oracle as O
 from paper_1208_0166_gb300 import _lib
+from tests.tolerances import compare32_frozen, compare64
 
 pytestmark = pytest.mark.gpu
-
-OBS_TOL = 1e-12
 
 
 def angle_diff(a, b):
@@ -27,8 +28,7 @@ def test_symmetrised_matches_oracle_fp64(L, Nt, tau, seed):
     gr = g.multilevel_fields_sym(tau, n_sub, r_max, d_max)
     cr = c.multilevel_sym(tau, n_sub, r_max, d_max)
     assert angle_diff(g.get_links(), c.theta).max() == 0.0
-    for key in ("corr", "fields", "vac"):
-        assert np.max(np.abs(np.asarray(gr[key]) - np.asarray(cr[key]))) < OBS_TOL, key
+    compare64(gr, cr, L, Nt, tau, n_sub, frames=24)
 
 
 def test_symmetrised_frozen_configuration_fp32_close_to_fp64():
@@ -49,8 +49,8 @@ def test_symmetrised_frozen_configuration_fp32_close_to_fp64():
         g.set_option("sub_metro", 0)
         g.set_option("sub_or", 0)
         res.append(g.multilevel_fields_sym(2, 2, 3, 3))
-    for key in ("corr", "fields", "vac"):
-        assert np.max(np.abs(np.asarray(res[0][key]) - np.asarray(res[1][key]))) < 2e-6, key
+    print("8^4 24-frame FP32 vs FP64 |diff| / tol:",
+          compare32_frozen(res[1], res[0], 8, 8, 2, frames=24, require_sensitive=False))
 
 
 @pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
@@ -171,8 +171,7 @@ def test_symmetrised_largest_separation_and_offset_match_oracle_fp64():
     gr = g.multilevel_fields_sym(tau, n_sub, r_max, d_max)
     cr = c.multilevel_sym(tau, n_sub, r_max, d_max)
     assert angle_diff(g.get_links(), c.theta).max() == 0.0
-    for key in ("corr", "fields", "vac"):
-        assert np.max(np.abs(np.asarray(gr[key]) - np.asarray(cr[key]))) < OBS_TOL, key
+    compare64(gr, cr, L, Nt, tau, n_sub, frames=24)
 
 
 def test_symmetrised_full_size_fp32_tiled_close_to_fp64():
@@ -190,5 +189,7 @@ def test_symmetrised_full_size_fp32_tiled_close_to_fp64():
         g.set_option("sub_or", 0)
         res.append(g.multilevel_fields_sym(2, 2, 8, 6))
         g.close()
-    for key in ("corr", "fields", "vac"):
-        assert np.max(np.abs(np.asarray(res[0][key]) - np.asarray(res[1][key]))) < 2e-6, key
+    # every element against the FP32 rounding bound; a 1e-3 relative error of any C(r), r >= 2,
+    # or of 99 % of the field elements exceeds its tolerance
+    ratios, sens = compare32_frozen(res[1], res[0], 24, 24, 2, frames=24, label="24^4 24-frame")
+    print("24^4 24-frame FP32 vs FP64 |diff| / tol:", ratios, "sensitive fraction:", sens)
