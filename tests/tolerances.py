@@ -40,6 +40,13 @@ import math
 
 import numpy as np
 
+# Field elements are sums with cancellation: a few per cent of them lie within 1000 times
+# their rounding bound of zero (by chance, or, for the 24-frame average, because the Im part
+# of a transverse channel nearly cancels between mirror frames); a 1e-3 relative error of
+# such an element is below rounding and cannot be detected.  Every correlator element and
+# at least this fraction of the field elements must be sensitive to a 1e-3 relative error.
+FIELD_SENSITIVE = 0.95
+
 U64 = 2.0 ** -53
 U32 = 2.0 ** -23
 BIAS32 = 2.0 ** -22
@@ -140,7 +147,8 @@ def plaquette_tol64(want: float, V: int) -> float:
 def compare64(got, want, L, Nt, tau, n_sub, frames=1, slab_factors=None, label="", require_sensitive=False):
     """FP64 CUDA result against the oracle's, element by element (tol64).  Accepts result
     dicts or bare correlator arrays.  With require_sensitive, also asserts that a 1e-3
-    relative error of any correlator element at r >= 2 would exceed its tolerance."""
+    relative error of any correlator element at r >= 2, and of at least FIELD_SENSITIVE of
+    the field elements, would exceed its tolerance."""
     if not isinstance(want, dict):
         got, want = {"corr": np.asarray(got)}, {"corr": np.asarray(want)}
     tol = fp64_tolerances(want, L, Nt, tau, n_sub, frames, slab_factors)
@@ -148,7 +156,7 @@ def compare64(got, want, L, Nt, tau, n_sub, frames=1, slab_factors=None, label="
     if require_sensitive:
         sens = sensitivity(want, tol)
         assert sens.get("corr", 1.0) == 1.0, (label, sens)
-        assert sens.get("fields", 1.0) >= 0.99, (label, sens)
+        assert sens.get("fields", 1.0) >= FIELD_SENSITIVE, (label, sens)
     return ratios
 
 
@@ -159,5 +167,5 @@ def compare32_frozen(got, want, L, Nt, tau, frames=1, label="", require_sensitiv
     sens = sensitivity(want, tol)
     if require_sensitive:
         assert sens.get("corr", 1.0) == 1.0, (label, sens)
-        assert sens.get("fields", 1.0) >= 0.99, (label, sens)
+        assert sens.get("fields", 1.0) >= FIELD_SENSITIVE, (label, sens)
     return ratios, sens
