@@ -627,6 +627,42 @@ def run_serve(args):
     return 0
 
 
+def run_sweep_scaling(args):
+    """Time per class launch of the compound sweep (1 Metropolis + 3 OR passes, 32 class
+    launches, graph replay) against the lattice size, both precisions, and the floor of a
+    chain of empty dependent launches: separates the fixed cost of a class launch from the
+    cost per link."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1208_0166_gb300 import _lib as lib
+
+    lib.load()
+    rows = []
+    for prec, name, sizes, n in ((lib.UL_FP32_ACC64, "fp32", (12, 16, 20, 24, 28, 32), 50),
+                                 (lib.UL_FP64, "fp64", (12, 16, 20, 24), 10)):
+        for L in sizes:
+            st = torch.cuda.Stream()
+            lat = lib.Lattice(L, L, 1.0, 1, prec)
+            lat.set_stream(st.cuda_stream)
+            for _ in range(10):
+                lat.sweep(1, 3)
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(n):
+                lat.sweep(1, 3)
+            e1.record(st)
+            st.synchronize()
+            rows.append({"precision": name, "L": L, "links_per_class": L ** 4 // 2,
+                         "us_per_class": e0.elapsed_time(e1) * 1e3 / (n * 32)})
+            lat.close()
+    floor = [{"blocks": b, "threads": t, "pdl": p, "us_per_kernel": lib.probe_launch_floor(b, t, p)}
+             for p in (False, True) for b, t in ((1, 32), (152, 160), (288, 576), (1037, 160))]
+    print(json.dumps({"workload_mode": "sweep-scaling", "classes": rows, "launch_floor": floor}), flush=True)
+    return 0
+
+
 def profile_step(args):
     """One step of the workload with no timing and no output (for profiler captures)."""
     import torch
@@ -771,7 +807,7 @@ def main():
     ap.add_argument("--pipeline", type=int, default=0, choices=[0, 1],
                     help="1: collect each configuration's level after queueing the next one's sweeps "
                          "(ul_multilevel_fields_begin/_end; one-level estimator only)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep-scaling"],
                     help="single: the 24^4 configuration step (default); batch: 32 uneven lattices; "
                          "serve: Poisson stream through the continuous-batching loop")
     ap.add_argument("--serve-jobs", type=int, default=48)
@@ -792,6 +828,8 @@ def main():
         if args.precision == "fp64" and "--precision" not in sys.argv:
             args.precision = "fp32"
         return run_batch(args)
+    if args.workload == "sweep-scaling":
+        return run_sweep_scaling(args)
     if args.workload == "serve":
         if "--precision" not in sys.argv:
             args.precision = "fp32"

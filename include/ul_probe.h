@@ -29,6 +29,14 @@ int ul_probe_l2_read(size_t bytes, int reps, double* gbs, void* cuda_stream);
  * UL_FP32_ACC64 (1) for FP32. */
 int ul_probe_fma(int precision, double* tflops, void* cuda_stream);
 
+/* ul_probe_launch_floor — time per kernel (microseconds) of a chain of 1000 empty kernels of
+ * `blocks` blocks of `threads` threads (a multiple of 32, <= 1024) replayed from a CUDA graph,
+ * each waiting for its predecessor; pdl != 0 launches them with programmatic dependent
+ * launch.  The floor under any chain of dependent launches, such as the class updates of a
+ * compound sweep (Section 2.1: each (direction, parity) class reads the links the previous
+ * class wrote). */
+int ul_probe_launch_floor(int blocks, int threads, int pdl, double* us_per_kernel, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

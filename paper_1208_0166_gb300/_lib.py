@@ -77,6 +77,7 @@ SIGNATURES = [
     ("ul_check_status", _I, [ctypes.POINTER(ctypes.c_ulonglong), _I]),
     ("ul_probe_l2_read", _I, [ctypes.c_size_t, _I, _DP, _P]),
     ("ul_probe_fma", _I, [_I, _DP, _P]),
+    ("ul_probe_launch_floor", _I, [_I, _I, _I, _DP, _P]),
 ]
 
 
@@ -367,4 +368,11 @@ def probe_fma(precision: int, cuda_stream=None) -> float:
     """ul_probe_fma: FP64 (UL_FP64) or FP32 (UL_FP32_ACC64) fused multiply-add TFLOP/s."""
     out = ctypes.c_double()
     _check(load().ul_probe_fma(int(precision), ctypes.byref(out), cuda_stream))
+    return out.value
+
+
+def probe_launch_floor(blocks: int, threads: int, pdl: bool, cuda_stream=None) -> float:
+    """ul_probe_launch_floor: microseconds per kernel of a chain of empty dependent kernels."""
+    out = ctypes.c_double()
+    _check(load().ul_probe_launch_floor(int(blocks), int(threads), 1 if pdl else 0, ctypes.byref(out), cuda_stream))
     return out.value

@@ -172,30 +172,46 @@ __device__ __forceinline__ void staple_term(Cx<R>& A, const cs_t<R>* __restrict_
                    load_link<R, CG>(cs, Vh, NU, q, i + dn_nu));
 }
 
-// Metropolis decision for a link with angle th, phase old() = (cos th, sin th) (read after
-// the proposal is formed, which keeps it out of registers during the generator) and staple
-// sum A; the two uniforms come from Philox(counter (link_id, pass, 0, 0), key (seed, 1)).
-// Proposal wrap(fma(width, 2 u1 - 1, th)); action change
-// dS = beta [(cos th - cos th') Re A - (sin th - sin th') Im A] = beta fma(dc, Re A, -(ds Im A)).
-// On acceptance returns true with the new angle and phase in nth, ncs.
-template <typename R, class OldPhase>
-__device__ __forceinline__ bool metropolis_new(R th, OldPhase old_phase, Cx<R> A, uint64_t link_id, uint64_t pass,
-                                               uint64_t seed, R width, R beta, R& nth, cs_t<R>& ncs)
+// Metropolis proposal and decision for a link with angle th, phase old = (cos th, sin th)
+// and staple sum A; the two uniforms come from Philox(counter (link_id, pass, 0, 0), key
+// (seed, 1)).  Proposal th' = wrap(fma(width, 2 u1 - 1, th)) with its phase (cn, sn);
+// action change dS = beta [(cos th - cos th') Re A - (sin th - sin th') Im A]
+// = beta fma(dc, Re A, -(ds Im A)); accept iff u2 < exp(-dS).  metro_propose needs no
+// neighbour link, so a kernel may form the proposal before the links it reads are final.
+template <typename R>
+__device__ __forceinline__ void metro_propose(R th, uint64_t link_id, uint64_t pass, uint64_t seed, R width, R& prop,
+                                              R& sn, R& cn, R& u2)
 {
     using P = Prec<R>;
-    R u1, u2;
+    R u1;
     P::metro_uniforms(link_id, pass, seed, &u1, &u2);
-    const R prop = P::wrap(fma_r(width, R(2) * u1 - R(1), th));
-    const cs_t<R> old = old_phase();
-    R sn, cn;
+    prop = P::wrap(fma_r(width, R(2) * u1 - R(1), th));
     P::sincos(prop, &sn, &cn);
+}
+
+template <typename R>
+__device__ __forceinline__ bool metro_accept(cs_t<R> old, Cx<R> A, R beta, R prop, R sn, R cn, R u2, R& nth,
+                                             cs_t<R>& ncs)
+{
     const R dS = beta * fma_r(old.x - cn, A.re, -((old.y - sn) * A.im));
-    if (u2 < P::exp(-dS)) {
+    if (u2 < Prec<R>::exp(-dS)) {
         nth = prop;
         ncs = cs_t<R>{cn, sn};
         return true;
     }
     return false;
+}
+
+// One Metropolis hit (the phase old() is read after the proposal is formed, which keeps it
+// out of registers during the generator).  On acceptance returns true with the new angle
+// and phase in nth, ncs.
+template <typename R, class OldPhase>
+__device__ __forceinline__ bool metropolis_new(R th, OldPhase old_phase, Cx<R> A, uint64_t link_id, uint64_t pass,
+                                               uint64_t seed, R width, R beta, R& nth, cs_t<R>& ncs)
+{
+    R prop, sn, cn, u2;
+    metro_propose<R>(th, link_id, pass, seed, width, prop, sn, cn, u2);
+    return metro_accept<R>(old_phase(), A, beta, prop, sn, cn, u2, nth, ncs);
 }
 
 // Overrelaxation: the reflection th' = wrap(-2 arg(A) - th) with its phase.
@@ -280,15 +296,12 @@ cudaError_t launch_rng_uniforms(uint64_t seed, uint64_t pass, uint64_t link0, in
 }
 
 // Threads per block of the one-class-per-launch update kernel: at most kUpdateThreads (eight
-// warps); update_block_threads picks the size per launch.
+// warps) for the FP64 kernel, at most kWideThreads (eighteen warps) for the FP32 one;
+// update_block_threads / wide_block_threads pick the size per launch.
 constexpr int kUpdateThreads = 256;
+constexpr int kWideThreads = 576;
 
-// Block size (in threads, 2 to 8 warps) for a class launch of `work` links: the size whose
-// blocks, spread evenly over the SMs in one wave, put the fewest warps on the busiest SM
-// (each SM's share is bound by its FP64 pipe or its issue rate), the larger block on a
-// tie.  24^4: a full class (5,184 warps) 5 warps per block (35 warps on the busiest SM,
-// against 36 with 4), a masked spatial class (2,592 warps) 6 warps (18 against 20).
-inline int update_block_threads(long work)
+inline int sm_count_cached()
 {
     static std::atomic<int> sms_of[16]; // SM count per device, queried once (any thread)
     int dev = 0;
@@ -298,12 +311,29 @@ inline int update_block_threads(long work)
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
         sms_of[dev].store(sms, std::memory_order_relaxed);
     }
+    return sms;
+}
+
+// Warps on the busiest SM when `warps` warps in blocks of k warps spread evenly in one wave.
+inline long busiest_sm_warps(long warps, int k, int sms)
+{
+    const long blocks = (warps + k - 1) / k;
+    return (blocks + sms - 1) / sms * k;
+}
+
+// Block size (in threads, 2 to 8 warps) for a class launch of `work` links: the size whose
+// blocks, spread evenly over the SMs in one wave, put the fewest warps on the busiest SM
+// (each SM's share is bound by its FP64 pipe or its issue rate), the larger block on a
+// tie.  24^4: a full class (5,184 warps) 5 warps per block (35 warps on the busiest SM,
+// against 36 with 4), a masked spatial class (2,592 warps) 6 warps (18 against 20).
+inline int update_block_threads(long work)
+{
+    const int sms = sm_count_cached();
     const long warps = (work + 31) / 32;
     int best_k = 4;
     long best = -1;
     for (int k = 2; k <= kUpdateThreads / 32; ++k) {
-        const long blocks = (warps + k - 1) / k;
-        const long busiest = (blocks + sms - 1) / sms * k;
+        const long busiest = busiest_sm_warps(warps, k, sms);
         if (best < 0 || busiest < best || (busiest == best && k > best_k)) {
             best = busiest;
             best_k = k;
@@ -312,11 +342,32 @@ inline int update_block_threads(long work)
     return best_k * 32;
 }
 
+// Block size (2 to 18 warps) of the FP32 class launch: among the sizes whose busiest SM holds
+// at most 3 % more warps than the best balance, the one with the fewest blocks.  A launch
+// pays for every block it dispatches (a chain of empty kernels of ~1,000 blocks measured
+// 1.4 us per kernel, of 152 blocks 0.6 us), which matters for the FP32 class kernel of a
+// few microseconds.  24^4: a full class 18 warps (288 blocks, 36 warps on the busiest SM,
+// against 1,037 blocks and 35 warps with 5), a masked spatial class 18 warps (144 blocks).
+inline int wide_block_threads(long work)
+{
+    const int sms = sm_count_cached();
+    const long warps = (work + 31) / 32;
+    long best = -1;
+    for (int k = 2; k <= kWideThreads / 32; ++k) {
+        const long b = busiest_sm_warps(warps, k, sms);
+        if (best < 0 || b < best) best = b;
+    }
+    int pick = 2;
+    for (int k = 2; k <= kWideThreads / 32; ++k)
+        if (busiest_sm_warps(warps, k, sms) * 100 <= best * 103) pick = k; // largest k = fewest blocks
+    return pick * 32;
+}
+
 // With compact_tau > 1 and mu != 0 the grid covers only the unfrozen time slices (those
 // with t % compact_tau != 0): thread q maps to the q-th link of those slices.
 template <typename R, int LC>
-__global__ void __launch_bounds__(kUpdateThreads, 5)
-    update_class_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int mu, UpdateArgs a, int compact_tau)
+__device__ __forceinline__ void update_class_body(const Geo& g, R* __restrict__ theta, cs_t<R>* __restrict__ cs,
+                                                  int mu, const UpdateArgs& a, int compact_tau)
 {
     int h = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = h < g.Vh;
@@ -349,6 +400,22 @@ __global__ void __launch_bounds__(kUpdateThreads, 5)
         const unsigned mask = __ballot_sync(0xffffffffu, acc);
         if ((threadIdx.x & 31) == 0 && mask) atomicAdd(a.accepted, static_cast<unsigned long long>(__popc(mask)));
     }
+}
+
+template <typename R, int LC>
+__global__ void __launch_bounds__(kUpdateThreads, 5)
+    update_class_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int mu, UpdateArgs a, int compact_tau)
+{
+    update_class_body<R, LC>(g, theta, cs, mu, a, compact_tau);
+}
+
+// The same update in blocks of up to 18 warps, two blocks per SM (FP32 class launches).
+template <typename R, int LC>
+__global__ void __launch_bounds__(kWideThreads, 2)
+    update_class_wide_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, int mu, UpdateArgs a,
+                             int compact_tau)
+{
+    update_class_body<R, LC>(g, theta, cs, mu, a, compact_tau);
 }
 
 // ---------------------------------------------------------------------------
@@ -973,7 +1040,8 @@ cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int pa
     if (work == 0) return cudaSuccess; // slab_t == 1: every spatial link is frozen
     *launched = 1;
     cudaLaunchConfig_t cfg{};
-    const int threads = update_block_threads(work);
+    const bool wide = sizeof(R) == 4;
+    const int threads = wide ? wide_block_threads(work) : update_block_threads(work);
     cfg.gridDim = dim3(static_cast<unsigned>((work + threads - 1) / threads));
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = 0;
@@ -983,6 +1051,17 @@ cudaError_t launch_update_class(const Geo& g, R* theta, void* cs, int mu, int pa
     attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (wide) {
+        switch (g.L) {
+        case 8: return cudaLaunchKernelEx(&cfg, update_class_wide_kernel<R, 8>, g, theta, c, mu, a, compact);
+        case 12: return cudaLaunchKernelEx(&cfg, update_class_wide_kernel<R, 12>, g, theta, c, mu, a, compact);
+        case 16: return cudaLaunchKernelEx(&cfg, update_class_wide_kernel<R, 16>, g, theta, c, mu, a, compact);
+        case 20: return cudaLaunchKernelEx(&cfg, update_class_wide_kernel<R, 20>, g, theta, c, mu, a, compact);
+        case 24: return cudaLaunchKernelEx(&cfg, update_class_wide_kernel<R, 24>, g, theta, c, mu, a, compact);
+        case 32: return cudaLaunchKernelEx(&cfg, update_class_wide_kernel<R, 32>, g, theta, c, mu, a, compact);
+        default: return cudaLaunchKernelEx(&cfg, update_class_wide_kernel<R, 0>, g, theta, c, mu, a, compact);
+        }
+    }
     switch (g.L) {
     case 8: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 8>, g, theta, c, mu, a, compact);
     case 12: return cudaLaunchKernelEx(&cfg, update_class_kernel<R, 12>, g, theta, c, mu, a, compact);

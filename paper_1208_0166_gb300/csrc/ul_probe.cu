@@ -56,6 +56,15 @@ __global__ void __launch_bounds__(256) fma_kernel(R b, R c, R* __restrict__ sink
     if (s != s) sink[blockIdx.x] = s;
 }
 
+// An empty kernel of a dependent chain: waits for its predecessor (programmatic dependent
+// launch), then lets its successor be scheduled.  The store never happens (flag is 0).
+__global__ void chain_kernel(int* flag)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (threadIdx.x == 0 && blockIdx.x == 0 && flag[0] == 12345) flag[1] = 1;
+}
+
 int sm_count()
 {
     int dev = 0, sms = 0;
@@ -95,6 +104,47 @@ cudaError_t best_time(cudaStream_t st, int trials, F launch, float* best_ms)
 } // namespace
 
 extern "C" {
+
+int ul_probe_launch_floor(int blocks, int threads, int pdl, double* us_per_kernel, void* cuda_stream)
+{
+    if (!us_per_kernel || blocks < 1 || blocks > 65535 || threads < 1 || threads > 1024 || (threads & 31))
+        return UL_EINVAL;
+    constexpr int kChain = 1000;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int* flag = nullptr;
+    if (cudaMalloc(&flag, 2 * sizeof(int)) != cudaSuccess) return UL_ENOMEM;
+    int rc = UL_OK;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    if (cudaMemsetAsync(flag, 0, 2 * sizeof(int), st) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+        rc = UL_ECUDA;
+    if (rc == UL_OK && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = UL_ECUDA;
+    if (rc == UL_OK) {
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(threads);
+        cfg.stream = cap;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        for (int k = 0; k < kChain; ++k) cudaLaunchKernelEx(&cfg, chain_kernel, flag);
+        if (cudaStreamEndCapture(cap, &graph) != cudaSuccess) rc = UL_ECUDA;
+    }
+    if (rc == UL_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = UL_ECUDA;
+    float ms = 0.f;
+    if (rc == UL_OK && cudaGraphLaunch(exec, st) != cudaSuccess) rc = UL_ECUDA; // warm-up
+    if (rc == UL_OK && best_time(st, 5, [&] { cudaGraphLaunch(exec, st); }, &ms) != cudaSuccess) rc = UL_ECUDA;
+    if (rc == UL_OK) *us_per_kernel = ms * 1e3 / kChain;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    cudaFree(flag);
+    return rc;
+}
 
 int ul_probe_l2_read(size_t bytes, int reps, double* gbs, void* cuda_stream)
 {
