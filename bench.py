@@ -515,7 +515,10 @@ def _torch_setup():
     return torch, dist, ws, rank, local
 
 
-def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000):
+BATCH_OPTIONS = ("slab_levels", "tune")
+
+
+def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, options=None):
     """32 independent configurations of uneven sizes (8 each of 12^4, 16^4, 20^4, 24^4,
     beta from {0.96, 0.98, 1.0}) advanced together by the batch engine; a step is the
     whole batch run to completion (100 sweeps + one 200-sample level + reduction each)."""
@@ -525,6 +528,9 @@ def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000):
     specs = batch_jobs_uneven(seed_base + 100 * rank)
     stream = torch.cuda.Stream()
     b = lib.Batch(prec, 8 << 30, stream.cuda_stream)
+    for k, v in (options or {}).items():
+        if k in BATCH_OPTIONS:
+            b.set_option(k, v)
 
     def step():
         ids = [b.submit(job_from(sp)) for sp in specs]
@@ -545,10 +551,11 @@ def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000):
     stream.synchronize()
     ms = e0.elapsed_time(e1)
     st = b.stats()
+    slab_launches = b.plan(24, 24, 2)[1]
     b.close()
     samples = sum(sp["n_sub"] * (sp["Nt"] // sp["slab_t"]) * sp["L"] ** 3 * sp["r_max"] for sp in specs) * steps
     return {"ms": ms, "updates": st["link_updates"] - u0, "launches": st["launches"] - l0, "samples": samples,
-            "block_threads": st["block_threads"], "jobs": len(specs),
+            "block_threads": st["block_threads"], "jobs": len(specs), "slab_level_launches": slab_launches,
             "C_r_first_job": [[z.real, z.imag] for z in res[min(res)]["corr"][:3]]}
 
 
@@ -588,7 +595,7 @@ def run_batch(args):
     prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
     clocks = ClockSampler(local)
     clocks.start()
-    r = batch_result(lib, prec, args.steps, args.warmup, rank, dist, torch)
+    r = batch_result(lib, prec, args.steps, args.warmup, rank, dist, torch, options=_options(args))
     clk = clocks.stop()
     from paper_1208_0166_gb300.replicas import aggregate
 
@@ -599,7 +606,9 @@ def run_batch(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "jobs": r["jobs"], "block_threads": r["block_threads"]},
+            "config": {"workload": BATCH_WORKLOAD, "jobs": r["jobs"], "block_threads": r["block_threads"],
+                       "options": _options(args)},
+            "slab_level_launches": r["slab_level_launches"],
             "correlator_samples_per_s": r["samples"] * ws / t, "gpu_launches": r["launches"], "clocks": clk,
             "C_r_first_job": r["C_r_first_job"]}
     print(json.dumps(line), flush=True)
@@ -759,6 +768,10 @@ def run_ours(args):
     if not args.no_serve and ws == 1:
         r = serve_result(lib, lib.UL_FP32_ACC64, args.serve_jobs, args.serve_rate, rank, torch)
         serve = {**r, "dtype": "f32 (FP64 accumulation)"}
+        # the same request mix arriving faster than it is served: the service rate
+        sat = serve_result(lib, lib.UL_FP32_ACC64, 64, 200.0, rank, torch)
+        serve["saturated"] = {k: sat[k] for k in ("jobs_per_s", "p50_latency_s", "p99_latency_s", "jobs",
+                                                  "link_updates_per_s", "max_resident", "workload")}
 
     if rank != 0:
         return 0

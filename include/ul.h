@@ -402,12 +402,41 @@ int ul_batch_poll(ul_batch* b, uint64_t job_id, double* out, int* state);
 int ul_batch_job_info(ul_batch* b, uint64_t job_id, int* state, uint64_t* passes_done, uint64_t* passes_total);
 
 /* ul_batch_stats — link updates and kernel launches issued so far, the block size the
- * autotuner chose for the batched update kernel (128, 256 or 512 threads, timed on the
- * first passes; results do not depend on it) and the device bytes held by jobs. */
+ * last lockstep pass used (per shape of lattice the autotuner times 64/128/256 threads
+ * (FP64) or 128/288/576 (FP32) on the first passes, or reads the choice from the tune cache;
+ * results do not depend on it) and the device bytes held by jobs.  Link updates include
+ * those of slab-resident levels. */
 int ul_batch_stats(ul_batch* b, uint64_t* link_updates, uint64_t* launches, int* block_threads,
                    size_t* bytes_in_use);
 
-/* ul_batch_free — wait for the batch's stream and release everything (NULL accepted). */
+/* ul_batch_set_option — batch options (none changes a result):
+ *   "group_mb" (default 64, 1 .. 65536): the lockstep passes advance the jobs of one shape in
+ *       groups whose links (angles and phases) fit this many MiB, each group for a whole
+ *       step's passes in a row, so that its links stay in L2; each shape's passes run on a
+ *       stream of their own, the largest shapes on the highest-priority streams.
+ *   "slab_levels" (default 2): 1 runs a job's level as one slab-resident cluster launch where
+ *       its slab fits (Section 2.2: with the slab boundaries frozen, the sub-samples of a slab
+ *       read only its own links), shared by the jobs of one shape that reach their level in
+ *       the same step, on a stream beside the lockstep passes; 2 does so only where two of
+ *       that launch's CTAs fit one SM's shared memory (a level of larger slabs would hold
+ *       whole SMs that the other shapes' passes cannot share); 0 runs every level in the
+ *       lockstep passes.
+ *   "tune" (default 1): choose each shape's cluster size by timing every feasible size once
+ *       on a scratch lattice (a cudaMalloc/cudaFree, the first time a shape is seen) and keep
+ *       the choice in the tune cache, a JSON file ($UL_TUNE_CACHE, else $XDG_CACHE_HOME or
+ *       $HOME/.cache + /paper_1208_0166_gb300/tune.json; UL_TUNE_CACHE="" keeps it in
+ *       memory), which also records the lockstep block size per shape; 0 uses the largest
+ *       cluster whose slabs are all resident.
+ * UL_EINVAL for a value out of range or an unknown key. */
+int ul_batch_set_option(ul_batch* b, const char* key, double value);
+
+/* ul_batch_plan — *cluster = CTAs per slab of the slab-resident level the batch would use
+ * for jobs of shape (L, Nt, slab_t) (tuning it now if needed), 0 where the level runs in
+ * the lockstep passes; *slab_launches = slab-resident level launches so far.  Either output
+ * may be NULL. */
+int ul_batch_plan(ul_batch* b, int L, int Nt, int slab_t, int* cluster, uint64_t* slab_launches);
+
+/* ul_batch_free — wait for the batch's streams and release everything (NULL accepted). */
 int ul_batch_free(ul_batch* b);
 
 /* ul_batch_last_error — text of the last error on b. */

@@ -69,6 +69,8 @@ SIGNATURES = [
     ("ul_batch_submit", _I, [_P, ctypes.POINTER(Job), _U64P]),
     ("ul_batch_step", _I, [_P, _I, ctypes.POINTER(_I)]),
     ("ul_batch_poll", _I, [_P, _U64, _DP, ctypes.POINTER(_I)]),
+    ("ul_batch_set_option", _I, [_P, ctypes.c_char_p, _D]),
+    ("ul_batch_plan", _I, [_P, _I, _I, _I, ctypes.POINTER(_I), _U64P]),
     ("ul_batch_job_info", _I, [_P, _U64, ctypes.POINTER(_I), _U64P, _U64P]),
     ("ul_batch_stats", _I, [_P, _U64P, _U64P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
     ("ul_batch_free", _I, [_P]),
@@ -307,6 +309,15 @@ class Batch:
         out = np.zeros(2 * self._rmax[job_id] + 2)
         self._check(load().ul_batch_poll(self._b, int(job_id), _dp(out), ctypes.byref(st)))
         return st.value
+
+    def set_option(self, key: str, value: float) -> None:
+        self._check(load().ul_batch_set_option(self._b, key.encode(), float(value)))
+
+    def plan(self, L: int, Nt: int, slab_t: int):
+        """(cluster size of the slab-resident level for this shape, 0 = lockstep; level launches so far)."""
+        c, n = ctypes.c_int(), ctypes.c_uint64()
+        self._check(load().ul_batch_plan(self._b, int(L), int(Nt), int(slab_t), ctypes.byref(c), ctypes.byref(n)))
+        return c.value, n.value
 
     def job_info(self, job_id: int):
         """(state, passes_done, passes_total) of a job not yet collected."""

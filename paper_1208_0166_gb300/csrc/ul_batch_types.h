@@ -53,6 +53,24 @@ struct SlabArgs {
 
 constexpr int kMaxBatchJobs = 48;
 
+// One lattice of a slab-resident launch over several lattices of one shape (L, Nt, slab
+// thickness): its links, its Metropolis arguments (first pass, seed, coupling, width,
+// acceptance counter), its transporter accumulator and its own level schedule.
+struct SlabJob {
+    void* theta;
+    void* cs;
+    double2* asum;
+    UpdateArgs u;
+    int n_units, n_metro, n_or, r_max;
+};
+
+constexpr int kMaxSlabJobs = 16;
+
+struct SlabJobTable {
+    int njobs;
+    SlabJob job[kMaxSlabJobs];
+};
+
 struct BatchUpdateJob {
     void* theta;
     void* cs;

@@ -127,8 +127,16 @@ cudaError_t launch_persistent(const Geo& g, R* theta, void* cs, const PersistArg
 // cluster size only.
 template <typename R>
 cudaError_t slab_plan(const Geo& g, int tau, int force_cluster, int* cluster, int* threads);
+// Shared memory of one CTA of a slab-resident launch (cluster CTAs per slab).
+template <typename R>
+size_t slab_level_smem(const Geo& g, int tau, int cluster);
 template <typename R>
 cudaError_t launch_slab(const Geo& g, R* theta, void* cs, const SlabArgs& a, int threads, cudaStream_t st);
+
+// One slab-resident level for every lattice of a table (same shape g and plan); see
+// slab_jobs_kernel in ul_slab.cuh.
+template <typename R>
+cudaError_t launch_slab_jobs(const Geo& g, const SlabArgs& a, const SlabJobTable& t, int threads, cudaStream_t st);
 
 // One batched class update over every lattice of the table (blocks: sum of the lattices'
 // block counts at `threads` <= 128 threads per block; a masked spatial class counts only the
@@ -140,5 +148,17 @@ cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int thr
 // One batched transporter measurement (correlators only) over the lattices of the table.
 template <typename R>
 cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaStream_t st);
+
+// Lockstep class update of a group of lattices of one extent L (grid: blocks_x blocks of
+// `threads` per lattice, t.njobs lattices), and its measurement (blocks_x blocks of 256).
+template <typename R>
+cudaError_t launch_group_update(const BatchUpdateTable& t, int L, int blocks_x, int threads, int mu, int parity,
+                                cudaStream_t st, bool pdl);
+template <typename R>
+cudaError_t launch_group_measure(const BatchMeasureTable& t, int blocks_x, cudaStream_t st);
+
+// Block size of a one-class launch of `work` links (the single-lattice choice): FP32 wide
+// blocks, FP64 balanced blocks.
+int class_block_threads(long work, bool fp32);
 
 } // namespace ul

@@ -996,6 +996,58 @@ __global__ void __launch_bounds__(kThreads) batched_measure_kernel(const __grid_
                           nullptr, k);
 }
 
+// Lockstep class update of a group of lattices of one shape: the grid's y index selects the
+// lattice, its x extent covers the lattice's links of the class (threads beyond a lattice's
+// work do nothing).  Each link is updated by update_class_body with the lattice's own
+// arguments, so its new value is the single-lattice kernel's.
+template <typename R, int LC>
+__device__ __forceinline__ void group_update(const BatchUpdateTable& t, int mu, int parity)
+{
+    const BatchUpdateJob& J = t.job[blockIdx.y];
+    const Geo g = geo_of(J.L, J.Nt, J.V, J.Vh, J.L3);
+    UpdateArgs a;
+    a.parity = parity;
+    a.metro = J.metro;
+    a.slab_t = J.slab_t;
+    a.frozen_mask = J.frozen_mask;
+    a.pass = J.pass;
+    a.pass_base = nullptr;
+    a.seed = J.seed;
+    a.beta = J.beta;
+    a.width = J.width;
+    a.beta_f = static_cast<float>(J.beta);
+    a.width_f = static_cast<float>(J.width);
+    a.accepted = J.accepted;
+    const int compact = (J.slab_t > 1 && mu != 0) ? J.slab_t : 0;
+    update_class_body<R, LC>(g, static_cast<R*>(J.theta), static_cast<cs_t<R>*>(J.cs), mu, a, compact);
+}
+
+template <typename R, int LC>
+__global__ void __launch_bounds__(kUpdateThreads, 5)
+    group_update_kernel(const __grid_constant__ BatchUpdateTable t, int mu, int parity)
+{
+    group_update<R, LC>(t, mu, parity);
+}
+
+template <typename R, int LC>
+__global__ void __launch_bounds__(kWideThreads, 2)
+    group_update_wide_kernel(const __grid_constant__ BatchUpdateTable t, int mu, int parity)
+{
+    group_update<R, LC>(t, mu, parity);
+}
+
+// Measurement of a group of lattices (y index: lattice), as measure_store_kernel.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) group_measure_kernel(const __grid_constant__ BatchMeasureTable t)
+{
+    const BatchMeasureJob& J = t.job[blockIdx.y];
+    const int k = static_cast<int>(blockIdx.x) * kThreads + static_cast<int>(threadIdx.x);
+    const Geo g = geo_of(J.L, J.Nt, J.V, J.Vh, J.L3);
+    if (k >= (J.Nt / J.slab_t) * J.L3) return;
+    measure_store_site<R>(g, static_cast<const cs_t<R>*>(J.cs), J.slab_t, J.r_max, 0, 0, J.asum, nullptr, nullptr,
+                          nullptr, k);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -1163,6 +1215,51 @@ cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int thr
     return cudaLaunchKernelEx(&cfg, batched_update_kernel<R>, t, mu, parity);
 }
 
+// Class (mu, parity) of every lattice of a group of one extent L: grid (blocks_x, t.njobs).
+// FP32 uses the wide kernel (blocks of up to kWideThreads), FP64 blocks of up to
+// kUpdateThreads.
+template <typename R>
+cudaError_t launch_group_update(const BatchUpdateTable& t, int L, int blocks_x, int threads, int mu, int parity,
+                                cudaStream_t st, bool pdl)
+{
+    if (t.njobs < 1 || blocks_x < 1) return cudaErrorInvalidValue;
+    const bool wide = sizeof(R) == 4;
+    if (threads > (wide ? kWideThreads : kUpdateThreads)) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks_x), static_cast<unsigned>(t.njobs));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define UL_GROUP_LAUNCH(K)                                                                                     \
+    switch (L) {                                                                                               \
+    case 8: return cudaLaunchKernelEx(&cfg, K<R, 8>, t, mu, parity);                                           \
+    case 12: return cudaLaunchKernelEx(&cfg, K<R, 12>, t, mu, parity);                                         \
+    case 16: return cudaLaunchKernelEx(&cfg, K<R, 16>, t, mu, parity);                                         \
+    case 20: return cudaLaunchKernelEx(&cfg, K<R, 20>, t, mu, parity);                                         \
+    case 24: return cudaLaunchKernelEx(&cfg, K<R, 24>, t, mu, parity);                                         \
+    case 32: return cudaLaunchKernelEx(&cfg, K<R, 32>, t, mu, parity);                                         \
+    default: return cudaLaunchKernelEx(&cfg, K<R, 0>, t, mu, parity);                                          \
+    }
+    if (wide) {
+        UL_GROUP_LAUNCH(group_update_wide_kernel)
+    }
+    UL_GROUP_LAUNCH(group_update_kernel)
+#undef UL_GROUP_LAUNCH
+}
+
+template <typename R>
+cudaError_t launch_group_measure(const BatchMeasureTable& t, int blocks_x, cudaStream_t st)
+{
+    if (t.njobs < 1 || blocks_x < 1) return cudaErrorInvalidValue;
+    group_measure_kernel<R><<<dim3(static_cast<unsigned>(blocks_x), static_cast<unsigned>(t.njobs)), kThreads, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaStream_t st)
 {
@@ -1245,10 +1342,15 @@ cudaError_t check_word(unsigned long long* out, bool clear)
                                                           const void*, double2*, bool, cudaStream_t, bool, int*); \
     template cudaError_t launch_rng_uniforms<R>(uint64_t, uint64_t, uint64_t, int, double*, cudaStream_t);        \
     template cudaError_t slab_plan<R>(const Geo&, int, int, int*, int*);                                           \
+    template size_t slab_level_smem<R>(const Geo&, int, int);                                                      \
     template cudaError_t launch_slab<R>(const Geo&, R*, void*, const SlabArgs&, int, cudaStream_t);               \
+    template cudaError_t launch_slab_jobs<R>(const Geo&, const SlabArgs&, const SlabJobTable&, int, cudaStream_t); \
     template cudaError_t launch_persistent<R>(const Geo&, R*, void*, const PersistArgs&, int, cudaStream_t);       \
     template cudaError_t launch_batched_update<R>(const BatchUpdateTable&, int, int, int, int, cudaStream_t, bool); \
     template cudaError_t launch_batched_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                   \
+    template cudaError_t launch_group_update<R>(const BatchUpdateTable&, int, int, int, int, int, cudaStream_t,    \
+                                                bool);                                                             \
+    template cudaError_t launch_group_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                     \
     template cudaError_t launch_hot_start<R>(const Geo&, R*, void*, uint64_t, cudaStream_t);                        \
     template cudaError_t launch_refresh_cs<R>(const Geo&, const R*, void*, cudaStream_t);                           \
     template cudaError_t launch_update_class<R>(const Geo&, R*, void*, int, int, bool, uint64_t,                    \

@@ -5,4 +5,6 @@
 
 namespace ul {
 UL_INSTANTIATE_KERNELS(float)
+
+int class_block_threads(long work, bool fp32) { return fp32 ? wide_block_threads(work) : update_block_threads(work); }
 } // namespace ul

@@ -244,8 +244,8 @@ __device__ __forceinline__ void slab_measure(const SlabLinks<R, LC>& S, const Ge
 }
 
 template <typename R, int LC>
-__global__ void __launch_bounds__(1024, 1) slab_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs,
-                                                        SlabArgs a)
+__device__ __forceinline__ void slab_body(const Geo& g, R* __restrict__ theta, cs_t<R>* __restrict__ cs,
+                                          const SlabArgs& a)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -347,7 +347,32 @@ __global__ void __launch_bounds__(1024, 1) slab_kernel(Geo g, R* __restrict__ th
     }
 }
 
-// Kernel instance for extent L (compile-time extents for the common sizes).
+template <typename R, int LC>
+__global__ void __launch_bounds__(1024, 1) slab_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs,
+                                                        SlabArgs a)
+{
+    slab_body<R, LC>(g, theta, cs, a);
+}
+
+// The same slab-resident level for several lattices of one shape in one launch: the grid's
+// y index selects the lattice (clusters never span two lattices), whose links, Metropolis
+// arguments, accumulator and schedule come from the table; every lattice's results are
+// those of its own slab_kernel launch.
+template <typename R, int LC>
+__global__ void __launch_bounds__(1024, 1) slab_jobs_kernel(Geo g, SlabArgs a, const __grid_constant__ SlabJobTable t)
+{
+    const SlabJob& j = t.job[blockIdx.y];
+    SlabArgs b = a;
+    b.u = j.u;
+    b.asum = j.asum;
+    b.n_units = j.n_units;
+    b.n_metro = j.n_metro;
+    b.n_or = j.n_or;
+    b.r_max = j.r_max;
+    slab_body<R, LC>(g, static_cast<R*>(j.theta), static_cast<cs_t<R>*>(j.cs), b);
+}
+
+// Kernel instances for extent L (compile-time extents for the common sizes).
 template <typename R>
 auto slab_kernel_for(int L)
 {
@@ -360,11 +385,29 @@ auto slab_kernel_for(int L)
 }
 
 template <typename R>
+auto slab_jobs_kernel_for(int L)
+{
+    switch (L) {
+    case 16: return slab_jobs_kernel<R, 16>;
+    case 24: return slab_jobs_kernel<R, 24>;
+    case 32: return slab_jobs_kernel<R, 32>;
+    default: return slab_jobs_kernel<R, 0>;
+    }
+}
+
+template <typename R>
 size_t slab_smem_bytes(int L, int nz, int tau)
 {
     const size_t P = static_cast<size_t>(L) * L * nz;
     return P * (static_cast<size_t>(slab_phase_slots(tau)) * 2 * sizeof(R) +
                 static_cast<size_t>(slab_angle_slots(tau)) * sizeof(R));
+}
+
+// Shared memory of one CTA of a slab-resident launch of shape g with `cluster` CTAs per slab.
+template <typename R>
+size_t slab_level_smem(const Geo& g, int tau, int cluster)
+{
+    return slab_smem_bytes<R>(g.L, g.L / cluster, tau);
 }
 
 template <typename R>
@@ -399,8 +442,13 @@ cudaError_t slab_plan(const Geo& g, int tau, int force_cluster, int* cluster, in
     nt = nt > 1024 ? 1024 : nt;
     const size_t smem = slab_smem_bytes<R>(g.L, nz, tau);
     auto fn = slab_kernel_for<R>(g.L);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    auto fnj = slab_jobs_kernel_for<R>(g.L);
+    // the attribute is an upper bound shared by every shape that uses this kernel instance:
+    // the device's opt-in maximum, so that no later plan lowers it below another's need
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fnj, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e == cudaSuccess && best > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess && best > 8) e = cudaFuncSetAttribute(fnj, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(static_cast<unsigned>(S * best));
@@ -423,6 +471,29 @@ cudaError_t slab_plan(const Geo& g, int tau, int force_cluster, int* cluster, in
     *cluster = best;
     *threads = nt;
     return cudaSuccess;
+}
+
+// The level of t.njobs lattices of shape g (slab thickness a.u.slab_t, a.cluster CTAs of
+// `threads` threads per slab, a plan of slab_plan) in one launch; a supplies the uniform
+// part (cluster, nz, skip_measure = 0, fields = 0), the table the rest.
+template <typename R>
+cudaError_t launch_slab_jobs(const Geo& g, const SlabArgs& a, const SlabJobTable& t, int threads, cudaStream_t st)
+{
+    if (t.njobs < 1 || t.njobs > kMaxSlabJobs) return cudaErrorInvalidValue;
+    const int S = g.Nt / a.u.slab_t;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(static_cast<unsigned>(S * a.cluster), static_cast<unsigned>(t.njobs));
+    cfg.blockDim = dim3(static_cast<unsigned>(threads));
+    cfg.dynamicSmemBytes = slab_smem_bytes<R>(g.L, a.nz, a.u.slab_t);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(a.cluster);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, slab_jobs_kernel_for<R>(g.L), g, a, t);
 }
 
 template <typename R>
