@@ -111,7 +111,8 @@ def roofline_block(prec_name, sweep_ms_per_step, peaks, traffic=None):
     fr = {"hbm": achieved / peaks["hbm_gbs"], "l2": achieved / peaks["l2_read_gbs"],
           "alu": alu_achieved / alu_peak}
     binding = max(fr, key=fr.get)
-    return {"bound": "hbm", "kernel": "update_class_kernel<%s>" % ("double" if prec_name == "fp64" else "float"),
+    return {"bound": "hbm",
+            "kernel": "update_class_kernel<double, 24>" if prec_name == "fp64" else "update_class_wide_kernel<float, 24>",
             "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": fr["hbm"],
             "traffic": traffic, "bytes_per_update": bpu, "updates_per_launch": UPDATES_PER_CLASS_LAUNCH,
             "avg_launch_us": avg_s * 1e6, "launches_per_step": CLASS_LAUNCHES_PER_STEP,
@@ -126,10 +127,12 @@ def roofline_block(prec_name, sweep_ms_per_step, peaks, traffic=None):
 # DRAM bytes per launch of the dominant kernel from a committed ncu capture, keyed by the
 # hash of the kernel sources it was taken on (null once the sources have changed).
 TRAFFIC = {
-    # mean DRAM bytes of two captured launches of the FP64 update kernel at 24^4 (launches 8
-    # and 9 of the profiled step; ncu replays with cold caches, while in the bench the
-    # lattice is L2-resident)
-    ("fp64", "3bc68a4c11a4ef4c"): 21.30e6,
+    # mean DRAM bytes (read + write) of two captured launches of the update kernel at 24^4
+    # (launches 8 and 9 of the profiled step, Metropolis mu = 3 and overrelaxation mu = 0;
+    # ncu replays with cold caches, while in the bench the lattice is L2-resident):
+    # profiles/update_class_f64_24x24.md, profiles/update_class_f32_24x24.md
+    ("fp64", "663d112ecedb9f54"): (22628864 + 19974400) / 2,
+    ("fp32", "663d112ecedb9f54"): (11328256 + 10000384) / 2,
 }
 
 
@@ -518,7 +521,7 @@ def _torch_setup():
 BATCH_OPTIONS = ("slab_levels", "tune")
 
 
-def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, options=None):
+def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, options=None, variant="full"):
     """32 independent configurations of uneven sizes (8 each of 12^4, 16^4, 20^4, 24^4,
     beta from {0.96, 0.98, 1.0}) advanced together by the batch engine; a step is the
     whole batch run to completion (100 sweeps + one 200-sample level + reduction each)."""
@@ -526,6 +529,10 @@ def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, op
     from paper_1208_0166_gb300.workloads import batch_jobs_uneven
 
     specs = batch_jobs_uneven(seed_base + 100 * rank)
+    if variant == "sweeps":      # the compound sweeps of every job (a level of one sub-sample)
+        specs = [dict(sp, n_sub=1) for sp in specs]
+    elif variant == "levels":    # the levels alone (no sweeps before them)
+        specs = [dict(sp, n_sweeps=0) for sp in specs]
     stream = torch.cuda.Stream()
     b = lib.Batch(prec, 8 << 30, stream.cuda_stream)
     for k, v in (options or {}).items():
@@ -595,7 +602,8 @@ def run_batch(args):
     prec = lib.UL_FP64 if args.precision == "fp64" else lib.UL_FP32_ACC64
     clocks = ClockSampler(local)
     clocks.start()
-    r = batch_result(lib, prec, args.steps, args.warmup, rank, dist, torch, options=_options(args))
+    r = batch_result(lib, prec, args.steps, args.warmup, rank, dist, torch, options=_options(args),
+                     variant=args.batch_variant)
     clk = clocks.stop()
     from paper_1208_0166_gb300.replicas import aggregate
 
@@ -607,7 +615,7 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "jobs": r["jobs"], "block_threads": r["block_threads"],
-                       "options": _options(args)},
+                       "options": _options(args), "variant": args.batch_variant},
             "slab_level_launches": r["slab_level_launches"],
             "correlator_samples_per_s": r["samples"] * ws / t, "gpu_launches": r["launches"], "clocks": clk,
             "C_r_first_job": r["C_r_first_job"]}
@@ -823,6 +831,9 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep-scaling"],
                     help="single: the 24^4 configuration step (default); batch: 32 uneven lattices; "
                          "serve: Poisson stream through the continuous-batching loop")
+    ap.add_argument("--batch-variant", default="full", choices=["full", "sweeps", "levels"],
+                    help="--workload batch: the whole program, its sweeps alone (one sub-sample per level) "
+                         "or its levels alone (no sweeps)")
     ap.add_argument("--serve-jobs", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--estimator", default="paper", choices=["paper", "sym", "two-level"],

@@ -3,10 +3,13 @@
 //
 // Every job runs the same program as a single handle: n_sweeps compound sweeps, then one
 // multilevel level of n_sub sub-samples (masked passes + transporter measurement), then
-// the cross-slab reduction and the plaquette.  The engine advances the jobs in their sweeps
-// in lockstep by update passes: each pass is 8 batched class launches that cover every
-// such lattice (each at its own position in its program), followed by one batched
-// measurement launch for the jobs that just finished a sub-sample.  A job whose slab fits
+// the cross-slab reduction and the plaquette.  The engine advances the jobs in lockstep by
+// update passes, in groups of one shape whose links fit L2 (option group_mb): a pass of a
+// group is 8 class launches that cover every lattice of the group (each at its own position
+// in its program; the grid's y index selects the lattice), followed by one measurement
+// launch for the lattices that just finished a sub-sample.  A group runs a whole step's
+// passes in a row (its links stay in L2); each shape has a stream of its own, the largest
+// shapes the highest-priority ones, so shapes overlap.  A job whose slab fits
 // the shared memory of a thread-block cluster runs its whole level as a slab-resident
 // launch instead (all sub-samples, cluster barriers between classes, measurements inside):
 // the jobs of one shape that reach their level in the same step share one such launch
@@ -784,7 +787,6 @@ int group_pass(ul_batch* b, const std::vector<Job*>& group, bool* did_work)
         u.V = j->g.V;
         u.Vh = j->g.Vh;
         u.L3 = j->g.L3;
-        u.block0 = 0;
         u.metro = metro ? 1 : 0;
         u.slab_t = slab_t;
         u.frozen_mask = 0;
@@ -846,7 +848,6 @@ int group_pass(ul_batch* b, const std::vector<Job*>& group, bool* did_work)
         mj.V = j->g.V;
         mj.Vh = j->g.Vh;
         mj.L3 = j->g.L3;
-        mj.block0 = 0;
         mj.slab_t = j->spec.slab_t;
         mj.r_max = j->spec.r_max;
         mwork = std::max<long>(mwork, static_cast<long>(j->S) * j->g.L3);

@@ -76,7 +76,6 @@ struct BatchUpdateJob {
     void* cs;
     unsigned long long* accepted;
     int L, Nt, V, Vh, L3;
-    int block0;
     int metro, slab_t;
     unsigned long long frozen_mask;
     uint64_t pass, seed;
@@ -92,7 +91,6 @@ struct BatchMeasureJob {
     const void* cs;
     double2* asum;
     int L, Nt, V, Vh, L3;
-    int block0;
     int slab_t, r_max;
 };
 

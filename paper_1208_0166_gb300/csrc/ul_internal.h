@@ -138,17 +138,6 @@ cudaError_t launch_slab(const Geo& g, R* theta, void* cs, const SlabArgs& a, int
 template <typename R>
 cudaError_t launch_slab_jobs(const Geo& g, const SlabArgs& a, const SlabJobTable& t, int threads, cudaStream_t st);
 
-// One batched class update over every lattice of the table (blocks: sum of the lattices'
-// block counts at `threads` <= 128 threads per block; a masked spatial class counts only the
-// unfrozen slices).  pdl: programmatic dependent launch.
-template <typename R>
-cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int threads, int mu, int parity,
-                                  cudaStream_t st, bool pdl);
-
-// One batched transporter measurement (correlators only) over the lattices of the table.
-template <typename R>
-cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaStream_t st);
-
 // Lockstep class update of a group of lattices of one extent L (grid: blocks_x blocks of
 // `threads` per lattice, t.njobs lattices), and its measurement (blocks_x blocks of 256).
 template <typename R>

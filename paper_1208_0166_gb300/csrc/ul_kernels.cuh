@@ -892,11 +892,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 4) persistent_kernel
 }
 
 // ---------------------------------------------------------------------------
-// Batched kernels: one launch updates class (mu, parity) of every resident lattice of a
-// batch (lattices of different shapes, couplings, seeds and schedule positions).  The
-// per-lattice parameters travel in the kernel's parameter block; block b belongs to the
-// last job whose block0 <= b.  Each link is updated by the same device function as in
-// the single-lattice kernel, so a lattice's trajectory does not depend on its batch.
+// Batch kernels: one launch updates class (mu, parity) of every lattice of a group of one
+// shape (couplings, seeds and schedule positions may differ).  The per-lattice parameters
+// travel in the kernel's parameter block; the grid's y index selects the lattice.  Each
+// link is updated by the same device function as in the single-lattice kernel, so a
+// lattice's trajectory does not depend on its batch.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ Geo geo_of(int L, int Nt, int V, int Vh, int L3)
 {
@@ -908,92 +908,6 @@ __device__ __forceinline__ Geo geo_of(int L, int Nt, int V, int Vh, int L3)
     g.V = V;
     g.Vh = Vh;
     return g;
-}
-
-template <typename R, int MU>
-__device__ __forceinline__ bool batch_update_link(const BatchUpdateJob& J, int parity, int h)
-{
-    const Geo g = geo_of(J.L, J.Nt, J.V, J.Vh, J.L3);
-    UpdateArgs a;
-    a.parity = parity;
-    a.metro = J.metro;
-    a.slab_t = J.slab_t;
-    a.frozen_mask = J.frozen_mask;
-    a.pass = J.pass;
-    a.pass_base = nullptr;
-    a.seed = J.seed;
-    a.beta = J.beta;
-    a.width = J.width;
-    a.beta_f = static_cast<float>(J.beta);
-    a.width_f = static_cast<float>(J.width);
-    a.accepted = J.accepted;
-    R* theta = static_cast<R*>(J.theta);
-    cs_t<R>* cs = static_cast<cs_t<R>*>(J.cs);
-    switch (J.L) {
-    case 8: return update_link<R, 8, MU>(g, theta, cs, h, a);
-    case 12: return update_link<R, 12, MU>(g, theta, cs, h, a);
-    case 16: return update_link<R, 16, MU>(g, theta, cs, h, a);
-    case 20: return update_link<R, 20, MU>(g, theta, cs, h, a);
-    case 24: return update_link<R, 24, MU>(g, theta, cs, h, a);
-    case 32: return update_link<R, 32, MU>(g, theta, cs, h, a);
-    default: return update_link<R, 0, MU>(g, theta, cs, h, a);
-    }
-}
-
-// Block b belongs to the last job whose block0 <= b.  For a masked spatial class (slab_t > 1,
-// mu != 0) a job's blocks cover only its unfrozen time slices (see update_class_kernel).
-// Minimum resident 128-thread blocks per SM.  The batched form reads its extents at run time
-// and needs more registers than the compile-time-extent class kernel: the FP64 form fits 6
-// blocks (80 registers) without spills, the FP32 form 12 (40 registers).
-template <typename R> struct BatchMinBlocks { static constexpr int value = 6; };
-template <> struct BatchMinBlocks<float> { static constexpr int value = 12; };
-
-template <typename R>
-__global__ void __launch_bounds__(128, BatchMinBlocks<R>::value) batched_update_kernel(const __grid_constant__ BatchUpdateTable t, int mu,
-                                                                 int parity)
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    int j = t.njobs - 1;
-    while (j > 0 && static_cast<int>(blockIdx.x) < t.job[j].block0) --j;
-    const BatchUpdateJob& J = t.job[j];
-    int h = (static_cast<int>(blockIdx.x) - J.block0) * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
-    bool valid = h < J.Vh;
-    if (J.slab_t > 1 && mu != 0) {
-        const int hs = J.L3 / 2;           // links of one parity on one time slice
-        const int per = J.slab_t - 1;      // unfrozen slices per slab
-        const int q = h;
-        valid = q < (J.Nt / J.slab_t) * per * hs;
-        const int slice = q / hs;
-        const int tt = (slice / per) * J.slab_t + 1 + slice % per;
-        h = tt * hs + (q - slice * hs);
-    }
-    bool acc = false;
-    if (valid) {
-        switch (mu) {
-        case 0: acc = batch_update_link<R, 0>(J, parity, h); break;
-        case 1: acc = batch_update_link<R, 1>(J, parity, h); break;
-        case 2: acc = batch_update_link<R, 2>(J, parity, h); break;
-        default: acc = batch_update_link<R, 3>(J, parity, h); break;
-        }
-    }
-    if (J.metro) {
-        const unsigned mask = __ballot_sync(0xffffffffu, acc);
-        if ((threadIdx.x & 31) == 0 && mask) atomicAdd(J.accepted, static_cast<unsigned long long>(__popc(mask)));
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kThreads) batched_measure_kernel(const __grid_constant__ BatchMeasureTable t)
-{
-    int j = t.njobs - 1;
-    while (j > 0 && static_cast<int>(blockIdx.x) < t.job[j].block0) --j;
-    const BatchMeasureJob& J = t.job[j];
-    const int k = (static_cast<int>(blockIdx.x) - J.block0) * kThreads + static_cast<int>(threadIdx.x);
-    const Geo g = geo_of(J.L, J.Nt, J.V, J.Vh, J.L3);
-    if (k >= (J.Nt / J.slab_t) * J.L3) return;
-    measure_store_site<R>(g, static_cast<const cs_t<R>*>(J.cs), J.slab_t, J.r_max, 0, 0, J.asum, nullptr, nullptr,
-                          nullptr, k);
 }
 
 // Lockstep class update of a group of lattices of one shape: the grid's y index selects the
@@ -1198,23 +1112,6 @@ cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int n
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_batched_update(const BatchUpdateTable& t, int blocks, int threads, int mu, int parity,
-                                  cudaStream_t st, bool pdl)
-{
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batched_update_kernel<R>, t, mu, parity);
-}
-
 // Class (mu, parity) of every lattice of a group of one extent L: grid (blocks_x, t.njobs).
 // FP32 uses the wide kernel (blocks of up to kWideThreads), FP64 blocks of up to
 // kUpdateThreads.
@@ -1257,13 +1154,6 @@ cudaError_t launch_group_measure(const BatchMeasureTable& t, int blocks_x, cudaS
 {
     if (t.njobs < 1 || blocks_x < 1) return cudaErrorInvalidValue;
     group_measure_kernel<R><<<dim3(static_cast<unsigned>(blocks_x), static_cast<unsigned>(t.njobs)), kThreads, 0, st>>>(t);
-    return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_batched_measure(const BatchMeasureTable& t, int blocks, cudaStream_t st)
-{
-    batched_measure_kernel<R><<<blocks, kThreads, 0, st>>>(t);
     return cudaGetLastError();
 }
 
@@ -1346,8 +1236,6 @@ cudaError_t check_word(unsigned long long* out, bool clear)
     template cudaError_t launch_slab<R>(const Geo&, R*, void*, const SlabArgs&, int, cudaStream_t);               \
     template cudaError_t launch_slab_jobs<R>(const Geo&, const SlabArgs&, const SlabJobTable&, int, cudaStream_t); \
     template cudaError_t launch_persistent<R>(const Geo&, R*, void*, const PersistArgs&, int, cudaStream_t);       \
-    template cudaError_t launch_batched_update<R>(const BatchUpdateTable&, int, int, int, int, cudaStream_t, bool); \
-    template cudaError_t launch_batched_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                   \
     template cudaError_t launch_group_update<R>(const BatchUpdateTable&, int, int, int, int, int, cudaStream_t,    \
                                                 bool);                                                             \
     template cudaError_t launch_group_measure<R>(const BatchMeasureTable&, int, cudaStream_t);                     \
