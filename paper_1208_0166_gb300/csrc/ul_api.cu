@@ -59,6 +59,7 @@ struct ul_lattice {
     int slab_mode = 0;    // 0: off, 1: on where the slab fits
     int slab_cluster = 0; // CTAs per slab (0: chosen by slab_plan)
     bool contract_tiled = true; // FP32 insertion contraction in the shared-memory tiled form
+    long long copy_wait_cycles = ul::kCopyWaitLimit; // option "copy_wait_cycles": the tiled contraction's copy wait
     unsigned long long spin_limit = 1ull << 24;
     unsigned int* d_bar = nullptr;    // [0] arrivals, [1] generation
     int* d_status = nullptr;          // nonzero after a wait gave up
@@ -444,10 +445,10 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
                 UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_slab[buf], 0));
                 e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum,
                                                                       chunk_first, h->aux_stream, h->contract_tiled,
-                                                                      h->d_status)
+                                                                      h->d_status, h->copy_wait_cycles)
                               : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum,
                                                                      chunk_first, h->aux_stream, h->contract_tiled,
-                                                                     h->d_status);
+                                                                     h->d_status, h->copy_wait_cycles);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 UL_CK(h, cudaEventRecord(h->ev_contract[buf], h->aux_stream));
                 h->launches += 1;
@@ -480,9 +481,9 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             if (fields) {
                 cudaError_t e = is_f64(h)
                     ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first,
-                                                            h->stream, h->contract_tiled, h->d_status)
+                                                            h->stream, h->contract_tiled, h->d_status, h->copy_wait_cycles)
                     : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first,
-                                                           h->stream, h->contract_tiled, h->d_status);
+                                                           h->stream, h->contract_tiled, h->d_status, h->copy_wait_cycles);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 h->launches += 1;
             }
@@ -512,9 +513,9 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             if (fields) {
                 cudaError_t e = is_f64(h)
                     ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first, st,
-                                                            h->contract_tiled, h->d_status)
+                                                            h->contract_tiled, h->d_status, h->copy_wait_cycles)
                     : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first, st,
-                                                           h->contract_tiled, h->d_status);
+                                                           h->contract_tiled, h->d_status, h->copy_wait_cycles);
                 if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 ++n;
             }
@@ -861,9 +862,9 @@ int ul_multilevel_fields_sym(ul_lattice* h, int slab_t, int n_sub, int r_max, in
             }
             cudaError_t e = is_f64(h)
                 ? ul::launch_insertion_contract_sym<double>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, k == 0, st,
-                                                            h->contract_tiled, h->d_status)
+                                                            h->contract_tiled, h->d_status, h->copy_wait_cycles)
                 : ul::launch_insertion_contract_sym<float>(g, slab_t, r_max, nd, count, tk3, csym, bsum3, k == 0, st,
-                                                           h->contract_tiled, h->d_status);
+                                                           h->contract_tiled, h->d_status, h->copy_wait_cycles);
             if (e != cudaSuccess) return cuda_fail(h, e, "symmetrised contraction launch");
             return n + 1;
         });
@@ -1203,6 +1204,11 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
     } else if (!std::strcmp(key, "contract_tiled")) {
         if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "contract_tiled must be 0 or 1");
         h->contract_tiled = v != 0.0;
+        drop_graphs(h, 0); // captured sequences hold the contraction launch
+    } else if (!std::strcmp(key, "copy_wait_cycles")) {
+        if (!(v >= 0.0) || v > static_cast<double>(ul::kCopyWaitLimit) || v != static_cast<double>(static_cast<long long>(v)))
+            return fail(h, UL_EINVAL, "copy_wait_cycles must be an integer in [0, 2e9]");
+        h->copy_wait_cycles = static_cast<long long>(v);
         drop_graphs(h, 0); // captured sequences hold the contraction launch
     } else if (!std::strcmp(key, "insertion_chunk_mb")) {
         if (!(v >= 1.0) || v > 1e6 || v != static_cast<int>(v))

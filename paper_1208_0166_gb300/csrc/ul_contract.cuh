@@ -117,13 +117,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 
 // Waits for the phase `parity` of the barrier, at most about kCopyWaitCycles SM cycles
 // (about a second); false when the limit was reached.
-constexpr long long kCopyWaitCycles = 2000000000LL;
+constexpr long long kCopyWaitCycles = kCopyWaitLimit;
 
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned int parity)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned int parity,
+                                                  long long limit = kCopyWaitCycles)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kCopyWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -205,7 +206,8 @@ template <typename R, bool SYM>
 __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     insertion_contract_tiled_kernel(Geo g, int S, int r_max, int nd, int count, ContractTile t,
                                     const Cx<float>* __restrict__ tk, const float* __restrict__ ok,
-                                    double2* __restrict__ bsum, bool first, int* __restrict__ status)
+                                    double2* __restrict__ bsum, bool first, int* __restrict__ status,
+                                    long long wait_cycles)
 {
     extern __shared__ __align__(16) float smem[];
     __shared__ unsigned long long bars[2];
@@ -289,10 +291,11 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
             for (int ch = 0; ch < 8; ++ch)
                 asm volatile("prefetch.global.L2 [%0];\n" ::"l"(bsum + out + ch * g.L3));
         }
-        const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1);
+        const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1, wait_cycles);
         if (__syncthreads_or(!arrived)) {
             // a copy did not complete in time: report it, give the copies in flight a bounded
-            // wait so that none lands after the block has left, and stop
+            // wait (the full limit, whatever wait_cycles is) so that none lands after the
+            // block has left, and stop
             if (tid == 0) {
                 atomicExch(status, 2);
                 mbar_wait_bounded(&bars[buf], (bi >> 1) & 1);
@@ -350,7 +353,8 @@ cudaError_t prepare_insertion_contract()
 // false (nothing launched) where it does not apply, and the caller runs the untiled kernel.
 template <typename R>
 bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
-                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err, bool sym)
+                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err, bool sym,
+                           long long wait_cycles)
 {
     if constexpr (sizeof(R) != 4) {
         return false;
@@ -362,10 +366,10 @@ bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, co
         const auto* okf = static_cast<const float*>(ok);
         if (sym)
             insertion_contract_tiled_kernel<float, true><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
-                g, S, r_max, nd, count, t, tkf, okf, bsum, first, status);
+                g, S, r_max, nd, count, t, tkf, okf, bsum, first, status, wait_cycles);
         else
             insertion_contract_tiled_kernel<float, false><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
-                g, S, r_max, nd, count, t, tkf, okf, bsum, first, status);
+                g, S, r_max, nd, count, t, tkf, okf, bsum, first, status, wait_cycles);
         *err = cudaGetLastError();
         return true;
     }

@@ -11,6 +11,11 @@ namespace ul {
 
 struct Geo;
 
+// SM cycles (about a second) a tiled insertion contraction waits for a batch of bulk copies
+// before it reports a timeout (status 2); wait_cycles of the launchers may lower the first
+// wait of each batch (a test makes it run out), never the wait that lets copies in flight land.
+constexpr long long kCopyWaitLimit = 2000000000LL;
+
 // Largest number of time slabs one multilevel level may have.
 constexpr int kMaxSlabs = 256;
 
@@ -72,7 +77,7 @@ cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_m
 template <typename R>
 cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
                                           const void* csym, double2* bsum3, bool first, cudaStream_t st, bool tiled,
-                                          int* status);
+                                          int* status, long long wait_cycles = kCopyWaitLimit);
 
 // Multihit temporal links ubar[i] (lexicographic site i, complex in precision R).
 template <typename R>
@@ -86,7 +91,7 @@ cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* uba
 template <typename R>
 cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
                                       const void* ok, double2* bsum, bool first, cudaStream_t st, bool tiled,
-                                      int* status);
+                                      int* status, long long wait_cycles = kCopyWaitLimit);
 
 // Raises the dynamic shared-memory limit of the tiled FP32 contraction (once per process,
 // before any launch or graph capture that may use it).

@@ -1095,16 +1095,18 @@ cudaError_t launch_multihit(const Geo& g, const void* cs, double beta, void* uba
 
 template <typename R>
 bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
-                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err, bool sym);
+                           double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err, bool sym,
+                           long long wait_cycles);
 
 template <typename R>
 cudaError_t launch_insertion_contract(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk,
                                       const void* ok, double2* bsum, bool first, cudaStream_t st, bool tiled,
-                                      int* status)
+                                      int* status, long long wait_cycles)
 {
     const int S = g.Nt / slab_t;
     cudaError_t err = cudaSuccess;
-    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk, ok, bsum, first, status, st, &err, false))
+    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk, ok, bsum, first, status, st, &err, false,
+                                          wait_cycles))
         return err;
     const long total = static_cast<long>(S) * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
@@ -1229,7 +1231,8 @@ cudaError_t check_word(unsigned long long* out, bool clear)
     template cudaError_t launch_measure_sym<R>(const Geo&, const void*, int, int, int, int, double2*, void*,       \
                                                void*, void*, double*, cudaStream_t);                              \
     template cudaError_t launch_insertion_contract_sym<R>(const Geo&, int, int, int, int, const void*,             \
-                                                          const void*, double2*, bool, cudaStream_t, bool, int*); \
+                                                          const void*, double2*, bool, cudaStream_t, bool, int*,  \
+                                                          long long);                                             \
     template cudaError_t launch_rng_uniforms<R>(uint64_t, uint64_t, uint64_t, int, double*, cudaStream_t);        \
     template cudaError_t slab_plan<R>(const Geo&, int, int, int*, int*);                                           \
     template size_t slab_level_smem<R>(const Geo&, int, int);                                                      \
@@ -1251,7 +1254,7 @@ cudaError_t check_word(unsigned long long* out, bool clear)
                                                  void*, double*, const void*, cudaStream_t);                        \
     template cudaError_t launch_multihit<R>(const Geo&, const void*, double, void*, cudaStream_t);                 \
     template cudaError_t launch_insertion_contract<R>(const Geo&, int, int, int, int, const void*, const void*,     \
-                                                      double2*, bool, cudaStream_t, bool, int*);                   \
+                                                      double2*, bool, cudaStream_t, bool, int*, long long);        \
     template cudaError_t prepare_insertion_contract<R>();
 
 } // namespace ul

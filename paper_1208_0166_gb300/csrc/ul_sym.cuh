@@ -326,11 +326,12 @@ cudaError_t launch_measure_sym(const Geo& g, const void* cs, int slab_t, int r_m
 template <typename R>
 cudaError_t launch_insertion_contract_sym(const Geo& g, int slab_t, int r_max, int nd, int count, const void* tk3,
                                           const void* csym, double2* bsum3, bool first, cudaStream_t st, bool tiled,
-                                          int* status)
+                                          int* status, long long wait_cycles)
 {
     const int S = g.Nt / slab_t;
     cudaError_t err = cudaSuccess;
-    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk3, csym, bsum3, first, status, st, &err, true))
+    if (tiled && launch_contract_tiled<R>(g, S, r_max, nd, count, tk3, csym, bsum3, first, status, st, &err, true,
+                                          wait_cycles))
         return err;
     const long total = 3L * S * r_max * nd * ((g.L3 + kThreads - 1) / kThreads) * kThreads;
     insertion_contract_sym_kernel<R><<<blocks_for(total), kThreads, 0, st>>>(
