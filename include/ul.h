@@ -304,12 +304,12 @@ int ul_free(ul_lattice* h);
  *                  way; UL_FP64 always uses the untiled form.  A staging-copy wait that
  *                  reaches its time limit (about a second) is reported as UL_ETIMEOUT by the
  *                  level's result call.
- *   "copy_wait_cycles"  limit, in SM cycles, of the tiled contraction's wait for each batch
- *                  of staging copies (default and maximum 2e9, about a second; integer >= 0).
- *                  A smaller limit makes that wait give up early, as a test of the timeout
- *                  path; the block then still waits (up to the full limit) for the copies in
- *                  flight before it leaves, so no copy lands after it.  The level then fails
- *                  with UL_ETIMEOUT and its results are not written.
+ *   "copy_stall_test"  0 (default), or n > 0 (integer <= 2e9): a test of the timeout path
+ *                  of the tiled contraction.  Each block's first staged batch then waits for
+ *                  16 bytes more than its copies deliver, so that wait gives up after n SM
+ *                  cycles; the block reports the timeout, waits (up to the full limit, about
+ *                  a second) while the copies it issued land, and leaves.  The level fails
+ *                  with UL_ETIMEOUT and writes no results; set 0 to contract normally again.
  */
 int ul_set_option(ul_lattice* h, const char* key, double value);
 

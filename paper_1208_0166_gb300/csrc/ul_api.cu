@@ -59,7 +59,7 @@ struct ul_lattice {
     int slab_mode = 0;    // 0: off, 1: on where the slab fits
     int slab_cluster = 0; // CTAs per slab (0: chosen by slab_plan)
     bool contract_tiled = true; // FP32 insertion contraction in the shared-memory tiled form
-    long long copy_wait_cycles = ul::kCopyWaitLimit; // option "copy_wait_cycles": the tiled contraction's copy wait
+    long long copy_wait_cycles = ul::kCopyWaitLimit; // the tiled contraction's copy wait (option "copy_stall_test")
     unsigned long long spin_limit = 1ull << 24;
     unsigned int* d_bar = nullptr;    // [0] arrivals, [1] generation
     int* d_status = nullptr;          // nonzero after a wait gave up
@@ -1205,10 +1205,10 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
         if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "contract_tiled must be 0 or 1");
         h->contract_tiled = v != 0.0;
         drop_graphs(h, 0); // captured sequences hold the contraction launch
-    } else if (!std::strcmp(key, "copy_wait_cycles")) {
+    } else if (!std::strcmp(key, "copy_stall_test")) {
         if (!(v >= 0.0) || v > static_cast<double>(ul::kCopyWaitLimit) || v != static_cast<double>(static_cast<long long>(v)))
-            return fail(h, UL_EINVAL, "copy_wait_cycles must be an integer in [0, 2e9]");
-        h->copy_wait_cycles = static_cast<long long>(v);
+            return fail(h, UL_EINVAL, "copy_stall_test must be an integer in [0, 2e9]");
+        h->copy_wait_cycles = v > 0.0 ? -static_cast<long long>(v) : ul::kCopyWaitLimit;
         drop_graphs(h, 0); // captured sequences hold the contraction launch
     } else if (!std::strcmp(key, "insertion_chunk_mb")) {
         if (!(v >= 1.0) || v > 1e6 || v != static_cast<int>(v))

@@ -168,11 +168,12 @@ __device__ __forceinline__ void issue_batch(float* smem, unsigned long long* bar
                                             int tsz, int osz, int o_at, int tplane, int nr,
                                             const Cx<float>* tsrc0, long t_db, long t_ks, unsigned int t_bytes,
                                             const float* osrc0, long o_ks, int row0, int n1, int rows, int L,
-                                            unsigned int o_bytes, int ndv, long o_ds, int blk)
+                                            unsigned int o_bytes, int ndv, long o_ds, int blk,
+                                            unsigned int extra_tx = 0)
 {
     float* base = smem + buf * bufsz;
     const int lane = static_cast<int>(threadIdx.x) & 31;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[buf], (nr * t_bytes + o_bytes) * nb);
+    if (lane == 0) mbar_arrive_expect_tx(&bars[buf], (nr * t_bytes + o_bytes) * nb + extra_tx);
     __syncwarp();
     for (int j = lane; j < nb; j += 32) {
         const long k = k0 + j;
@@ -209,6 +210,12 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
                                     double2* __restrict__ bsum, bool first, int* __restrict__ status,
                                     long long wait_cycles)
 {
+    // wait_cycles < 0: the timeout test.  The first batch's barrier then expects 16 bytes
+    // more than its copies deliver, so its phase cannot complete: the first wait gives up
+    // after -wait_cycles cycles, the block reports status 2, waits (the full limit) while the
+    // copies it issued land, and leaves.
+    const bool stall_test = wait_cycles < 0;
+    const long long first_wait = stall_test ? -wait_cycles : wait_cycles;
     extern __shared__ __align__(16) float smem[];
     __shared__ unsigned long long bars[2];
     constexpr int BS = kInsertionBlock;
@@ -275,7 +282,8 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     const int nbatch = (count + BS - 1) / BS;
     if (tid < 32)
         issue_batch<SYM>(smem, bars, 0, 0, min(BS, count), bufsz, tsz, osz, BS * tsz, tplane, nr, tsrc0, t_db, t_ks,
-                         t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes, ndv, o_ds, t.ny * L * 8);
+                         t_bytes, osrc0, o_ks, row0, n1, t.rows, L, o_bytes, ndv, o_ds, t.ny * L * 8,
+                         stall_test ? 16u : 0u);
     for (int bi = 0; bi < nbatch; ++bi) {
         const int buf = bi & 1;
         const int k0 = bi * BS;
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
             for (int ch = 0; ch < 8; ++ch)
                 asm volatile("prefetch.global.L2 [%0];\n" ::"l"(bsum + out + ch * g.L3));
         }
-        const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1, wait_cycles);
+        const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1, first_wait);
         if (__syncthreads_or(!arrived)) {
             // a copy did not complete in time: report it, give the copies in flight a bounded
             // wait (the full limit, whatever wait_cycles is) so that none lands after the

@@ -12,8 +12,11 @@ namespace ul {
 struct Geo;
 
 // SM cycles (about a second) a tiled insertion contraction waits for a batch of bulk copies
-// before it reports a timeout (status 2); wait_cycles of the launchers may lower the first
-// wait of each batch (a test makes it run out), never the wait that lets copies in flight land.
+// before it reports a timeout (status 2).  wait_cycles of the launchers: the limit of that
+// first wait of each batch; a negative value -n runs the timeout test (the first batch's
+// barrier expects 16 bytes more than its copies deliver, so its wait gives up after n
+// cycles).  The wait that lets copies in flight land before a block leaves always has the
+// full limit.
 constexpr long long kCopyWaitLimit = 2000000000LL;
 
 // Largest number of time slabs one multilevel level may have.

@@ -80,9 +80,10 @@ def test_contract_tiled_option_validated():
 
 
 def test_copy_wait_timeout_is_reported_and_recoverable():
-    """A copy-wait limit of 0 cycles makes the tiled contraction's wait for its staged batch
-    give up: the level reports UL_ETIMEOUT (the blocks still let their copies land before
-    leaving) and the handle then runs the same level correctly with the default limit."""
+    """The timeout path of the tiled contraction's copy wait: with option copy_stall_test each
+    block's first staged batch waits for 16 bytes more than its copies deliver, so the wait
+    gives up (the copies themselves land before the block leaves).  The level reports
+    UL_ETIMEOUT, and the handle then runs the same level bit for bit with the normal wait."""
     L, Nt, tau, n_sub, r_max, d_max = 8, 8, 2, 5, 4, 7
     ref, ref_links = _level(L, Nt, tau, n_sub, r_max, d_max, tiled=1, slab=0)
     g = _lib.Lattice(L, Nt, 1.0, 71, _lib.UL_FP32_ACC64)
@@ -91,11 +92,11 @@ def test_copy_wait_timeout_is_reported_and_recoverable():
     g.sweep(1, 3)
     before = g.get_links()
     state = g.get_state()
-    g.set_option("copy_wait_cycles", 0)
+    g.set_option("copy_stall_test", 100000)
     with pytest.raises(_lib.ULError) as e:
         g.multilevel_fields(tau, n_sub, r_max, d_max)
     assert e.value.code == _lib.UL_ETIMEOUT
-    g.set_option("copy_wait_cycles", 2e9)
+    g.set_option("copy_stall_test", 0)
     g.set_links(before)
     g.set_state(*state)
     res = g.multilevel_fields(tau, n_sub, r_max, d_max)
@@ -103,5 +104,5 @@ def test_copy_wait_timeout_is_reported_and_recoverable():
     for key in ("corr", "fields", "vac"):
         assert np.array_equal(res[key], ref[key]), key
     with pytest.raises(_lib.ULError):
-        g.set_option("copy_wait_cycles", -1)
+        g.set_option("copy_stall_test", -1)
     g.close()
