@@ -558,11 +558,12 @@ def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, op
     stream.synchronize()
     ms = e0.elapsed_time(e1)
     st = b.stats()
-    slab_launches = b.plan(24, 24, 2)[1]
+    slab_launches, graph_launches = b.counters()
     b.close()
     samples = sum(sp["n_sub"] * (sp["Nt"] // sp["slab_t"]) * sp["L"] ** 3 * sp["r_max"] for sp in specs) * steps
     return {"ms": ms, "updates": st["link_updates"] - u0, "launches": st["launches"] - l0, "samples": samples,
             "block_threads": st["block_threads"], "jobs": len(specs), "slab_level_launches": slab_launches,
+            "graph_launches": graph_launches,
             "C_r_first_job": [[z.real, z.imag] for z in res[min(res)]["corr"][:3]]}
 
 
@@ -616,7 +617,7 @@ def run_batch(args):
             "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "jobs": r["jobs"], "block_threads": r["block_threads"],
                        "options": _options(args), "variant": args.batch_variant},
-            "slab_level_launches": r["slab_level_launches"],
+            "slab_level_launches": r["slab_level_launches"], "graph_launches": r["graph_launches"],
             "correlator_samples_per_s": r["samples"] * ws / t, "gpu_launches": r["launches"], "clocks": clk,
             "C_r_first_job": r["C_r_first_job"]}
     print(json.dumps(line), flush=True)
@@ -766,6 +767,7 @@ def run_ours(args):
         batch = {"value": r["updates"] / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"] / 2,
                  "steps": 2, "warmup": 1, "correlator_samples_per_s": r["samples"] / (r["ms"] / 1e3),
                  "gpu_launches": r["launches"], "block_threads": r["block_threads"],
+                 "slab_level_launches": r["slab_level_launches"], "graph_launches": r["graph_launches"],
                  "dtype": "f32 (FP64 accumulation)", "workload": BATCH_WORKLOAD,
                  "roofline_step": {"achieved": r["updates"] * 36 / (r["ms"] / 1e3) / 1e9, "unit": "GB/s",
                                    "bytes_per_update": 36, "peak_hbm": peaks["hbm_gbs"],

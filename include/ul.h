@@ -427,6 +427,10 @@ int ul_batch_stats(ul_batch* b, uint64_t* link_updates, uint64_t* launches, int*
  *       that launch's CTAs fit one SM's shared memory (a level of larger slabs would hold
  *       whole SMs that the other shapes' passes cannot share); 0 runs every level in the
  *       lockstep passes.
+ *   "graphs" (default 1): where every lattice of a lockstep group is at the start of a
+ *       compound sweep with a step's passes of sweeps left, the step's passes are captured
+ *       once into a CUDA graph (with each lattice's Metropolis pass base in device memory)
+ *       and replayed every step; 0 launches every pass directly.
  *   "tune" (default 1): choose each shape's cluster size by timing every feasible size once
  *       on a scratch lattice (a cudaMalloc/cudaFree, the first time a shape is seen) and keep
  *       the choice in the tune cache, a JSON file ($UL_TUNE_CACHE, else $XDG_CACHE_HOME or
@@ -441,6 +445,10 @@ int ul_batch_set_option(ul_batch* b, const char* key, double value);
  * the lockstep passes; *slab_launches = slab-resident level launches so far.  Either output
  * may be NULL. */
 int ul_batch_plan(ul_batch* b, int L, int Nt, int slab_t, int* cluster, uint64_t* slab_launches);
+
+/* ul_batch_counters — slab-resident level launches and replayed graphs of sweep passes so far
+ * (either output may be NULL). */
+int ul_batch_counters(ul_batch* b, uint64_t* slab_level_launches, uint64_t* graph_launches);
 
 /* ul_batch_free — wait for the batch's streams and release everything (NULL accepted). */
 int ul_batch_free(ul_batch* b);

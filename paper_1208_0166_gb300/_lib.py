@@ -71,6 +71,7 @@ SIGNATURES = [
     ("ul_batch_poll", _I, [_P, _U64, _DP, ctypes.POINTER(_I)]),
     ("ul_batch_set_option", _I, [_P, ctypes.c_char_p, _D]),
     ("ul_batch_plan", _I, [_P, _I, _I, _I, ctypes.POINTER(_I), _U64P]),
+    ("ul_batch_counters", _I, [_P, _U64P, _U64P]),
     ("ul_batch_job_info", _I, [_P, _U64, ctypes.POINTER(_I), _U64P, _U64P]),
     ("ul_batch_stats", _I, [_P, _U64P, _U64P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
     ("ul_batch_free", _I, [_P]),
@@ -318,6 +319,12 @@ class Batch:
         c, n = ctypes.c_int(), ctypes.c_uint64()
         self._check(load().ul_batch_plan(self._b, int(L), int(Nt), int(slab_t), ctypes.byref(c), ctypes.byref(n)))
         return c.value, n.value
+
+    def counters(self):
+        """(slab-resident level launches, replayed graphs of sweep passes) so far."""
+        a, g = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(load().ul_batch_counters(self._b, ctypes.byref(a), ctypes.byref(g)))
+        return a.value, g.value
 
     def job_info(self, job_id: int):
         """(state, passes_done, passes_total) of a job not yet collected."""
