@@ -185,7 +185,7 @@ __device__ __forceinline__ void metro_propose(R th, uint64_t link_id, uint64_t p
     using P = Prec<R>;
     R u1;
     P::metro_uniforms(link_id, pass, seed, &u1, &u2);
-    prop = P::wrap(fma_r(width, R(2) * u1 - R(1), th));
+    prop = P::wrap(fma_r(width, P::two_u_minus_one(u1), th));
     P::sincos(prop, &sn, &cn);
 }
 
@@ -194,7 +194,7 @@ __device__ __forceinline__ bool metro_accept(cs_t<R> old, Cx<R> A, R beta, R pro
                                              cs_t<R>& ncs)
 {
     const R dS = beta * fma_r(old.x - cn, A.re, -((old.y - sn) * A.im));
-    if (u2 < Prec<R>::exp(-dS)) {
+    if (Prec<R>::less_nonneg(u2, Prec<R>::exp(-dS))) {
         nth = prop;
         ncs = cs_t<R>{cn, sn};
         return true;
@@ -220,7 +220,7 @@ __device__ __forceinline__ void overrelax_new(R th, Cx<R> A, R& nth, cs_t<R>& nc
 {
     using P = Prec<R>;
     const R alpha = P::atan2(A.im, A.re);
-    nth = P::wrap(R(-2) * alpha - th);
+    nth = P::wrap(P::minus_twice(alpha) - th);
     R sn, cn;
     P::sincos(nth, &sn, &cn);
     ncs = cs_t<R>{cn, sn};

@@ -47,6 +47,25 @@ constexpr double LN2_B = 0x1.abc9e3b39803fp-56; // ln 2 - LN2_A rounded
 constexpr double LOG2_E = 0x1.71547652b82fep+0; // 1/ln 2
 constexpr double PI = 0x1.921fb54442d18p+1;     // pi rounded to double
 
+// Exact integer forms of some FP64 steps (the FP64 pipe is the update's bottleneck; the
+// integer pipes are idle).  For doubles that are not NaN:
+//   order_key(x) is monotonic in x and equal for +0 and -0, so x < y <=> key(x) < key(y);
+//   for x >= +0 the bit patterns themselves are ordered;
+//   multiplying a normal double by 2^n is adding n to its exponent field, exact as long as
+//   the result is normal.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double from_bits(long long b) { return __longlong_as_double(b); }
+__device__ __forceinline__ long long order_key(double x)
+{
+    const long long b = dbits(x);
+    return b >= 0 ? b : -(b & 0x7fffffffffffffffLL);
+}
+constexpr long long kExpUnit = 1LL << 52;                      // one step of the exponent field
+constexpr long long kBitsTwoPi = 0x401921fb54442d18LL;         // 2 pi (= 2 PI below)
+constexpr long long kBitsFourPi = 0x402921fb54442d18LL;        // 4 pi
+constexpr long long kBits700 = 0x4085e00000000000LL;           // 700.0
+constexpr long long kBitsInf = 0x7ff0000000000000LL;           // +infinity
+
 static __device__ const double kAtanJ8[2][9] = {
     // atan(j/8) rounded to double, j = 0..8
     {0.0, 0x1.fd5ba9aac2f6ep-4, 0x1.f5b75f92c80ddp-3, 0x1.6f61941e4def1p-2, 0x1.dac670561bb4fp-2,
@@ -93,8 +112,9 @@ __device__ __forceinline__ void sincos_det(double x, double* sp, double* cp)
 
 __device__ __forceinline__ double exp_det(double x)
 {
-    if (x > 700.0) return __longlong_as_double(0x7ff0000000000000LL);
-    if (x < -700.0) return 0.0;
+    // x > 700: +inf, x < -700: 0 (as floating-point comparisons; NaN falls through)
+    const long long xb = dbits(x), ab = xb & 0x7fffffffffffffffLL;
+    if (ab > kBits700 && ab <= kBitsInf) return xb < 0 ? 0.0 : from_bits(kBitsInf);
     const double k = rint(x * LOG2_E);
     double r = fma(-k, LN2_A, x);
     r = fma(-k, LN2_B, r);
@@ -112,7 +132,8 @@ __device__ __forceinline__ double exp_det(double x)
     e = fma(e, r, 0.5);
     e = fma(e, r, 1.0);
     e = fma(e, r, 1.0);
-    return ldexp(e, static_cast<int>(k));
+    // ldexp(e, k): e is within (0.7, 1.5) and |k| <= 1010, so e 2^k is normal and exact
+    return from_bits(dbits(e) + static_cast<long long>(k) * kExpUnit);
 }
 
 __device__ __forceinline__ double atan_small(double u)
@@ -132,21 +153,25 @@ __device__ __forceinline__ double atan_small(double u)
 __device__ __forceinline__ double atan2_det(double y, double x)
 {
     const double ax = fabs(x), ay = fabs(y);
-    if (ax == 0.0 && ay == 0.0) return 0.0;
-    const bool steep = ay > ax;
+    const long long bx = dbits(ax), by = dbits(ay);
+    if ((bx | by) == 0) return 0.0;          // ax == 0 and ay == 0
+    const bool steep = by > bx;              // ay > ax (both >= +0)
     const double t = steep ? ax / ay : ay / ax;
-    const int j = static_cast<int>(rint(t * 8.0));
+    // t 8: an exponent change where t is normal (t = 0 or subnormal: the multiplication)
+    const long long tb = dbits(t);
+    const double jd = rint(tb >= kExpUnit ? from_bits(tb + 3 * kExpUnit) : t * 8.0);
+    const int j = static_cast<int>(jd);
     double a;
     if (j == 0) {
         a = atan_small(t);
     } else {
-        const double cj = static_cast<double>(j) * 0.125;
+        const double cj = from_bits(dbits(jd) - 3 * kExpUnit); // j * 0.125, exact (j >= 1)
         const double u = (t - cj) / (1.0 + t * cj);
         a = kAtanJ8[0][j] + (kAtanJ8[1][j] + atan_small(u));
     }
     if (steep) a = (P1 - a) + P2;
-    if (x < 0.0) a = (2.0 * P1 - a) + 2.0 * P2;
-    return y < 0.0 ? -a : a;
+    if (dbits(x) < 0 && bx != 0) a = (2.0 * P1 - a) + 2.0 * P2; // x < 0.0
+    return (dbits(y) < 0 && by != 0) ? -a : a;                  // y < 0.0
 }
 } // namespace dm
 
@@ -165,10 +190,21 @@ struct Prec<double> {
     static __device__ __forceinline__ double exp(double x) { return dm::exp_det(x); }
     static __device__ __forceinline__ double atan2(double y, double x) { return dm::atan2_det(y, x); }
     // uniform in [0,1) from a 64-bit word
+    // (w >> 11) 2^-53: the conversion is exact (< 2^53) and the scaling an exponent change
     static __device__ __forceinline__ double uniform(uint64_t w)
     {
-        return static_cast<double>(w >> 11) * 0x1.0p-53;
+        const uint64_t m = w >> 11;
+        const double d = static_cast<double>(m);
+        return m ? dm::from_bits(dm::dbits(d) - 53 * dm::kExpUnit) : 0.0;
     }
+    // 2 u - 1 for a uniform u (0 or >= 2^-53): the doubling is an exponent change
+    static __device__ __forceinline__ double two_u_minus_one(double u)
+    {
+        const double twice = dm::dbits(u) ? dm::from_bits(dm::dbits(u) + dm::kExpUnit) : 0.0;
+        return twice - 1.0;
+    }
+    // a < b for doubles >= +0 that are not NaN (the Metropolis test u2 < exp(-dS))
+    static __device__ __forceinline__ bool less_nonneg(double a, double b) { return dm::dbits(a) < dm::dbits(b); }
     // Metropolis uniforms of link link_id in pass `pass`: words 0 and 1 of
     // Philox4x64-10(counter (link_id, pass, 0, 0), key (seed, 1))
     static __device__ __forceinline__ void metro_uniforms(uint64_t link_id, uint64_t pass, uint64_t seed, double* u1,
@@ -183,16 +219,27 @@ struct Prec<double> {
     // a < 4pi (no quotient in that range rounds across an integer: the double nearest
     // below 2pi (4pi) divided by 2pi lies more than half an ulp below 1 (2)), so the
     // comparisons reproduce the division's result bit for bit; other a take the division.
+    // (The comparisons run on integer keys of a: the same decisions, off the FP64 pipe.)
     static __device__ __forceinline__ double wrap(double th)
     {
         const double two_pi = 2.0 * PI;
         const double a = th + PI;
-        double k;
-        if (a >= -two_pi && a < 2.0 * two_pi)
-            k = a < 0.0 ? -1.0 : (a < two_pi ? 0.0 : 1.0);
-        else
-            k = floor(a / two_pi);
-        return th - two_pi * k;
+        const long long ka = dm::order_key(a);
+        if (ka >= -dm::kBitsTwoPi && ka < dm::kBitsFourPi) {
+            // two_pi k for k = -1, 0, 1 is exact: select it instead of multiplying
+            const double shift = ka < 0 ? -two_pi : (ka < dm::kBitsTwoPi ? 0.0 : two_pi);
+            return th - shift;
+        }
+        return th - two_pi * floor(a / two_pi);
+    }
+    // -2 a: an exponent change and a sign flip where a is normal (else the multiplication)
+    static __device__ __forceinline__ double minus_twice(double a)
+    {
+        const long long b = dm::dbits(a);
+        const long long m = b & 0x7fffffffffffffffLL;
+        if (m >= dm::kExpUnit && m < dm::kBitsInf - dm::kExpUnit)
+            return dm::from_bits((b ^ static_cast<long long>(0x8000000000000000ULL)) + dm::kExpUnit);
+        return -2.0 * a;
     }
 };
 
@@ -219,6 +266,9 @@ struct Prec<float> {
         *u1 = static_cast<float>(w.w[0] >> 8) * 0x1.0p-24f;
         *u2 = static_cast<float>(w.w[1] >> 8) * 0x1.0p-24f;
     }
+    static __device__ __forceinline__ float two_u_minus_one(float u) { return 2.0f * u - 1.0f; }
+    static __device__ __forceinline__ float minus_twice(float a) { return -2.0f * a; }
+    static __device__ __forceinline__ bool less_nonneg(float a, float b) { return a < b; }
     static __device__ __forceinline__ float wrap(float th)
     {
         const float two_pi = 2.0f * PI;
