@@ -296,14 +296,19 @@ int ul_free(ul_lattice* h);
  *                  least 48, smaller where the bound requires; in the slab-resident form one chunk's
  *                  contraction overlaps the next chunk's updates); fewer MiB means more,
  *                  smaller contractions (results change only by rounding)
- *   "contract_tiled"  1 (default): for UL_FP32_ACC64 the insertion contraction runs in a
- *                  tiled form (per block one slab, one z-plane, a tile of y-rows, two
- *                  separations and a set of offsets d; batches of 8 samples staged in shared
- *                  memory by bulk copies, two blocks per SM); 0: one thread per output
- *                  reading its operands from global memory.  Results are identical either
- *                  way; UL_FP64 always uses the untiled form.  A staging-copy wait that
- *                  reaches its time limit (about a second) is reported as UL_ETIMEOUT by the
- *                  level's result call.
+ *   "contract_tiled"  1 (default): the insertion contraction runs in a tiled form (per
+ *                  block one slab, one z-plane, a tile of y-rows, two separations and a set
+ *                  of offsets d; batches of samples staged in shared memory by bulk copies,
+ *                  two blocks per SM); 0: one thread per output reading its operands from
+ *                  global memory.  UL_FP32_ACC64: identical results either way.  UL_FP64:
+ *                  the per-sample values are stored as double-single pairs of floats (48
+ *                  significant bits) and the tiled form contracts them in double-single
+ *                  arithmetic on the FP32 pipes (a slab mean of T O within
+ *                  (2^-42 + n 2^-48) times the slab thickness for n samples per chunk), the
+ *                  untiled form in FP64; the field sums differ by that much, everything else
+ *                  is identical.  The 24-frame sums of UL_FP64 keep the untiled FP64 form.
+ *                  A staging-copy wait that reaches its time limit (about a second) is
+ *                  reported as UL_ETIMEOUT by the level's result call.
  *   "copy_stall_test"  0 (default), or n > 0 (integer <= 2e9): a test of the timeout path
  *                  of the tiled contraction.  Each block's first staged batch then waits for
  *                  16 bytes more than its copies deliver, so that wait gives up after n SM

@@ -64,10 +64,11 @@ struct ul_lattice {
     unsigned int* d_bar = nullptr;    // [0] arrivals, [1] generation
     int* d_status = nullptr;          // nonzero after a wait gave up
     cudaStream_t cap_stream = nullptr;
-    // second stream of the slab-resident form: the insertion contraction of one chunk runs
-    // on it while the next chunk's slab kernel runs on the handle's stream
+    // second stream: the insertion contraction of one chunk of sub-samples runs on it while
+    // the next chunk's updates run on the handle's stream; per sample buffer, ev_stored marks
+    // the chunk's samples written and ev_contract their contraction done
     cudaStream_t aux_stream = nullptr;
-    cudaEvent_t ev_slab[2] = {nullptr, nullptr};
+    cudaEvent_t ev_stored[2] = {nullptr, nullptr};
     cudaEvent_t ev_contract[2] = {nullptr, nullptr};
     // a level begun by ul_multilevel_fields_begin: its reduction and result copy run on
     // aux_stream into the pinned staging buffer; ev_result marks their completion
@@ -138,7 +139,7 @@ void release(ul_lattice* h)
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->aux_stream) cudaStreamSynchronize(h->aux_stream);
     for (int b = 0; b < 2; ++b) {
-        if (h->ev_slab[b]) cudaEventDestroy(h->ev_slab[b]);
+        if (h->ev_stored[b]) cudaEventDestroy(h->ev_stored[b]);
         if (h->ev_contract[b]) cudaEventDestroy(h->ev_contract[b]);
     }
     if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
@@ -441,8 +442,8 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             if (e != cudaSuccess) return cuda_fail(h, e, "slab-resident launch");
             h->launches += 1;
             if (fields) {
-                UL_CK(h, cudaEventRecord(h->ev_slab[buf], h->stream));
-                UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_slab[buf], 0));
+                UL_CK(h, cudaEventRecord(h->ev_stored[buf], h->stream));
+                UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_stored[buf], 0));
                 e = is_f64(h) ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum,
                                                                       chunk_first, h->aux_stream, h->contract_tiled,
                                                                       h->d_status, h->copy_wait_cycles)
@@ -460,11 +461,6 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
                 UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
             continue;
         }
-        const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count, chunk_first ? 1 : 0,
-                                            bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
-                                            reinterpret_cast<long long>(asum), reinterpret_cast<long long>(bsum),
-                                            reinterpret_cast<long long>(tk), reinterpret_cast<long long>(ok),
-                                            reinterpret_cast<long long>(osum), reinterpret_cast<long long>(ubar)};
         if (h->use_persistent) {
             ul::PersistArgs a = persist_args(h, count, sm, so, slab_t);
             a.measure = 1;
@@ -476,6 +472,8 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             a.ok = ok;
             a.osum = osum;
             a.ubar = ubar;
+            if (fields) // sample buffer 0 is free once earlier contractions on the second stream are done
+                for (int q = 0; q < 2; ++q) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[q], 0));
             rc = launch_persistent(h, a);
             if (rc) return rc;
             if (fields) {
@@ -491,6 +489,20 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
             k += count;
             continue;
         }
+        // Per-class launches: the chunk's passes and measurements, one launch sequence replayed
+        // as a graph, fill sample buffer chunk % 2 on the handle's stream; the chunk's
+        // contraction runs on the auxiliary stream beside the next chunk's updates (for FP64
+        // links the updates occupy the FP64 pipe and the double-single contraction the FP32
+        // pipes), in chunk order, so the sums are those of the serial order.
+        const int buf = (buf0 + chunk_index) % 2;
+        void* tkb = fields ? static_cast<char*>(tk) + static_cast<size_t>(buf) * n_a * 2 * rs * chunk : tk;
+        void* okb = fields ? static_cast<char*>(ok) + static_cast<size_t>(buf) * 8ull * S * g.L3 * rs * chunk : ok;
+        if (fields) UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
+        const std::vector<long long> key = {kGraphChunk, slab_t, sm, so, r_max, nd, count,
+                                            bits_of(h->beta), bits_of(h->width), static_cast<long long>(h->seed),
+                                            reinterpret_cast<long long>(asum), reinterpret_cast<long long>(tkb),
+                                            reinterpret_cast<long long>(okb), reinterpret_cast<long long>(osum),
+                                            reinterpret_cast<long long>(ubar)};
         rc = run_sequence(h, key, [&](cudaStream_t st, uint64_t first, const unsigned long long* base) -> long {
             long n = 0;
             for (int j = 0; j < count; ++j) {
@@ -505,25 +517,31 @@ int run_level(ul_lattice* h, int slab_t, int n_sub, int r_max, int nd, bool fiel
                     ++n;
                 }
                 e = is_f64(h)
-                    ? ul::launch_measure_store<double>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st)
-                    : ul::launch_measure_store<float>(g, h->cs, slab_t, r_max, fields, j, asum, tk, ok, osum, ubar, st);
+                    ? ul::launch_measure_store<double>(g, h->cs, slab_t, r_max, fields, j, asum, tkb, okb, osum, ubar, st)
+                    : ul::launch_measure_store<float>(g, h->cs, slab_t, r_max, fields, j, asum, tkb, okb, osum, ubar, st);
                 if (e != cudaSuccess) return cuda_fail(h, e, "measurement launch");
-                ++n;
-            }
-            if (fields) {
-                cudaError_t e = is_f64(h)
-                    ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first, st,
-                                                            h->contract_tiled, h->d_status, h->copy_wait_cycles)
-                    : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tk, ok, bsum, chunk_first, st,
-                                                           h->contract_tiled, h->d_status, h->copy_wait_cycles);
-                if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
                 ++n;
             }
             return n;
         });
         if (rc) return rc;
+        if (fields) {
+            UL_CK(h, cudaEventRecord(h->ev_stored[buf], h->stream));
+            UL_CK(h, cudaStreamWaitEvent(h->aux_stream, h->ev_stored[buf], 0));
+            cudaError_t e = is_f64(h)
+                ? ul::launch_insertion_contract<double>(g, slab_t, r_max, nd, count, tkb, okb, bsum, chunk_first,
+                                                        h->aux_stream, h->contract_tiled, h->d_status, h->copy_wait_cycles)
+                : ul::launch_insertion_contract<float>(g, slab_t, r_max, nd, count, tkb, okb, bsum, chunk_first,
+                                                       h->aux_stream, h->contract_tiled, h->d_status, h->copy_wait_cycles);
+            if (e != cudaSuccess) return cuda_fail(h, e, "insertion contraction launch");
+            UL_CK(h, cudaEventRecord(h->ev_contract[buf], h->aux_stream));
+            h->launches += 1;
+        }
         account_passes(h, sm * count, slab_t);
         k += count;
+        ++chunk_index;
+        if (k >= n_sub && fields && wait_contraction)
+            UL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_contract[buf], 0));
     }
     return UL_OK;
 }
@@ -701,7 +719,7 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
         if ((e = cudaEventCreateWithFlags(&h->ev_fold[b], cudaEventDisableTiming)) != cudaSuccess)
             return bail(e, "event");
     for (int b = 0; b < 2; ++b) {
-        if ((e = cudaEventCreateWithFlags(&h->ev_slab[b], cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
+        if ((e = cudaEventCreateWithFlags(&h->ev_stored[b], cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
         if ((e = cudaEventCreateWithFlags(&h->ev_contract[b], cudaEventDisableTiming)) != cudaSuccess)
             return bail(e, "event");
     }

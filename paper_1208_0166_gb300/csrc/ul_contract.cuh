@@ -338,37 +338,261 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     }
 }
 
-// set once the shared-memory limit has been raised: until then a tile that needs more than
-// the default 48 KB runs as the untiled kernel
+// ---------------------------------------------------------------------------
+// FP64 links: the same contraction over the double-single samples (SampleStore<double>),
+// in double-single arithmetic on the FP32 pipes.  A product a b of a = ah + al and
+// b = bh + bl is p = fl(ah bh) plus e = (ah bh - p) + ah bl + al bh (the first term exact by
+// a fused multiply-add; al bl, below 2^-46 |ah bh|, is left out), so with the 2^-48
+// representation error of each factor a term is within 2^-44 |a b|.  The running sum is a
+// pair (s, c): s takes p by an error-free two-sum whose error, with e, goes to c; after
+// each staged batch the pair is renormalised by a two-sum, so |c| stays near 2^-24 |s| and
+// a chunk of n samples is summed within (n 2^-48 + 2^-43) sum |T O|.  Once per output the
+// pair is widened to FP64 and added into bsum.  Same tiles, copies and bounded waits as the
+// FP32 form; a value takes two floats, so a staged batch holds kDsBatch samples.
+// ---------------------------------------------------------------------------
+constexpr int kDsBatch = 4;
+
+struct DsSum {
+    float s = 0.f, c = 0.f;
+    // s + c += (ah + al)(bh + bl)
+    __device__ __forceinline__ void add_prod(float ah, float al, float bh, float bl)
+    {
+        const float p = __fmul_rn(ah, bh);
+        float e = __fmaf_rn(ah, bh, -p);
+        e = __fmaf_rn(ah, bl, e);
+        e = __fmaf_rn(al, bh, e);
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void renormalise()
+    {
+        const float t = __fadd_rn(s, c);
+        const float z = __fsub_rn(t, s);
+        c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
+        s = t;
+    }
+    __device__ __forceinline__ double total() const { return static_cast<double>(s) + static_cast<double>(c); }
+};
+
+// Tile plan of the double-single form (see contract_tile): 16 bytes per staged transporter,
+// 64 per staged channel site.
+inline ContractTile contract_tile_ds(const Geo& g, int r_max, int nd, int max_items, int max_smem)
+{
+    ContractTile t;
+    const int L = g.L;
+    const int per_row = 2 * L;
+    t.ndb = std::min(nd, std::max(1, max_items / per_row));
+    t.ny = std::max(1, std::min(L, max_items / (per_row * t.ndb)));
+    t.bs = kDsBatch;
+    auto tpad = [&](int ny) { return ((64 - 16 * L * ny) % 128 + 128) % 128 / 4; };
+    auto rows_for = [&](int ny) { return std::min(L, ny + t.ndb - 1); };
+    auto smem_for = [&](int ny) {
+        const long per_sample = (8L * L * ny + tpad(ny) + 16L * rows_for(ny) * L) * sizeof(float);
+        return 2 * t.bs * per_sample;
+    };
+    while (t.ny > 1 && smem_for(t.ny) > max_smem) --t.ny;
+    t.tpad = tpad(t.ny);
+    t.rows = rows_for(t.ny);
+    const int items = per_row * t.ny * t.ndb;
+    t.threads = (items + 31) / 32 * 32;
+    t.smem = static_cast<int>(smem_for(t.ny));
+    t.ytiles = (L + t.ny - 1) / t.ny;
+    t.dsubs = (nd + t.ndb - 1) / t.ndb;
+    t.groups = (r_max + 1) / 2;
+    t.ok = items <= max_items && t.smem <= max_smem;
+    return t;
+}
+
+// Shared memory of one batch buffer (floats):
+//   T[j][ri][x0l] float4 {re hi, im hi, re lo, im lo}   (plane ri = 1 starts 4 L ny + tpad
+//                                                        floats after plane 0)
+//   O[j][rl][q][x] float4, part q of the channel pairs   (16 L floats per row)
+// Eight lanes of a 128-bit load read four consecutive sites of one part (64 contiguous
+// bytes) or the two transporter planes (64 bytes apart modulo 128): no bank conflicts.
+template <typename R> // double: the kernel of the FP64 links
+__global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
+    insertion_contract_ds_kernel(Geo g, int S, int r_max, int nd, int count, ContractTile t,
+                                 const float4* __restrict__ tk, const float4* __restrict__ ok,
+                                 double2* __restrict__ bsum, bool first, int* __restrict__ status,
+                                 long long wait_cycles)
+{
+    const bool stall_test = wait_cycles < 0;
+    const long long first_wait = stall_test ? -wait_cycles : wait_cycles;
+    extern __shared__ __align__(16) float smem[];
+    __shared__ unsigned long long bars[2];
+    constexpr int BS = kDsBatch;
+    const int L = g.L, L2 = g.L * g.L;
+    int b = static_cast<int>(blockIdx.x);
+    const int dsub = b % t.dsubs;
+    b /= t.dsubs;
+    const int gi = b % t.groups;
+    b /= t.groups;
+    const int ytile = b % t.ytiles;
+    b /= t.ytiles;
+    const int pz = b % L;
+    const int s = b / L;
+    int ra, rb;
+    contract_group(gi, r_max, ra, rb);
+    const int nr = rb ? 2 : 1;
+    const int py0 = ytile * t.ny, d0 = dsub * t.ndb;
+    const int nyv = min(t.ny, L - py0);
+    const int XT = L * t.ny;
+    const int row0 = (py0 + d0) % L;
+    const int tplane = 4 * XT + t.tpad;
+    const int tsz = 8 * XT + t.tpad, osz = t.rows * L * 16;
+    const int bufsz = BS * (tsz + osz);
+    const long plane = static_cast<long>(L2) * pz;
+
+    const int tid = static_cast<int>(threadIdx.x);
+    const int ri = tid & 1, item = tid >> 1;
+    const int px = item % L, pyl = (item / L) % t.ny, dl = item / (L * t.ny);
+    const int r = ri ? rb : ra;
+    const bool active = item < L * t.ny * t.ndb && r != 0 && pyl < nyv && d0 + dl < nd;
+    const int toff = ri * tplane + 4 * (px + L * pyl);
+    const int ooff = ((pyl + dl) % L) * L * 16 + ((px + r / 2) % L) * 4;
+
+    const int n1 = min(t.rows, L - row0);
+    const unsigned int t_bytes = static_cast<unsigned int>(nyv * L * sizeof(float4));
+    const unsigned int o_bytes = static_cast<unsigned int>(t.rows * L * 4 * sizeof(float4));
+    const float4* tsrc0 = tk + (static_cast<long>(s) * r_max + (ra - 1)) * g.L3 + plane + static_cast<long>(L) * py0;
+    const long t_db = static_cast<long>(rb - ra) * g.L3;
+    const long t_ks = static_cast<long>(S) * r_max * g.L3;       // float4 per sample
+    const float4* osrc0 = ok + (static_cast<long>(s) * g.L3 + plane) * 4;
+    const long o_ks = static_cast<long>(S) * g.L3 * 4;          // float4 per sample
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+
+    // copies of one batch into buffer buf by the lanes of warp 0 (lane j: sample k0 + j)
+    auto issue = [&](int k0, int buf, int nb, unsigned int extra_tx) {
+        float* base = smem + buf * bufsz;
+        const int lane = tid & 31;
+        if (lane == 0) mbar_arrive_expect_tx(&bars[buf], (nr * t_bytes + o_bytes) * nb + extra_tx);
+        __syncwarp();
+        for (int j = lane; j < nb; j += 32) {
+            const long k = k0 + j;
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            const float4* ts = tsrc0 + k * t_ks;
+            bulk_copy_g2s(base + j * tsz, ts, t_bytes, &bars[buf]);
+            if (nr == 2) bulk_copy_g2s(base + j * tsz + tplane, ts + t_db, t_bytes, &bars[buf]);
+            const float4* os = osrc0 + k * o_ks;
+            float* od = base + BS * tsz + j * osz;
+            const unsigned int seg1 = static_cast<unsigned int>(n1 * L * 4 * sizeof(float4));
+            bulk_copy_g2s(od, os + static_cast<long>(row0) * L * 4, seg1, &bars[buf]);
+            if (n1 < t.rows) bulk_copy_g2s(od + n1 * L * 16, os, o_bytes - seg1, &bars[buf]);
+        }
+    };
+
+    const long out = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d0 + dl) * 8) * g.L3 + px + L * (py0 + pyl) + plane;
+    DsSum are[8], aim[8];
+    const int nbatch = (count + BS - 1) / BS;
+    if (tid < 32) issue(0, 0, min(BS, count), stall_test ? 16u : 0u);
+    for (int bi = 0; bi < nbatch; ++bi) {
+        const int buf = bi & 1;
+        const int k0 = bi * BS;
+        const int nb = min(BS, count - k0);
+        if (bi + 1 < nbatch && tid < 32) issue(k0 + BS, buf ^ 1, min(BS, count - k0 - BS), 0u);
+        if (bi + 1 == nbatch && active && !first) {
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch)
+                asm volatile("prefetch.global.L2 [%0];\n" ::"l"(bsum + out + ch * g.L3));
+        }
+        const bool arrived = mbar_wait_bounded(&bars[buf], (bi >> 1) & 1, first_wait);
+        if (__syncthreads_or(!arrived)) {
+            if (tid == 0) {
+                atomicExch(status, 2);
+                mbar_wait_bounded(&bars[buf], (bi >> 1) & 1);
+                if (bi + 1 < nbatch) mbar_wait_bounded(&bars[buf ^ 1], ((bi + 1) >> 1) & 1);
+            }
+            return;
+        }
+        if (active) {
+            const float* sT = smem + buf * bufsz + toff;
+            const float* sO = smem + buf * bufsz + BS * tsz + ooff;
+            for (int j = 0; j < nb; ++j) {
+                const float4 tv = *reinterpret_cast<const float4*>(sT + j * tsz);
+                const float* o = sO + j * osz;
+                const float4 h0 = *reinterpret_cast<const float4*>(o);
+                const float4 h1 = *reinterpret_cast<const float4*>(o + 4 * L);
+                const float4 l0 = *reinterpret_cast<const float4*>(o + 8 * L);
+                const float4 l1 = *reinterpret_cast<const float4*>(o + 12 * L);
+                const float oh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                const float ol[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    are[ch].add_prod(tv.x, tv.z, oh[ch], ol[ch]);
+                    aim[ch].add_prod(tv.y, tv.w, oh[ch], ol[ch]);
+                }
+            }
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+                are[ch].renormalise();
+                aim[ch].renormalise();
+            }
+        }
+        __syncthreads(); // the next batch overwrites this buffer
+    }
+    if (!active) return;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+        double2 v = first ? make_double2(0.0, 0.0) : bsum[out + ch * g.L3];
+        v.x += are[ch].total();
+        v.y += aim[ch].total();
+        bsum[out + ch * g.L3] = v;
+    }
+}
+
+// set (per link precision) once the shared-memory limit has been raised: until then a tile
+// that needs more than the default 48 KB runs as the untiled kernel
+template <typename R>
 inline std::atomic<bool> g_contract_prepared{false};
 
 template <typename R>
 cudaError_t prepare_insertion_contract()
 {
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 8) {
+        const cudaError_t e = cudaFuncSetAttribute(insertion_contract_ds_kernel<double>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
+        if (e == cudaSuccess) g_contract_prepared<R>.store(true);
+        return e;
+    } else {
         cudaError_t e = cudaFuncSetAttribute(insertion_contract_tiled_kernel<float, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(insertion_contract_tiled_kernel<float, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kContractSmem);
-        if (e == cudaSuccess) g_contract_prepared.store(true);
+        if (e == cudaSuccess) g_contract_prepared<R>.store(true);
         return e;
     }
     return cudaSuccess;
 }
 
-// Launches the tiled form for FP32 links (sym: the 24-frame sums of three axes); returns
-// false (nothing launched) where it does not apply, and the caller runs the untiled kernel.
+// Launches the tiled form: for FP32 links the FP32 kernel (sym: the 24-frame sums of three
+// axes), for FP64 links the double-single kernel (single-frame sums only); returns false
+// (nothing launched) where it does not apply, and the caller runs the untiled kernel.
 template <typename R>
 bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, const void* tk, const void* ok,
                            double2* bsum, bool first, int* status, cudaStream_t st, cudaError_t* err, bool sym,
                            long long wait_cycles)
 {
-    if constexpr (sizeof(R) != 4) {
-        return false;
+    if constexpr (sizeof(R) == 8) {
+        const ContractTile t = contract_tile_ds(g, r_max, nd, kContractItems, kContractSmem);
+        if (sym || !t.ok || count < 1 || (t.smem > 48 * 1024 && !g_contract_prepared<R>.load())) return false;
+        const long blocks = static_cast<long>(S) * g.L * t.ytiles * t.groups * t.dsubs;
+        insertion_contract_ds_kernel<double><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
+            g, S, r_max, nd, count, t, static_cast<const float4*>(tk), static_cast<const float4*>(ok), bsum, first,
+            status, wait_cycles);
+        *err = cudaGetLastError();
+        return true;
     } else {
         const ContractTile t = contract_tile(g, r_max, nd, kContractItems, kContractSmem, sym);
-        if (!t.ok || count < 1 || (t.smem > 48 * 1024 && !g_contract_prepared.load())) return false;
+        if (!t.ok || count < 1 || (t.smem > 48 * 1024 && !g_contract_prepared<R>.load())) return false;
         const long blocks = static_cast<long>(sym ? 3 : 1) * S * g.L * t.ytiles * t.groups * t.dsubs;
         const auto* tkf = static_cast<const Cx<float>*>(tk);
         const auto* okf = static_cast<const float*>(ok);

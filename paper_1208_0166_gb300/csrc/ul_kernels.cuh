@@ -512,6 +512,105 @@ static __global__ void __launch_bounds__(kThreads) sum_partials_kernel(const dou
 __device__ __constant__ static const int kPlaneMu[4] = {0, 0, 0, 2};
 __device__ __constant__ static const int kPlaneNu[4] = {1, 2, 3, 3};
 
+// ---------------------------------------------------------------------------
+// Per-sample storage of the deferred insertion contraction (Section 2.2: the insertion
+// term of a slab is the sample mean of T O).  FP32 links: T as a complex float, the 8
+// channel sums of a site as 8 floats.  FP64 links: every value as a double-single pair
+// (hi, lo) of floats in the value's own 8 bytes, so that the contraction runs in
+// double-single arithmetic on the FP32 pipes instead of on the FP64 pipe:
+//   T: one float4 {re hi, im hi, re lo, im lo} in the 16 bytes of the complex double;
+//   O: the 64 bytes per site of an x-row of L sites hold four parts {hi ch 0-3, hi ch 4-7,
+//      lo ch 0-3, lo ch 4-7}, part-major: part q of site x at float4 (row start) + q L + x,
+//      so that one part of consecutive sites is contiguous.
+// ---------------------------------------------------------------------------
+
+// x = hi + lo: hi the leading 24 significant bits of x (truncated), lo the remaining 29
+// bits rounded to a float, so |lo| < 2^-23 |hi| and |x - hi - lo| <= max(2^-48 |x|, 2^-126):
+// integer operations only; a part below the normal float range (2^-126) is stored as 0,
+// |x| >= 2^128 as infinity (the stored samples are bounded by the slab thickness).
+__device__ __forceinline__ float2 ds_split(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int hw = static_cast<unsigned int>(b >> 32), lw = static_cast<unsigned int>(b);
+    const unsigned int sign = hw & 0x80000000u;
+    const int e = static_cast<int>((hw >> 20) & 0x7ffu); // biased FP64 exponent
+    const int ef = e - 1023 + 127;                       // biased FP32 exponent of hi
+    if (ef <= 0) return make_float2(0.f, 0.f);
+    if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const float hi = __uint_as_float(sign | (static_cast<unsigned int>(ef) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    const unsigned int rem = lw & 0x1fffffffu; // the remaining bits, in units of 2^(e - 1075)
+    float lo = 0.f;
+    if (rem != 0) {
+        const unsigned int fr = __float_as_uint(__uint2float_rn(rem));
+        const int ex = static_cast<int>(fr >> 23) + (e - 1075); // biased exponent of rem 2^(e - 1075)
+        if (ex > 0) lo = __uint_as_float(sign | (static_cast<unsigned int>(ex) << 23) | (fr & 0x7fffffu));
+    }
+    return make_float2(hi, lo);
+}
+
+template <typename R>
+struct SampleStore;
+
+template <>
+struct SampleStore<float> {
+    static __device__ __forceinline__ void put_T(Cx<float>* tk, long i, Cx<float> T) { tk[i] = T; }
+    // site: index of the site in the buffer (slot S L3 + s L3 + x0); x: its x coordinate
+    static __device__ __forceinline__ void put_O(float* ok, long site, int /*x*/, int /*L*/, const float v[8])
+    {
+        float4* o = reinterpret_cast<float4*>(ok + site * 8);
+        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    static __device__ __forceinline__ Cx<float> get_T(const Cx<float>* tk, long i) { return tk[i]; }
+    static __device__ __forceinline__ void get_O(const float* ok, long site, int /*x*/, int /*L*/, float v[8])
+    {
+        const float4 a = reinterpret_cast<const float4*>(ok + site * 8)[0];
+        const float4 b = reinterpret_cast<const float4*>(ok + site * 8)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+};
+
+template <>
+struct SampleStore<double> {
+    static __device__ __forceinline__ void put_T(Cx<double>* tk, long i, Cx<double> T)
+    {
+        const float2 re = ds_split(T.re), im = ds_split(T.im);
+        reinterpret_cast<float4*>(tk)[i] = make_float4(re.x, im.x, re.y, im.y);
+    }
+    static __device__ __forceinline__ void put_O(double* ok, long site, int x, int L, const double v[8])
+    {
+        float2 d[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) d[ch] = ds_split(v[ch]);
+        float4* o = reinterpret_cast<float4*>(ok) + (site - x) * 4 + x;
+        o[0] = make_float4(d[0].x, d[1].x, d[2].x, d[3].x);
+        o[L] = make_float4(d[4].x, d[5].x, d[6].x, d[7].x);
+        o[2 * L] = make_float4(d[0].y, d[1].y, d[2].y, d[3].y);
+        o[3 * L] = make_float4(d[4].y, d[5].y, d[6].y, d[7].y);
+    }
+    // the stored pairs as doubles (hi + lo is exact in FP64)
+    static __device__ __forceinline__ Cx<double> get_T(const Cx<double>* tk, long i)
+    {
+        const float4 v = reinterpret_cast<const float4*>(tk)[i];
+        return Cx<double>{static_cast<double>(v.x) + static_cast<double>(v.z),
+                          static_cast<double>(v.y) + static_cast<double>(v.w)};
+    }
+    static __device__ __forceinline__ void get_O(const double* ok, long site, int x, int L, double v[8])
+    {
+        const float4* o = reinterpret_cast<const float4*>(ok) + (site - x) * 4 + x;
+        const float4 h0 = o[0], h1 = o[L], l0 = o[2 * L], l1 = o[3 * L];
+        v[0] = static_cast<double>(h0.x) + static_cast<double>(l0.x);
+        v[1] = static_cast<double>(h0.y) + static_cast<double>(l0.y);
+        v[2] = static_cast<double>(h0.z) + static_cast<double>(l0.z);
+        v[3] = static_cast<double>(h0.w) + static_cast<double>(l0.w);
+        v[4] = static_cast<double>(h1.x) + static_cast<double>(l1.x);
+        v[5] = static_cast<double>(h1.y) + static_cast<double>(l1.y);
+        v[6] = static_cast<double>(h1.z) + static_cast<double>(l1.z);
+        v[7] = static_cast<double>(h1.w) + static_cast<double>(l1.w);
+    }
+};
+
 // One measurement after sub-sample k, thread per (s, x0).  With the slab line
 // W(s, x) = prod_{t in slab s} U_0(x, t) (partial Polyakov line),
 //   T(s, x0, r) = prod_{t in slab} U*_0(x0,t) U_0(x0 + r xhat, t) = W*(s, x0) W(s, x0 + r xhat),
@@ -519,7 +618,8 @@ __device__ __constant__ static const int kPlaneNu[4] = {1, 2, 3, 3};
 // and, with fields, the slab sums of the 8 plaquette channels at x0,
 //   O(s, x0, ch) = sum_{t in slab s} channel_ch(x0, t),   osum[ch*SL3 + s*L3 + x0] += O,
 // with T and O stored for the deferred insertion contraction:
-//   tk[((slot*S + s)*R + r-1)*L3 + x0] = T,   ok[((slot*S + s)*L3 + x0)*8 + ch] = O.
+//   tk[((slot*S + s)*R + r-1)*L3 + x0] = T,   ok at site (slot*S + s)*L3 + x0 = O
+// (SampleStore: plain values for FP32 links, double-single pairs for FP64 links).
 // The per-sample products are formed in the link precision R (FP64 or FP32); every
 // accumulator is FP64.
 template <typename R, bool CG = false>
@@ -581,7 +681,7 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
 #ifdef UL_CHECK
         if (fields && (slot < 0 || x1 < 0 || x1 >= g.L3)) (void)UL_IDX(-1, 0, kChkSample);
 #endif
-        if (fields) tk[(static_cast<long>(slot * S + s) * r_max + (r - 1)) * g.L3 + x0] = T;
+        if (fields) SampleStore<R>::put_T(tk, (static_cast<long>(slot * S + s) * r_max + (r - 1)) * g.L3 + x0, T);
     }
     if (!fields) return;
     R acc[8];
@@ -603,10 +703,9 @@ __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* 
         }
     }
     const int SL3 = S * g.L3;
-    R* o = ok + (static_cast<long>(slot) * SL3 + k) * 8;
+    SampleStore<R>::put_O(ok, static_cast<long>(slot) * SL3 + k, px, g.L, acc);
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
-        o[ch] = acc[ch];
 #ifdef UL_CHECK
         const long oi = UL_IDX(static_cast<long>(ch) * SL3 + k, 8LL * SL3, kChkOsum);
         osum[oi] = ld_link<double, CG>(osum + oi) + static_cast<double>(acc[ch]);
@@ -774,13 +873,14 @@ __global__ void __launch_bounds__(kThreads, kContractMinBlocks)
     const int x0 = tile * kThreads + static_cast<int>(threadIdx.x);
     if (x0 >= g.L3) return;
     const int px = x0 % g.L, py = (x0 / g.L) % g.L, pz = x0 / (g.L * g.L);
-    const int y = (px + r / 2) % g.L + g.L * ((py + d) % g.L + g.L * pz);
+    const int yx = (px + r / 2) % g.L;
+    const int y = yx + g.L * ((py + d) % g.L + g.L * pz);
     const long SL3 = static_cast<long>(S) * g.L3;
     InsertionAcc<R> acc[8];
     for (int k = 0; k < count; ++k) {
-        const Cx<R> T = tk[(static_cast<long>(k * S + s) * r_max + (r - 1)) * g.L3 + x0];
+        const Cx<R> T = SampleStore<R>::get_T(tk, (static_cast<long>(k * S + s) * r_max + (r - 1)) * g.L3 + x0);
         R o[8];
-        Vec8<R>::load(ok + (k * SL3 + static_cast<long>(s) * g.L3 + y) * 8, o);
+        SampleStore<R>::get_O(ok, k * SL3 + static_cast<long>(s) * g.L3 + y, yx, g.L, o);
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) acc[ch].add(T, o[ch]);
         if (k % kInsertionBlock == kInsertionBlock - 1)

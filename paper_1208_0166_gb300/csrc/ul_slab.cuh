@@ -201,7 +201,8 @@ __device__ __forceinline__ void slab_measure(const SlabLinks<R, LC>& S, const Ge
             av.y += static_cast<double>(T.im);
             a.asum[ai] = av;
             if (a.fields)
-                static_cast<Cx<R>*>(a.tk)[(static_cast<long>(slot * nS + s) * a.r_max + (r - 1)) * g.L3 + x0] = T;
+                SampleStore<R>::put_T(static_cast<Cx<R>*>(a.tk),
+                                      (static_cast<long>(slot * nS + s) * a.r_max + (r - 1)) * g.L3 + x0, T);
         }
         if (!a.fields) continue;
         const SlabSteps st(x, y, L);
@@ -234,12 +235,9 @@ __device__ __forceinline__ void slab_measure(const SlabLinks<R, LC>& S, const Ge
             acc[6] += b1.im;
             acc[7] += b1.re;
         }
-        R* o = static_cast<R*>(a.ok) + (static_cast<long>(slot) * SL3 + kk) * 8;
+        SampleStore<R>::put_O(static_cast<R*>(a.ok), static_cast<long>(slot) * SL3 + kk, x, L, acc);
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-            o[ch] = acc[ch];
-            a.osum[ch * SL3 + kk] += static_cast<double>(acc[ch]);
-        }
+        for (int ch = 0; ch < 8; ++ch) a.osum[ch * SL3 + kk] += static_cast<double>(acc[ch]);
     }
 }
 

@@ -15,6 +15,12 @@ unit phases).  Hence
 
     tol64 = 1e-12 |want| + u B (n / N) (2 (n - 1) + 8 S (2 tau + 4)).
 
+The field sums of FP64 links have one more term.  Their samples are stored as
+double-single pairs of floats (48 significant bits) and contracted in double-single
+arithmetic: a product within 2^-44 |T O|, a chunk of n_c <= n_sub samples summed within
+(n_c 2^-48 + 2^-43) sum |T O|, so a slab mean of T O is within (2^-42 + n_c 2^-48) B =
+u B (2^11 + 32 n_c), and the field estimator gains u B (n / N) (2^11 + 32 n_sub).
+
 FP32 links against the FP64 path on a frozen configuration (sub-samples without updates,
 so every slab mean equals its one transporter and |A_s| = 1).  Each rounded FP32 quantity
 (a link angle, a sine or cosine, a component of a complex product) carries an error with a
@@ -76,7 +82,8 @@ def fp64_tolerances(want: dict, L: int, Nt: int, tau: int, n_sub: int, frames: i
     if "fields" in want:
         n, N = L3 * S * frames, V * frames
         B = float(tau)
-        out["fields"] = 1e-12 * np.abs(want["fields"]) + U64 * B * (n / N) * (2 * (n - 1) + per)
+        ds = 2 ** 11 + 32 * max(n_sub, 1)  # double-single contraction of the FP64 samples
+        out["fields"] = 1e-12 * np.abs(want["fields"]) + U64 * B * (n / N) * (2 * (n - 1) + per + ds)
     if "vac" in want:
         n = V * max(n_sub, 1) * frames
         out["vac"] = 1e-12 * np.abs(want["vac"]) + U64 * 1.0 * (2 * (n - 1) + per)
