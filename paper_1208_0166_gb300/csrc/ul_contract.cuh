@@ -347,8 +347,9 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
 // pair (s, c): s takes p by an error-free two-sum whose error, with e, goes to c; after
 // each staged batch the pair is renormalised by a two-sum, so |c| stays near 2^-24 |s| and
 // a chunk of n samples is summed within (n 2^-48 + 2^-43) sum |T O|.  Once per output the
-// pair is widened to FP64 and added into bsum.  Same tiles, copies and bounded waits as the
-// FP32 form; a value takes two floats, so a staged batch holds kDsBatch samples.
+// pair is widened to FP64 (exactly, by integer operations) and added into bsum.  Same tiles,
+// copies and bounded waits as the FP32 form; a value takes two floats, so a staged batch
+// holds kDsBatch samples.
 // ---------------------------------------------------------------------------
 constexpr int kDsBatch = 4;
 
@@ -374,7 +375,17 @@ struct DsSum {
         c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
         s = t;
     }
-    __device__ __forceinline__ double total() const { return static_cast<double>(s) + static_cast<double>(c); }
+    // bsum + s + c in FP64; the widening of s and c to FP64 is exact and done by integer
+    // operations (a part below 2^-126 counts as 0), leaving two FP64 additions
+    __device__ __forceinline__ double added_to(double b) const { return (b + widen(s)) + widen(c); }
+    static __device__ __forceinline__ double widen(float x)
+    {
+        const unsigned int u = __float_as_uint(x);
+        const unsigned int e = (u >> 23) & 0xffu;
+        if (e == 0) return 0.0;
+        const unsigned int hi = (u & 0x80000000u) | ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+        return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+    }
 };
 
 // Tile plan of the double-single form (see contract_tile): 16 bytes per staged transporter,
@@ -515,7 +526,7 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
         if (active) {
             const float* sT = smem + buf * bufsz + toff;
             const float* sO = smem + buf * bufsz + BS * tsz + ooff;
-            for (int j = 0; j < nb; ++j) {
+            auto sample = [&](int j) {
                 const float4 tv = *reinterpret_cast<const float4*>(sT + j * tsz);
                 const float* o = sO + j * osz;
                 const float4 h0 = *reinterpret_cast<const float4*>(o);
@@ -529,6 +540,12 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
                     are[ch].add_prod(tv.x, tv.z, oh[ch], ol[ch]);
                     aim[ch].add_prod(tv.y, tv.w, oh[ch], ol[ch]);
                 }
+            };
+            if (nb == BS) {
+#pragma unroll
+                for (int j = 0; j < BS; ++j) sample(j);
+            } else {
+                for (int j = 0; j < nb; ++j) sample(j);
             }
 #pragma unroll
             for (int ch = 0; ch < 8; ++ch) {
@@ -542,8 +559,8 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
         double2 v = first ? make_double2(0.0, 0.0) : bsum[out + ch * g.L3];
-        v.x += are[ch].total();
-        v.y += aim[ch].total();
+        v.x = are[ch].added_to(v.x);
+        v.y = aim[ch].added_to(v.y);
         bsum[out + ch * g.L3] = v;
     }
 }

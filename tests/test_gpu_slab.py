@@ -118,3 +118,18 @@ def test_slab_resident_sixteen_cta_clusters_at_32():
     assert np.array_equal(a.get_links(), b.get_links())
     for key in ("corr", "fields", "vac"):
         assert np.array_equal(ra[key], rb[key])
+
+
+@pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
+@pytest.mark.parametrize("L,Nt,tau,cluster", [(12, 4, 2, 4), (10, 4, 2, 2), (6, 4, 2, 1), (4, 4, 1, 1)])
+def test_slab_resident_several_planes_per_cta(prec, L, Nt, tau, cluster):
+    """CTAs of three or more z planes (inner planes whose staples stay inside the CTA; planes
+    of 72, 50, 18 and 8 half-sites, so warps that span two planes): the trajectory and the
+    observables are those of the per-class launches bit for bit."""
+    a, ra, la = _run(L, Nt, 19, prec, 1, tau, 3, 2, 3, cluster)
+    b, rb, lb = _run(L, Nt, 19, prec, 0, tau, 3, 2, 3)
+    assert la <= 2 * 3 + 3 < lb, "the slab-resident form did not run"
+    assert np.array_equal(a.get_links(), b.get_links())
+    assert a.stats() == b.stats()
+    for key in ("corr", "fields", "vac"):
+        assert np.array_equal(ra[key], rb[key]), key
