@@ -131,8 +131,8 @@ TRAFFIC = {
     # (launches 8 and 9 of the profiled step, Metropolis mu = 3 and overrelaxation mu = 0;
     # ncu replays with cold caches, while in the bench the lattice is L2-resident):
     # profiles/update_class_f64_24x24.md, profiles/update_class_f32_24x24.md
-    ("fp64", "31960ca63a73c73e"): (22628864 + 19974400) / 2,
-    ("fp32", "663d112ecedb9f54"): (11328256 + 10000384) / 2,
+    ("fp64", "b522978fea71983f"): (22629120 + 19974400) / 2,
+    ("fp32", "b522978fea71983f"): (11328256 + 10000384) / 2,
 }
 
 
