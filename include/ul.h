@@ -273,8 +273,9 @@ int ul_free(ul_lattice* h);
  *                  every wait runs into its limit (for testing the timeout path); 0 (default).
  *   "pdl"          1: consecutive class kernels use programmatic dependent launch (the
  *                  next one is scheduled while the previous one runs and waits for its
- *                  completion before reading links); 0: plain stream order.  Default 1
- *                  for UL_FP32_ACC64, 0 for UL_FP64.  Results are identical either way.
+ *                  completion before reading links); 2: in compound sweeps only, not in
+ *                  the passes of sub-samples; 0: plain stream order.  Default 1 for
+ *                  UL_FP32_ACC64, 2 for UL_FP64.  Results are identical in every mode.
  *   "graphs"       1 (default): recurring launch sequences (a compound sweep, a chunk of
  *                  sub-samples) are captured once into CUDA graphs and replayed; 0: every
  *                  kernel is launched directly.  Results are identical either way.

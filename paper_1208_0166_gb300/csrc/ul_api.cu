@@ -50,7 +50,9 @@ struct ul_lattice {
     };
     std::vector<Graph> graphs;
     bool use_graphs = true;
-    bool use_pdl = true; // programmatic dependent launch of consecutive class kernels
+    // programmatic dependent launch of consecutive class kernels: 0 never, 1 always, 2 in
+    // compound sweeps only (not in the sub-sample passes, which alternate with measurements)
+    int use_pdl = 1;
     unsigned long long* d_pass_base = nullptr;
     // persistent cooperative sweeps with a bounded-wait grid barrier
     bool use_persistent = false;
@@ -202,6 +204,7 @@ long enqueue_passes(ul_lattice* h, cudaStream_t st, int n_metro, int n_or, int s
                     const unsigned long long* pass_base)
 {
     long n = 0;
+    const bool pdl = h->use_pdl == 1 || (h->use_pdl == 2 && slab_t == 0);
     for (int k = 0; k < n_metro + n_or; ++k) {
         const bool metro = k < n_metro;
         const uint64_t pass = first_pass + (metro ? static_cast<uint64_t>(k) : 0);
@@ -211,10 +214,10 @@ long enqueue_passes(ul_lattice* h, cudaStream_t st, int n_metro, int n_or, int s
                 cudaError_t e = is_f64(h)
                     ? ul::launch_update_class<double>(h->g, static_cast<double*>(h->theta), h->cs, mu, par, metro, pass,
                                                       pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st,
-                                                      &launched, h->use_pdl)
+                                                      &launched, pdl)
                     : ul::launch_update_class<float>(h->g, static_cast<float*>(h->theta), h->cs, mu, par, metro, pass,
                                                      pass_base, h->seed, h->beta, h->width, slab_t, h->d_accepted, st,
-                                                     &launched, h->use_pdl);
+                                                     &launched, pdl);
                 if (e != cudaSuccess) return cuda_fail(h, e, "update kernel launch");
                 n += launched;
             }
@@ -705,7 +708,7 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
     h->use_persistent = false;
     // programmatic dependent launch: measured faster for FP32 classes (4.94 -> 4.60 us at 24^4)
     // and slower for FP64 classes (51.8 -> 56.5 us), so on by default for FP32 only
-    h->use_pdl = precision == UL_FP32_ACC64;
+    h->use_pdl = precision == UL_FP32_ACC64 ? 1 : 2;
     // slab-resident sub-samples: measured faster for FP32 at 24^4 (step 57.4 -> 49.8 ms); the
     // FP64 form is bound by the FP64 pipe and a cluster form leaves a third of the SMs idle
     h->slab_mode = precision == UL_FP32_ACC64 ? 1 : 0;
@@ -1206,8 +1209,8 @@ int ul_set_option(ul_lattice* h, const char* key, double v)
         if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "barrier_unreachable must be 0 or 1");
         h->barrier_unreachable = v != 0.0;
     } else if (!std::strcmp(key, "pdl")) {
-        if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "pdl must be 0 or 1");
-        h->use_pdl = v != 0.0;
+        if (v != 0.0 && v != 1.0 && v != 2.0) return fail(h, UL_EINVAL, "pdl must be 0, 1 or 2");
+        h->use_pdl = static_cast<int>(v);
         drop_graphs(h, 0); // captured sequences carry the launch attribute
     } else if (!std::strcmp(key, "graphs")) {
         if (v != 0.0 && v != 1.0) return fail(h, UL_EINVAL, "graphs must be 0 or 1");

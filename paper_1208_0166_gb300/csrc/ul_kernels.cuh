@@ -654,23 +654,26 @@ __device__ __forceinline__ Cx<R> slab_line_mh(const Geo& g, const Cx<R>* __restr
 
 // ubar (may be null): multihit temporal links by lexicographic site; when set, the
 // correlator at r >= 2 uses them (the insertion samples keep the links themselves).
+// wrow (may be null): the slab lines W(s, x) of the x-row of site k, indexed by x (formed
+// once per row by the caller); when null each line is formed here.  Same products either way.
 template <typename R, bool CG = false>
 __device__ __forceinline__ void measure_store_site(const Geo& g, const cs_t<R>* __restrict__ cs, int slab_t,
                                                    int r_max, int fields, int slot, double2* __restrict__ asum,
                                                    Cx<R>* __restrict__ tk, R* __restrict__ ok,
                                                    double* __restrict__ osum, int k,
-                                                   const Cx<R>* __restrict__ ubar = nullptr)
+                                                   const Cx<R>* __restrict__ ubar = nullptr,
+                                                   const Cx<R>* wrow = nullptr)
 {
     const int S = g.Nt / slab_t;
     const int s = k / g.L3;
     const int x0 = k - s * g.L3;
     const int px = x0 % g.L, pyz = x0 - px;
     const int t0 = s * slab_t;
-    const Cx<R> w0 = cconj(slab_line<R, CG>(g, cs, x0, t0, slab_t));
+    const Cx<R> w0 = cconj(wrow ? wrow[px] : slab_line<R, CG>(g, cs, x0, t0, slab_t));
     const Cx<R> w0m = ubar ? cconj(slab_line_mh<R, CG>(g, ubar, x0, t0, slab_t)) : w0;
     for (int r = 1; r <= r_max; ++r) {
         const int x1 = (px + r) % g.L + pyz;
-        const Cx<R> T = cmul_rn(w0, slab_line<R, CG>(g, cs, x1, t0, slab_t));
+        const Cx<R> T = cmul_rn(w0, wrow ? wrow[(px + r) % g.L] : slab_line<R, CG>(g, cs, x1, t0, slab_t));
         const Cx<R> Tc = (ubar && r >= 2) ? cmul_rn(w0m, slab_line_mh<R, CG>(g, ubar, x1, t0, slab_t)) : T;
         const long ai = UL_IDX(static_cast<long>(s * r_max + (r - 1)) * g.L3 + x0,
                                static_cast<long long>(S) * r_max * g.L3, kChkAsum);
@@ -724,6 +727,28 @@ __global__ void __launch_bounds__(kThreads)
     const int k = blockIdx.x * blockDim.x + threadIdx.x; // s*L3 + x0
     if (k >= (g.Nt / slab_t) * g.L3) return;
     measure_store_site<R>(g, cs, slab_t, r_max, fields, slot, asum, tk, ok, osum, k, ubar);
+}
+
+// The same with blocks of whole x-rows (blockDim a multiple of L): each thread forms the
+// slab line of its own site into shared memory, and the transporters T(x0, r) take the
+// lines of the row from there (each line formed once instead of r_max + 1 times).
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    measure_store_rows_kernel(Geo g, const cs_t<R>* __restrict__ cs, int slab_t, int r_max, int fields, int slot,
+                              double2* __restrict__ asum, Cx<R>* __restrict__ tk, R* __restrict__ ok,
+                              double* __restrict__ osum)
+{
+    __shared__ Cx<R> w[kThreads];
+    const int tid = static_cast<int>(threadIdx.x);
+    const int k = blockIdx.x * blockDim.x + tid; // s*L3 + x0
+    const bool valid = k < (g.Nt / slab_t) * g.L3;
+    if (valid) {
+        const int s = k / g.L3;
+        w[tid] = slab_line<R>(g, cs, k - s * g.L3, s * slab_t, slab_t);
+    }
+    __syncthreads();
+    if (!valid) return;
+    measure_store_site<R>(g, cs, slab_t, r_max, fields, slot, asum, tk, ok, osum, k, nullptr, w + (tid - k % g.L));
 }
 
 // ---------------------------------------------------------------------------
@@ -1168,6 +1193,14 @@ cudaError_t launch_measure_store(const Geo& g, const void* cs, int slab_t, int r
 {
     const int S = g.Nt / slab_t;
     const long n = static_cast<long>(S) * g.L3;
+    if (!ubar && g.L <= kThreads) {
+        // blocks of whole x-rows, about 192 threads
+        const int threads = g.L * std::max(1, std::min(kThreads / g.L, 192 / g.L));
+        measure_store_rows_kernel<R><<<static_cast<unsigned int>((n + threads - 1) / threads), threads, 0, st>>>(
+            g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, fields ? 1 : 0, slot, asum, static_cast<Cx<R>*>(tk),
+            static_cast<R*>(ok), osum);
+        return cudaGetLastError();
+    }
     const int threads = update_block_threads(n); // balanced over the SMs, as the class updates
     measure_store_kernel<R><<<static_cast<unsigned int>((n + threads - 1) / threads), threads, 0, st>>>(
         g, static_cast<const cs_t<R>*>(cs), slab_t, r_max, fields ? 1 : 0, slot, asum, static_cast<Cx<R>*>(tk),
