@@ -349,35 +349,45 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
 // a chunk of n samples is summed within (n 2^-48 + 2^-43) sum |T O|.  Once per output the
 // pair is widened to FP64 (exactly, by integer operations) and added into bsum.  Same tiles,
 // copies and bounded waits as the FP32 form; a value takes two floats, so a staged batch
-// holds kDsBatch samples.
+// holds kDsBatch samples.  The real and imaginary parts run as the two lanes of paired FP32
+// instructions.
 // ---------------------------------------------------------------------------
 constexpr int kDsBatch = 4;
 
-struct DsSum {
-    float s = 0.f, c = 0.f;
-    // s + c += (ah + al)(bh + bl)
-    __device__ __forceinline__ void add_prod(float ah, float al, float bh, float bl)
+// Paired FP32 arithmetic on (re, im) lanes (FFMA2 / FADD2 / FMUL2: two IEEE single
+// operations per instruction, each lane rounded as the scalar operation would be).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+
+// Running double-single sums of the real and imaginary parts of one output channel.
+struct DsSum2 {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    // (s + c) += (ah + al)(bh + bl) in each lane
+    __device__ __forceinline__ void add_prod(float2 ah, float2 al, float2 bh, float2 bl)
     {
-        const float p = __fmul_rn(ah, bh);
-        float e = __fmaf_rn(ah, bh, -p);
-        e = __fmaf_rn(ah, bl, e);
-        e = __fmaf_rn(al, bh, e);
-        const float t = __fadd_rn(s, p);
-        const float z = __fsub_rn(t, s);
-        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        const float2 p = __fmul2_rn(ah, bh);
+        float2 e = __ffma2_rn(ah, bh, neg2(p));
+        e = __ffma2_rn(ah, bl, e);
+        e = __ffma2_rn(al, bh, e);
+        const float2 t = __fadd2_rn(s, p);
+        const float2 z = sub2(t, s);
+        const float2 err = __fadd2_rn(sub2(s, sub2(t, z)), sub2(p, z));
         s = t;
-        c = __fadd_rn(c, __fadd_rn(err, e));
+        c = __fadd2_rn(c, __fadd2_rn(err, e));
     }
     __device__ __forceinline__ void renormalise()
     {
-        const float t = __fadd_rn(s, c);
-        const float z = __fsub_rn(t, s);
-        c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
+        const float2 t = __fadd2_rn(s, c);
+        const float2 z = sub2(t, s);
+        c = __fadd2_rn(sub2(s, sub2(t, z)), sub2(c, z));
         s = t;
     }
-    // bsum + s + c in FP64; the widening of s and c to FP64 is exact and done by integer
-    // operations (a part below 2^-126 counts as 0), leaving two FP64 additions
-    __device__ __forceinline__ double added_to(double b) const { return (b + widen(s)) + widen(c); }
+    // bsum + s + c in FP64 per lane; the widening of s and c to FP64 is exact and done by
+    // integer operations (a part below 2^-126 counts as 0), leaving two FP64 additions
+    __device__ __forceinline__ double2 added_to(double2 b) const
+    {
+        return make_double2((b.x + widen(s.x)) + widen(c.x), (b.y + widen(s.y)) + widen(c.y));
+    }
     static __device__ __forceinline__ double widen(float x)
     {
         const unsigned int u = __float_as_uint(x);
@@ -501,7 +511,7 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
     };
 
     const long out = (((static_cast<long>(s) * r_max + (r - 1)) * nd + d0 + dl) * 8) * g.L3 + px + L * (py0 + pyl) + plane;
-    DsSum are[8], aim[8];
+    DsSum2 acc[8];
     const int nbatch = (count + BS - 1) / BS;
     if (tid < 32) issue(0, 0, min(BS, count), stall_test ? 16u : 0u);
     for (int bi = 0; bi < nbatch; ++bi) {
@@ -535,11 +545,10 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
                 const float4 l1 = *reinterpret_cast<const float4*>(o + 12 * L);
                 const float oh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
                 const float ol[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                const float2 th = make_float2(tv.x, tv.y), tl = make_float2(tv.z, tv.w);
 #pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    are[ch].add_prod(tv.x, tv.z, oh[ch], ol[ch]);
-                    aim[ch].add_prod(tv.y, tv.w, oh[ch], ol[ch]);
-                }
+                for (int ch = 0; ch < 8; ++ch)
+                    acc[ch].add_prod(th, tl, make_float2(oh[ch], oh[ch]), make_float2(ol[ch], ol[ch]));
             };
             if (nb == BS) {
 #pragma unroll
@@ -548,20 +557,15 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
                 for (int j = 0; j < nb; ++j) sample(j);
             }
 #pragma unroll
-            for (int ch = 0; ch < 8; ++ch) {
-                are[ch].renormalise();
-                aim[ch].renormalise();
-            }
+            for (int ch = 0; ch < 8; ++ch) acc[ch].renormalise();
         }
         __syncthreads(); // the next batch overwrites this buffer
     }
     if (!active) return;
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
-        double2 v = first ? make_double2(0.0, 0.0) : bsum[out + ch * g.L3];
-        v.x = are[ch].added_to(v.x);
-        v.y = aim[ch].added_to(v.y);
-        bsum[out + ch * g.L3] = v;
+        const double2 v = first ? make_double2(0.0, 0.0) : bsum[out + ch * g.L3];
+        bsum[out + ch * g.L3] = acc[ch].added_to(v);
     }
 }
 

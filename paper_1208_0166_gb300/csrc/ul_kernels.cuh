@@ -819,32 +819,28 @@ struct InsertionAcc<double> {
 // with the block length (kInsertionBlock) and not with the number of samples.
 constexpr int kInsertionBlock = 8;
 
+// The real and imaginary parts are the two lanes of paired FP32 instructions (FFMA2 / FADD2:
+// each lane rounded as the scalar operation).
 template <>
 struct InsertionAcc<float> {
-    float re = 0.f, re_c = 0.f, im = 0.f, im_c = 0.f; // Kahan sums of block partials
-    float bre = 0.f, bim = 0.f;                       // partial sums of the current block
-    static __device__ __forceinline__ void kahan(float& sum, float& comp, float v)
-    {
-        const float y = __fsub_rn(v, comp);
-        const float t = __fadd_rn(sum, y);
-        comp = __fsub_rn(__fsub_rn(t, sum), y);
-        sum = t;
-    }
+    float2 sum = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f); // Kahan sums of block partials
+    float2 blk = make_float2(0.f, 0.f);                               // partial sums of the current block
     __device__ __forceinline__ void add(Cx<float> T, float o)
     {
-        bre = __fmaf_rn(T.re, o, bre);
-        bim = __fmaf_rn(T.im, o, bim);
+        blk = __ffma2_rn(make_float2(T.re, T.im), make_float2(o, o), blk);
     }
     __device__ __forceinline__ void fold()
     {
-        kahan(re, re_c, bre);
-        kahan(im, im_c, bim);
-        bre = 0.f;
-        bim = 0.f;
+        const float2 y = __fadd2_rn(blk, make_float2(-comp.x, -comp.y));
+        const float2 t = __fadd2_rn(sum, y);
+        const float2 d = __fadd2_rn(t, make_float2(-sum.x, -sum.y));
+        comp = __fadd2_rn(d, make_float2(-y.x, -y.y));
+        sum = t;
+        blk = make_float2(0.f, 0.f);
     }
     // the compensated sum rounded once to FP32, then widened (one FP64-pipe conversion)
-    __device__ __forceinline__ double total_re() const { return static_cast<double>(__fsub_rn(re, re_c)); }
-    __device__ __forceinline__ double total_im() const { return static_cast<double>(__fsub_rn(im, im_c)); }
+    __device__ __forceinline__ double total_re() const { return static_cast<double>(__fsub_rn(sum.x, comp.x)); }
+    __device__ __forceinline__ double total_im() const { return static_cast<double>(__fsub_rn(sum.y, comp.y)); }
 };
 
 template <typename R>
