@@ -136,6 +136,14 @@ TRAFFIC = {
 }
 
 
+_T0 = time.monotonic()
+
+
+def _progress(msg):
+    """One line per finished stage on stderr (the result line goes to stdout)."""
+    print(f"bench: {time.monotonic() - _T0:8.1f} s  {msg}", file=sys.stderr, flush=True)
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     for f in ("ul_kernels.cuh", "ul_math.cuh", "ul_device.cuh"):
@@ -541,11 +549,12 @@ def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, op
 
     def step():
         ids = [b.submit(job_from(sp)) for sp in specs]
-        return b.run_to_completion(ids, passes_per_step=32)
+        return b.run_to_completion(ids, passes_per_step=32, timeout_s=300.0)
 
     for _ in range(warmup):
         step()
     stream.synchronize()
+    _progress("batch warm-up done")
     if dist:
         dist.barrier()
     u0, l0 = b.stats()["link_updates"], b.stats()["launches"]
@@ -558,12 +567,11 @@ def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, op
     stream.synchronize()
     ms = e0.elapsed_time(e1)
     st = b.stats()
-    slab_launches, graph_launches = b.counters()
+    slab_launches = b.counters()
     b.close()
     samples = sum(sp["n_sub"] * (sp["Nt"] // sp["slab_t"]) * sp["L"] ** 3 * sp["r_max"] for sp in specs) * steps
     return {"ms": ms, "updates": st["link_updates"] - u0, "launches": st["launches"] - l0, "samples": samples,
             "block_threads": st["block_threads"], "jobs": len(specs), "slab_level_launches": slab_launches,
-            "graph_launches": graph_launches,
             "C_r_first_job": [[z.real, z.imag] for z in res[min(res)]["corr"][:3]]}
 
 
@@ -578,6 +586,7 @@ def serve_result(lib, prec, n_jobs, rate_hz, rank, torch):
     srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
     srv.run(warm)
     srv.close()
+    _progress("serve warm-up done")
     reqs = serving_stream(n_jobs, rate_hz=rate_hz, seed=7 + rank)
     srv = Server(prec, 16 << 30, passes_per_tick=8, cuda_stream=stream.cuda_stream)
     results, summary = srv.run(reqs)
@@ -617,7 +626,7 @@ def run_batch(args):
             "dtype": "f64" if prec == lib.UL_FP64 else "f32 (FP64 accumulation)", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "jobs": r["jobs"], "block_threads": r["block_threads"],
                        "options": _options(args), "variant": args.batch_variant},
-            "slab_level_launches": r["slab_level_launches"], "graph_launches": r["graph_launches"],
+            "slab_level_launches": r["slab_level_launches"],
             "correlator_samples_per_s": r["samples"] * ws / t, "gpu_launches": r["launches"], "clocks": clk,
             "C_r_first_job": r["C_r_first_job"]}
     print(json.dumps(line), flush=True)
@@ -727,6 +736,7 @@ def run_ours(args):
     clocks.start()
     main = _run_gpu(args, prec, K, Wm, rank, ws, dist, torch, lib)
     clk = clocks.stop()
+    _progress("main leg done")
 
     from paper_1208_0166_gb300.replicas import aggregate
 
@@ -740,6 +750,7 @@ def run_ours(args):
     samples = SAMPLES_PER_STEP * K * ws / total_s
 
     peaks = probe_peaks(lib, None)
+    _progress("peak probes done")
     prec_name = "fp64" if prec == lib.UL_FP64 else "fp32"
     roofline = roofline_block(prec_name, main["sweep_ms"] / K, peaks, TRAFFIC.get((prec_name, _kernel_hash())))
 
@@ -758,6 +769,7 @@ def run_ours(args):
                    "roofline": roofline_block(other_name, o["sweep_ms"] / K, peaks,
                                               TRAFFIC.get((other_name, _kernel_hash()))),
                    "fp32_error_vs_fp64": fp32_error_vs_fp64(lib)}
+        _progress("compare leg and accuracy done")
 
     # the batched (configuration 3) and served (configuration 4) forms, FP32 links with FP64
     # accumulation, each timed on its own (one GPU only: replicas would repeat them)
@@ -767,7 +779,7 @@ def run_ours(args):
         batch = {"value": r["updates"] / (r["ms"] / 1e3), "unit": UNIT, "ms_per_step": r["ms"] / 2,
                  "steps": 2, "warmup": 1, "correlator_samples_per_s": r["samples"] / (r["ms"] / 1e3),
                  "gpu_launches": r["launches"], "block_threads": r["block_threads"],
-                 "slab_level_launches": r["slab_level_launches"], "graph_launches": r["graph_launches"],
+                 "slab_level_launches": r["slab_level_launches"],
                  "dtype": "f32 (FP64 accumulation)", "workload": BATCH_WORKLOAD,
                  "roofline_step": {"achieved": r["updates"] * 36 / (r["ms"] / 1e3) / 1e9, "unit": "GB/s",
                                    "bytes_per_update": 36, "peak_hbm": peaks["hbm_gbs"],
@@ -775,6 +787,7 @@ def run_ours(args):
                                    "peak_l2": peaks["l2_read_gbs"],
                                    "frac_l2": r["updates"] * 36 / (r["ms"] / 1e3) / 1e9 / peaks["l2_read_gbs"],
                                    "note": "whole batch step (every launch: updates, measurements, reductions)"}}
+        _progress("batch leg done")
     if not args.no_serve and ws == 1:
         r = serve_result(lib, lib.UL_FP32_ACC64, args.serve_jobs, args.serve_rate, rank, torch)
         serve = {**r, "dtype": "f32 (FP64 accumulation)"}
@@ -782,12 +795,14 @@ def run_ours(args):
         sat = serve_result(lib, lib.UL_FP32_ACC64, 64, 200.0, rank, torch)
         serve["saturated"] = {k: sat[k] for k in ("jobs_per_s", "p50_latency_s", "p99_latency_s", "jobs",
                                                   "link_updates_per_s", "max_resident", "workload")}
+        _progress("serve legs done")
 
     if rank != 0:
         return 0
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline_sample()
+        _progress("cpu baseline done")
     accuracy = compare["fp32_error_vs_fp64"]["summary"] if compare else None
     fp32_vs_fp64 = None
     if compare:

@@ -394,8 +394,11 @@ int ul_batch_submit(ul_batch* b, const ul_job* job, uint64_t* job_id);
 
 /* ul_batch_step — admit queued jobs that fit, then run up to max_passes lockstep passes
  * (with the measurements and final reductions they reach).  Work is enqueued on the
- * batch's stream; the call blocks only when the launch queue is full.  *n_active
- * (may be NULL) receives the number of queued plus resident jobs. */
+ * batch's stream; the call blocks only when the launch queue is full (or, the first time a
+ * shape reaches a slab-resident level with option "tune" on, while that shape's cluster
+ * sizes are timed).  *n_active (may be NULL) receives the number of queued plus resident
+ * jobs.  With the environment variable UL_BATCH_TRACE=1 every step prints its host stages
+ * (admission, cluster-size tuning, slab-resident level launches, retirement) on stderr. */
 int ul_batch_step(ul_batch* b, int max_passes, int* n_active);
 
 /* ul_batch_poll — *state = UL_JOB_QUEUED, UL_JOB_RUNNING or UL_JOB_DONE.  When done, out
@@ -433,10 +436,6 @@ int ul_batch_stats(ul_batch* b, uint64_t* link_updates, uint64_t* launches, int*
  *       that launch's CTAs fit one SM's shared memory (a level of larger slabs would hold
  *       whole SMs that the other shapes' passes cannot share); 0 runs every level in the
  *       lockstep passes.
- *   "graphs" (default 1): where every lattice of a lockstep group is at the start of a
- *       compound sweep with a step's passes of sweeps left, the step's passes are captured
- *       once into a CUDA graph (with each lattice's Metropolis pass base in device memory)
- *       and replayed every step; 0 launches every pass directly.
  *   "tune" (default 1): choose each shape's cluster size by timing every feasible size once
  *       on a scratch lattice (a cudaMalloc/cudaFree, the first time a shape is seen) and keep
  *       the choice in the tune cache, a JSON file ($UL_TUNE_CACHE, else $XDG_CACHE_HOME or
@@ -452,9 +451,8 @@ int ul_batch_set_option(ul_batch* b, const char* key, double value);
  * may be NULL. */
 int ul_batch_plan(ul_batch* b, int L, int Nt, int slab_t, int* cluster, uint64_t* slab_launches);
 
-/* ul_batch_counters — slab-resident level launches and replayed graphs of sweep passes so far
- * (either output may be NULL). */
-int ul_batch_counters(ul_batch* b, uint64_t* slab_level_launches, uint64_t* graph_launches);
+/* ul_batch_counters — slab-resident level launches so far (the output may be NULL). */
+int ul_batch_counters(ul_batch* b, uint64_t* slab_level_launches);
 
 /* ul_batch_free — wait for the batch's streams and release everything (NULL accepted). */
 int ul_batch_free(ul_batch* b);

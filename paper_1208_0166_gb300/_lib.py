@@ -71,7 +71,7 @@ SIGNATURES = [
     ("ul_batch_poll", _I, [_P, _U64, _DP, ctypes.POINTER(_I)]),
     ("ul_batch_set_option", _I, [_P, ctypes.c_char_p, _D]),
     ("ul_batch_plan", _I, [_P, _I, _I, _I, ctypes.POINTER(_I), _U64P]),
-    ("ul_batch_counters", _I, [_P, _U64P, _U64P]),
+    ("ul_batch_counters", _I, [_P, _U64P]),
     ("ul_batch_job_info", _I, [_P, _U64, ctypes.POINTER(_I), _U64P, _U64P]),
     ("ul_batch_stats", _I, [_P, _U64P, _U64P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t)]),
     ("ul_batch_free", _I, [_P]),
@@ -321,10 +321,10 @@ class Batch:
         return c.value, n.value
 
     def counters(self):
-        """(slab-resident level launches, replayed graphs of sweep passes) so far."""
-        a, g = ctypes.c_uint64(), ctypes.c_uint64()
-        self._check(load().ul_batch_counters(self._b, ctypes.byref(a), ctypes.byref(g)))
-        return a.value, g.value
+        """Slab-resident level launches so far."""
+        a = ctypes.c_uint64()
+        self._check(load().ul_batch_counters(self._b, ctypes.byref(a)))
+        return a.value
 
     def job_info(self, job_id: int):
         """(state, passes_done, passes_total) of a job not yet collected."""
@@ -337,10 +337,17 @@ class Batch:
         self._check(load().ul_batch_stats(self._b, ctypes.byref(u), ctypes.byref(l), ctypes.byref(t), ctypes.byref(m)))
         return {"link_updates": u.value, "launches": l.value, "block_threads": t.value, "bytes_in_use": m.value}
 
-    def run_to_completion(self, job_ids, passes_per_step: int = 64):
+    def run_to_completion(self, job_ids, passes_per_step: int = 64, timeout_s: float | None = None):
+        """Step the batch until every job in job_ids has a result; TimeoutError after
+        timeout_s seconds of wall-clock time (no limit when None)."""
+        import time
+
+        t0 = time.perf_counter()
         results = {}
         pending = set(job_ids)
         while pending:
+            if timeout_s is not None and time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError(f"batch: {len(pending)} jobs unfinished after {timeout_s} s")
             self.step(passes_per_step)
             for j in list(pending):
                 r = self.poll(j)

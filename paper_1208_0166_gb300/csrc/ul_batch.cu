@@ -37,6 +37,25 @@
 #include "ul_device.cuh"
 #include "ul_internal.h"
 
+// Optional trace of the engine's host steps on stderr (environment variable
+// UL_BATCH_TRACE=1), to locate a call that does not return.
+static bool ub_trace_on()
+{
+    static const bool on = [] {
+        const char* v = std::getenv("UL_BATCH_TRACE");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
+#define UB_TRACE(...)                                      \
+    do {                                                   \
+        if (ub_trace_on()) {                               \
+            std::fprintf(stderr, "ul_batch: " __VA_ARGS__); \
+            std::fputc('\n', stderr);                      \
+            std::fflush(stderr);                           \
+        }                                                  \
+    } while (0)
+
 namespace {
 
 size_t round256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
@@ -105,7 +124,6 @@ struct Job {
     double* dout = nullptr;
     double* plaq_partials = nullptr;
     unsigned long long* accepted = nullptr;
-    unsigned long long* d_pass = nullptr; // Metropolis pass base of replayed graphs
     long pos = 0, sweep_passes = 0, total_passes = 0;
     uint64_t metro_pass = 0, proposed = 0;
     int state = kQueued;
@@ -115,7 +133,7 @@ struct Job {
 };
 
 struct Layout {
-    size_t theta, cs, asum, partials, dout, plaq, acc, pass, total;
+    size_t theta, cs, asum, partials, dout, plaq, acc, total;
 };
 
 Layout layout_of(const Job& j, size_t rs)
@@ -136,8 +154,6 @@ Layout layout_of(const Job& j, size_t rs)
     l.plaq = o;
     o += round256(static_cast<size_t>(ul::plaquette_partials(j.g)) * sizeof(double));
     l.acc = o;
-    o += round256(sizeof(unsigned long long));
-    l.pass = o;
     o += round256(sizeof(unsigned long long));
     l.total = o;
     return l;
@@ -307,14 +323,6 @@ struct ul_batch {
     };
     std::map<std::string, ShapeTune> tunes;
     size_t group_bytes = 64ull << 20; // option "group_mb": links of one lockstep group
-    bool use_graphs = true;           // option "graphs": replay captured sweep passes
-    struct GroupGraph {
-        std::vector<uint64_t> ids;
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-    };
-    std::map<std::string, GroupGraph> group_graphs;
-    uint64_t graph_launches = 0;
     uint64_t link_updates = 0, launches = 0, passes = 0, slab_launches = 0;
     std::string err;
 };
@@ -395,7 +403,6 @@ int admit(ul_batch* b)
         j->dout = reinterpret_cast<double*>(p + l.dout);
         j->plaq_partials = reinterpret_cast<double*>(p + l.plaq);
         j->accepted = reinterpret_cast<unsigned long long*>(p + l.acc);
-        j->d_pass = reinterpret_cast<unsigned long long*>(p + l.pass);
         UB_CK(b, cudaMemsetAsync(j->asum, 0, static_cast<size_t>(j->S) * j->spec.r_max * j->g.L3 * sizeof(double2),
                                  b->stream));
         UB_CK(b, cudaMemsetAsync(j->accepted, 0, sizeof(unsigned long long), b->stream));
@@ -500,10 +507,12 @@ int slab_level_plan(ul_batch* b, const ul::Geo& g, int slab_t, int* cluster, int
     if (e == cudaSuccess) e = cudaMemsetAsync(asum, 0, bytes_asum + 256, st);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    UB_TRACE("slab tuning L=%d Nt=%d slab_t=%d", g.L, g.Nt, slab_t);
     for (int c = 1; c <= 16 && e == cudaSuccess; ++c) {
         int cc = 0, tt = 0;
         e = ul::slab_plan<R>(g, slab_t, c, &cc, &tt);
         if (e != cudaSuccess || cc != c) continue;
+        UB_TRACE("slab tuning trial cluster=%d threads=%d", c, tt);
         ul::SlabArgs a{};
         a.u.slab_t = slab_t;
         if (g.Nt <= 64)
@@ -539,6 +548,7 @@ int slab_level_plan(ul_batch* b, const ul::Geo& g, int slab_t, int* cluster, int
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    UB_TRACE("slab tuning trials done, freeing scratch");
     const cudaError_t ef = cudaFree(mem);
     if (e == cudaSuccess) e = ef;
     if (e != cudaSuccess) return bcuda(b, e, "slab cluster tuning");
@@ -623,6 +633,8 @@ int offload_levels(ul_batch* b)
                 sj.n_or = j->spec.sub_or;
                 sj.r_max = j->spec.r_max;
             }
+            UB_TRACE("slab level launch L=%d jobs=%d cluster=%d threads=%d stream=%d", g.L, t.njobs, cluster, threads,
+                     si % ul_batch::kLevelStreams);
             cudaError_t e = b->precision == UL_FP64 ? ul::launch_slab_jobs<double>(g, a, t, threads, lst)
                                                     : ul::launch_slab_jobs<float>(g, a, t, threads, lst);
             if (e != cudaSuccess) return bcuda(b, e, "slab-resident level launch");
@@ -794,7 +806,6 @@ int group_pass(ul_batch* b, const std::vector<Job*>& group, bool* did_work)
         u.theta = j->theta;
         u.cs = j->cs;
         u.accepted = j->accepted;
-        u.pass_base = nullptr;
         u.L = j->g.L;
         u.Nt = j->g.Nt;
         u.V = j->g.V;
@@ -880,136 +891,6 @@ int group_pass(ul_batch* b, const std::vector<Job*>& group, bool* did_work)
     return UL_OK;
 }
 
-__global__ void set_pass_bases_kernel(const __grid_constant__ ul::PassBaseTable t)
-{
-    const int k = static_cast<int>(threadIdx.x);
-    if (k < t.n) *t.ptr[k] = t.val[k];
-}
-
-void destroy_graph(ul_batch::GroupGraph& gg)
-{
-    if (gg.exec) cudaGraphExecDestroy(gg.exec);
-    if (gg.graph) cudaGraphDestroy(gg.graph);
-    gg.exec = nullptr;
-    gg.graph = nullptr;
-}
-
-// Graphs whose lattices are no longer all running are dropped (their memory may be reused).
-void evict_graphs(ul_batch* b)
-{
-    for (auto it = b->group_graphs.begin(); it != b->group_graphs.end();) {
-        bool live = true;
-        for (uint64_t id : it->second.ids) {
-            auto jt = b->jobs.find(id);
-            live = live && jt != b->jobs.end() && jt->second->state == kRunning;
-        }
-        if (live) {
-            ++it;
-        } else {
-            destroy_graph(it->second);
-            it = b->group_graphs.erase(it);
-        }
-    }
-}
-
-// Sweep passes of a group as a replayed CUDA graph: where every lattice of the group is
-// running, at the start of a compound sweep of one composition, with at least P sweep
-// passes left (P = max_passes rounded down to whole compound sweeps) and the shape's block
-// size chosen, the group's P passes (8 class launches each) are captured once per group and
-// replayed every step, after a one-thread-per-lattice kernel that sets each lattice's
-// Metropolis pass base in device memory (the captured launches hold pass offsets).  The
-// same updates as P calls of group_pass.  *done = false where the group does not qualify.
-int group_graph_step(ul_batch* b, const std::vector<Job*>& group, int max_passes, bool* done)
-{
-    *done = false;
-    if (!b->use_graphs || group.empty()) return UL_OK;
-    const Job* j0 = group[0];
-    const int per = j0->spec.sweep_metro + j0->spec.sweep_or;
-    if (per < 1) return UL_OK;
-    const int P = (max_passes / per) * per;
-    if (P < per) return UL_OK;
-    for (const Job* j : group)
-        if (j->state != kRunning || j->spec.sweep_metro != j0->spec.sweep_metro || j->spec.sweep_or != j0->spec.sweep_or ||
-            j->pos % per != 0 || j->sweep_passes - j->pos < P)
-            return UL_OK;
-    const ul::Geo g = j0->g;
-    bool timing = false;
-    const int threads = lockstep_threads(b, g, &timing);
-    if (timing || !threads) return UL_OK;
-    cudaStream_t st = b->lock_streams[j0->sidx];
-    std::string key = std::to_string(threads) + "/" + std::to_string(P) + "/" + std::to_string(j0->spec.sweep_metro) +
-                      "/" + std::to_string(per);
-    for (const Job* j : group) key += "/" + std::to_string(j->id);
-    auto it = b->group_graphs.find(key);
-    if (it == b->group_graphs.end()) {
-        ul_batch::GroupGraph gg;
-        for (const Job* j : group) gg.ids.push_back(j->id);
-        const bool pdl = b->precision == UL_FP32_ACC64;
-        UB_CK(b, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        for (int k = 0; k < P && e == cudaSuccess; ++k) {
-            const bool metro = (k % per) < j0->spec.sweep_metro;
-            const uint64_t offset = static_cast<uint64_t>(k / per) * j0->spec.sweep_metro + static_cast<uint64_t>(k % per);
-            ul::BatchUpdateTable t{};
-            for (const Job* j : group) {
-                ul::BatchUpdateJob& u = t.job[t.njobs++];
-                u.theta = j->theta;
-                u.cs = j->cs;
-                u.accepted = j->accepted;
-                u.pass_base = j->d_pass;
-                u.L = j->g.L;
-                u.Nt = j->g.Nt;
-                u.V = j->g.V;
-                u.Vh = j->g.Vh;
-                u.L3 = j->g.L3;
-                u.metro = metro ? 1 : 0;
-                u.slab_t = 0;
-                u.frozen_mask = 0;
-                u.pass = metro ? offset : 0;
-                u.seed = j->spec.seed;
-                u.beta = j->spec.beta;
-                u.width = j->spec.metro_width;
-            }
-            const int bx = static_cast<int>((g.Vh + threads - 1) / threads);
-            for (int mu = 0; mu < 4 && e == cudaSuccess; ++mu)
-                for (int par = 0; par < 2 && e == cudaSuccess; ++par)
-                    e = b->precision == UL_FP64 ? ul::launch_group_update<double>(t, g.L, bx, threads, mu, par, st, pdl)
-                                                : ul::launch_group_update<float>(t, g.L, bx, threads, mu, par, st, pdl);
-        }
-        cudaGraph_t graph = nullptr;
-        const cudaError_t e_end = cudaStreamEndCapture(st, &graph);
-        if (e == cudaSuccess) e = e_end;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&gg.exec, graph, 0);
-        gg.graph = graph;
-        if (e != cudaSuccess) {
-            destroy_graph(gg);
-            return bcuda(b, e, "lockstep graph capture");
-        }
-        it = b->group_graphs.emplace(key, gg).first;
-    }
-    ul::PassBaseTable pb{};
-    for (const Job* j : group) {
-        pb.ptr[pb.n] = j->d_pass;
-        pb.val[pb.n] = j->metro_pass;
-        ++pb.n;
-    }
-    set_pass_bases_kernel<<<1, 64, 0, st>>>(pb);
-    UB_CK(b, cudaGetLastError());
-    UB_CK(b, cudaGraphLaunch(it->second.exec, st));
-    b->launches += static_cast<uint64_t>(P) * 8 + 1;
-    b->graph_launches += 1;
-    b->passes += static_cast<uint64_t>(P);
-    const uint64_t metro_passes = static_cast<uint64_t>(P / per) * j0->spec.sweep_metro;
-    for (Job* j : group) {
-        const uint64_t n_up = updatable(*j, 0);
-        b->link_updates += static_cast<uint64_t>(P) * n_up;
-        j->metro_pass += metro_passes;
-        j->proposed += metro_passes * n_up;
-        j->pos += P;
-    }
-    *done = true;
-    return UL_OK;
-}
 
 } // namespace
 
@@ -1117,22 +998,15 @@ int ul_batch_step(ul_batch* b, int max_passes, int* n_active)
 {
     if (!b) return UL_EINVAL;
     if (max_passes < 0) return bfail(b, UL_EINVAL, "ul_batch_step: max_passes must be >= 0");
+    UB_TRACE("step: %zu queued, %zu resident", b->queue.size(), b->resident.size());
     if (max_passes > 0) {
         int rc = admit(b);
         if (rc) return rc;
+        UB_TRACE("admitted: %zu resident", b->resident.size());
         rc = offload_levels(b);
         if (rc) return rc;
         // each group runs its passes back to back, so that its links stay in L2
-        evict_graphs(b);
         for (const std::vector<Job*>& group : lockstep_groups(b)) {
-            bool replayed = false;
-            rc = group_graph_step(b, group, max_passes, &replayed);
-            if (rc) return rc;
-            if (replayed) {
-                rc = offload_levels(b);
-                if (rc) return rc;
-                continue;
-            }
             for (int it = 0; it < max_passes; ++it) {
                 bool work = false;
                 rc = group_pass(b, group, &work);
@@ -1146,8 +1020,10 @@ int ul_batch_step(ul_batch* b, int max_passes, int* n_active)
         rc = offload_levels(b);
         if (rc) return rc;
     }
+    UB_TRACE("step: retire");
     retire_finished(b);
     collect_tuning(b);
+    UB_TRACE("step: done");
     if (n_active) *n_active = static_cast<int>(b->queue.size() + b->resident.size());
     return UL_OK;
 }
@@ -1211,11 +1087,10 @@ int ul_batch_plan(ul_batch* b, int L, int Nt, int slab_t, int* cluster, uint64_t
     return UL_OK;
 }
 
-int ul_batch_counters(ul_batch* b, uint64_t* slab_level_launches, uint64_t* graph_launches)
+int ul_batch_counters(ul_batch* b, uint64_t* slab_level_launches)
 {
     if (!b) return UL_EINVAL;
     if (slab_level_launches) *slab_level_launches = b->slab_launches;
-    if (graph_launches) *graph_launches = b->graph_launches;
     return UL_OK;
 }
 
@@ -1242,7 +1117,6 @@ int ul_batch_free(ul_batch* b)
             cudaEventDestroy(smp.a);
             cudaEventDestroy(smp.b);
         }
-    for (auto& kv : b->group_graphs) destroy_graph(kv.second);
     for (auto& kv : b->jobs) destroy_job(kv.second);
     cudaFree(b->base);
     if (b->ev_admit) cudaEventDestroy(b->ev_admit);
@@ -1269,11 +1143,6 @@ int ul_batch_set_option(ul_batch* b, const char* key, double v)
     if (!std::strcmp(key, "slab_levels")) {
         if (v != 0.0 && v != 1.0 && v != 2.0) return bfail(b, UL_EINVAL, "ul_batch_set_option: slab_levels must be 0, 1 or 2");
         b->slab_levels = static_cast<int>(v);
-        return UL_OK;
-    }
-    if (!std::strcmp(key, "graphs")) {
-        if (v != 0.0 && v != 1.0) return bfail(b, UL_EINVAL, "ul_batch_set_option: graphs must be 0 or 1");
-        b->use_graphs = v != 0.0;
         return UL_OK;
     }
     if (!std::strcmp(key, "tune")) {

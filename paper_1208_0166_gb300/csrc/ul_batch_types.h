@@ -75,19 +75,11 @@ struct BatchUpdateJob {
     void* theta;
     void* cs;
     unsigned long long* accepted;
-    const unsigned long long* pass_base; // null, or a device counter added to pass (replayed graphs)
     int L, Nt, V, Vh, L3;
     int metro, slab_t;
     unsigned long long frozen_mask;
     uint64_t pass, seed;
     double beta, width;
-};
-
-// Device counters set before a replayed graph of lockstep passes: *ptr[k] = val[k].
-struct PassBaseTable {
-    int n;
-    unsigned long long* ptr[kMaxBatchJobs];
-    unsigned long long val[kMaxBatchJobs];
 };
 
 struct BatchUpdateTable {

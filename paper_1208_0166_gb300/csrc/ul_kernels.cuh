@@ -1046,7 +1046,7 @@ __device__ __forceinline__ void group_update(const BatchUpdateTable& t, int mu, 
     a.slab_t = J.slab_t;
     a.frozen_mask = J.frozen_mask;
     a.pass = J.pass;
-    a.pass_base = J.pass_base;
+    a.pass_base = nullptr;
     a.seed = J.seed;
     a.beta = J.beta;
     a.width = J.width;

@@ -179,27 +179,3 @@ def test_lockstep_groups_do_not_change_results(prec, tmp_path, monkeypatch):
     for spec, a, b in zip(specs, small, large):
         assert np.array_equal(a["corr"], b["corr"]), spec
         assert a["plaquette"] == b["plaquette"] and a["accept"] == b["accept"], spec
-
-
-@pytest.mark.parametrize("prec", [_lib.UL_FP64, _lib.UL_FP32_ACC64])
-def test_replayed_sweep_graphs_equal_direct_passes(prec, tmp_path, monkeypatch):
-    """Aligned lattices of one shape: their sweep passes replayed from captured graphs (once
-    the block size is tuned) give the bits of direct launches."""
-    monkeypatch.setenv("UL_TUNE_CACHE", str(tmp_path / "tune.json"))
-    specs = [(8, 8, 1.0, 51 + k, 9, 2, 3, 3) for k in range(3)] + [(6, 4, 0.97, 61 + k, 9, 2, 2, 2) for k in range(2)]
-
-    def run(graphs):
-        b = _lib.Batch(prec, 1 << 30)
-        b.set_option("graphs", graphs)
-        ids = [b.submit(_job(s)) for s in specs]
-        res = b.run_to_completion(ids, passes_per_step=8)
-        c = b.counters()
-        b.close()
-        return [res[i] for i in ids], c
-
-    g, (_, n_graphs) = run(1)
-    d, (_, n0) = run(0)
-    assert n_graphs > 0 and n0 == 0
-    for spec, a, b in zip(specs, g, d):
-        assert np.array_equal(a["corr"], b["corr"]), spec
-        assert a["plaquette"] == b["plaquette"] and a["accept"] == b["accept"], spec

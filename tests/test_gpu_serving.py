@@ -74,3 +74,16 @@ def test_request_arriving_mid_run_is_admitted_and_overlaps(prec):
         alone = _alone(prec, spec)
         assert np.array_equal(alone["corr"], srv.done[idx]["corr"]), idx
         assert alone["plaquette"] == srv.done[idx]["plaquette"]
+
+
+def test_mixed_size_stream_completes():
+    """A Poisson stream of 24 requests of every size of the serving workload (L = 12 ... 32,
+    slab-resident levels for the small shapes beside the lockstep passes of the others)
+    runs to completion inside the server's time limit, every request answered once."""
+    reqs = serving_stream(24, rate_hz=40.0, seed=11, n_sweeps=20, n_sub_range=(8, 24))
+    srv = Server(_lib.UL_FP32_ACC64, 8 << 30, passes_per_tick=8)
+    results, summary = srv.run(reqs, timeout_s=240.0)
+    srv.close()
+    assert summary["jobs"] == len(reqs) and sorted(results) == list(range(len(reqs)))
+    for r in results.values():
+        assert np.all(np.isfinite(np.asarray(r["corr"])))
