@@ -128,11 +128,13 @@ def roofline_block(prec_name, sweep_ms_per_step, peaks, traffic=None):
 # hash of the kernel sources it was taken on (null once the sources have changed).
 TRAFFIC = {
     # mean DRAM bytes (read + write) of two captured launches of the update kernel at 24^4
-    # (launches 8 and 9 of the profiled step, Metropolis mu = 3 and overrelaxation mu = 0;
-    # ncu replays with cold caches, while in the bench the lattice is L2-resident):
+    # (launches 8 and 9 of the profiled step, Metropolis mu = 3 and overrelaxation mu = 0),
+    # captured with --cache-control none, so that the lattice stays in L2 as in the bench
+    # (with ncu's default cache flush before each replay the same launches read 22.6 / 20.0 MB
+    # in FP64 and 11.3 / 10.0 MB in FP32):
     # profiles/update_class_f64_24x24.md, profiles/update_class_f32_24x24.md
-    ("fp64", "b522978fea71983f"): (22629120 + 19974400) / 2,
-    ("fp32", "b522978fea71983f"): (11328256 + 10000384) / 2,
+    ("fp64", "e300a7837b27be12"): (256 + 1024) / 2,
+    ("fp32", "e300a7837b27be12"): (256 + 256) / 2,
 }
 
 
@@ -541,6 +543,8 @@ def batch_result(lib, prec, steps, warmup, rank, dist, torch, seed_base=1000, op
         specs = [dict(sp, n_sub=1) for sp in specs]
     elif variant == "levels":    # the levels alone (no sweeps before them)
         specs = [dict(sp, n_sweeps=0) for sp in specs]
+    elif variant == "profile":   # 2 sweeps and one sub-sample each: few launches, for profiler captures
+        specs = [dict(sp, n_sweeps=2, n_sub=1) for sp in specs]
     stream = torch.cuda.Stream()
     b = lib.Batch(prec, 8 << 30, stream.cuda_stream)
     for k, v in (options or {}).items():
@@ -848,9 +852,10 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep-scaling"],
                     help="single: the 24^4 configuration step (default); batch: 32 uneven lattices; "
                          "serve: Poisson stream through the continuous-batching loop")
-    ap.add_argument("--batch-variant", default="full", choices=["full", "sweeps", "levels"],
+    ap.add_argument("--batch-variant", default="full", choices=["full", "sweeps", "levels", "profile"],
                     help="--workload batch: the whole program, its sweeps alone (one sub-sample per level) "
-                         "or its levels alone (no sweeps)")
+                         "or its levels alone (no sweeps); profile: 2 sweeps and one sub-sample per job "
+                         "(few launches, for profiler captures)")
     ap.add_argument("--serve-jobs", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--estimator", default="paper", choices=["paper", "sym", "two-level"],
