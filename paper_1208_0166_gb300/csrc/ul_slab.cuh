@@ -39,28 +39,33 @@ __host__ __device__ __forceinline__ int slab_angle_slots(int tau) { return tau +
 // Phase arrays of a CTA and of the CTAs holding the z planes below and above it.  A site
 // is addressed by its local lexicographic index li = x + L (y + L zl); after a step in z,
 // li < 0 or li >= P addresses the neighbouring CTA (its local index li + P or li - P).
-template <typename R, int LC>
+// TC, NZC: the slab thickness and the z planes per CTA when known at compile time (0: taken
+// from the launch), so that every shared-memory offset of a staple folds to a constant.
+template <typename R, int LC, int TC = 0, int NZC = 0>
 struct SlabLinks {
     cs_t<R>* own; // this CTA's phases (shared memory)
     cs_t<R>* dn;  // the CTA below (distributed shared memory)
     cs_t<R>* up;  // the CTA above
-    int P, Ph, tau;
+    int P_rt, Ph_rt, tau_rt;
 
+    __device__ __forceinline__ int P() const { return (LC && NZC) ? LC * LC * NZC : P_rt; }
+    __device__ __forceinline__ int Ph() const { return (LC && NZC) ? LC * LC * NZC / 2 : Ph_rt; }
+    __device__ __forceinline__ int tau() const { return TC ? TC : tau_rt; }
     __device__ __forceinline__ int slot(int dir, int tl) const
     {
-        return dir == 0 ? tl : tau + (dir - 1) * (tau + 1) + tl;
+        return dir == 0 ? tl : tau() + (dir - 1) * (tau() + 1) + tl;
     }
     // ZS: the z step (-1, 0, +1) taken to reach the site.
     template <int ZS>
     __device__ __forceinline__ Cx<R> ld(int dir, int tl, int li, int par) const
     {
-        const int base = (slot(dir, tl) * 2 + par) * Ph;
+        const int base = (slot(dir, tl) * 2 + par) * Ph();
         cs_t<R> v;
         if constexpr (ZS > 0) {
-            if (li >= P) v = up[base + ((li - P) >> 1)];
+            if (li >= P()) v = up[base + ((li - P()) >> 1)];
             else v = own[base + (li >> 1)];
         } else if constexpr (ZS < 0) {
-            if (li < 0) v = dn[base + ((li + P) >> 1)];
+            if (li < 0) v = dn[base + ((li + P()) >> 1)];
             else v = own[base + (li >> 1)];
         } else {
             v = own[base + (li >> 1)];
@@ -93,8 +98,8 @@ struct SlabSteps {
     }
 };
 
-template <typename R, int LC, int MU, int NU>
-__device__ __forceinline__ void slab_staple_term(Cx<R>& A, const SlabLinks<R, LC>& S, const SlabSteps& st, int tl,
+template <typename R, int LC, int TC, int NZC, int MU, int NU>
+__device__ __forceinline__ void slab_staple_term(Cx<R>& A, const SlabLinks<R, LC, TC, NZC>& S, const SlabSteps& st, int tl,
                                                  int li, int p)
 {
     constexpr int ZM = MU == 3 ? 1 : 0;
@@ -122,11 +127,11 @@ __device__ __forceinline__ int slab_global_offset(const Geo& g, int dir, int x, 
 
 // Class (MU, p) of this CTA: thread tid updates the links at half index hl = tid (+ nthr ...)
 // on every updatable slice.  Returns the number of Metropolis acceptances.
-template <typename R, int LC, int MU>
-__device__ __forceinline__ int slab_class(const SlabLinks<R, LC>& S, R* th_own, const Geo& g, int L, int z0, int t0,
-                                          int p, bool metro, uint64_t pass, const UpdateArgs& a)
+template <typename R, int LC, int TC, int NZC, int MU>
+__device__ __forceinline__ int slab_class(const SlabLinks<R, LC, TC, NZC>& S, R* th_own, const Geo& g, int L, int z0,
+                                          int t0, int p, bool metro, uint64_t pass, const UpdateArgs& a)
 {
-    const int Lh = L / 2, tau = S.tau, Ph = S.Ph;
+    const int Lh = L / 2, tau = S.tau(), Ph = S.Ph();
     const int nsl = MU == 0 ? tau : tau - 1;
     int accepted = 0;
     for (int hl = static_cast<int>(threadIdx.x); hl < Ph; hl += static_cast<int>(blockDim.x)) {
@@ -140,10 +145,10 @@ __device__ __forceinline__ int slab_class(const SlabLinks<R, LC>& S, R* th_own, 
             const int li = x + L * (y + L * zl);
             const SlabSteps st(x, y, L);
             Cx<R> A{R(0), R(0)};
-            if (MU != 0) slab_staple_term<R, LC, MU, 0>(A, S, st, tl, li, p);
-            if (MU != 1) slab_staple_term<R, LC, MU, 1>(A, S, st, tl, li, p);
-            if (MU != 2) slab_staple_term<R, LC, MU, 2>(A, S, st, tl, li, p);
-            if (MU != 3) slab_staple_term<R, LC, MU, 3>(A, S, st, tl, li, p);
+            if (MU != 0) slab_staple_term<R, LC, TC, NZC, MU, 0>(A, S, st, tl, li, p);
+            if (MU != 1) slab_staple_term<R, LC, TC, NZC, MU, 1>(A, S, st, tl, li, p);
+            if (MU != 2) slab_staple_term<R, LC, TC, NZC, MU, 2>(A, S, st, tl, li, p);
+            if (MU != 3) slab_staple_term<R, LC, TC, NZC, MU, 3>(A, S, st, tl, li, p);
             const int ph_idx = (S.slot(MU, tl) * 2 + p) * Ph + hl;
             const int th_slot = MU == 0 ? tl : tau + (MU - 1) * (tau - 1) + tl - 1;
             const int th_idx = (th_slot * 2 + p) * Ph + hl;
@@ -171,11 +176,11 @@ __device__ __forceinline__ int slab_class(const SlabLinks<R, LC>& S, R* th_own, 
 
 // Measurement of one sub-sample for this CTA's sites (same products, order and stores as
 // measure_store_site).
-template <typename R, int LC>
-__device__ __forceinline__ void slab_measure(const SlabLinks<R, LC>& S, const Geo& g, int L, int z0, int t0, int s,
+template <typename R, int LC, int TC, int NZC>
+__device__ __forceinline__ void slab_measure(const SlabLinks<R, LC, TC, NZC>& S, const Geo& g, int L, int z0, int t0, int s,
                                              int slot, const SlabArgs& a)
 {
-    const int tau = S.tau, P = S.P;
+    const int tau = S.tau(), P = S.P();
     const int nS = g.Nt / tau, SL3 = nS * g.L3;
     for (int q = static_cast<int>(threadIdx.x); q < P; q += static_cast<int>(blockDim.x)) {
         const int x = q % L;
@@ -241,7 +246,7 @@ __device__ __forceinline__ void slab_measure(const SlabLinks<R, LC>& S, const Ge
     }
 }
 
-template <typename R, int LC>
+template <typename R, int LC, int TC = 0, int NZC = 0>
 __device__ __forceinline__ void slab_body(const Geo& g, R* __restrict__ theta, cs_t<R>* __restrict__ cs,
                                           const SlabArgs& a)
 {
@@ -250,8 +255,8 @@ __device__ __forceinline__ void slab_body(const Geo& g, R* __restrict__ theta, c
     const int rank = static_cast<int>(cl.block_rank());
     const int ncl = a.cluster;
     const int s = static_cast<int>(blockIdx.x) / ncl;
-    const int tau = a.u.slab_t;
-    const int L = LC ? LC : g.L, Lh = L / 2, nz = a.nz;
+    const int tau = TC ? TC : a.u.slab_t;
+    const int L = LC ? LC : g.L, Lh = L / 2, nz = NZC ? NZC : a.nz;
     const int P = L * L * nz, Ph = P / 2;
     const int z0 = rank * nz, t0 = s * tau;
     const int NS = slab_phase_slots(tau), NT = slab_angle_slots(tau);
@@ -261,13 +266,13 @@ __device__ __forceinline__ void slab_body(const Geo& g, R* __restrict__ theta, c
     cs_t<R>* ph = reinterpret_cast<cs_t<R>*>(slab_smem);
     R* th = reinterpret_cast<R*>(ph + NS * P);
 
-    SlabLinks<R, LC> S;
+    SlabLinks<R, LC, TC, NZC> S;
     S.own = ph;
     S.dn = cl.map_shared_rank(ph, (rank + ncl - 1) % ncl);
     S.up = cl.map_shared_rank(ph, (rank + 1) % ncl);
-    S.P = P;
-    S.Ph = Ph;
-    S.tau = tau;
+    S.P_rt = P;
+    S.Ph_rt = Ph;
+    S.tau_rt = tau;
 
     // entry e of the phase (angle) array -> direction, slice and site
     auto decode = [&](int e, bool angle, int& dir, int& tl, int& par, int& x, int& y, int& zl) {
@@ -314,10 +319,10 @@ __device__ __forceinline__ void slab_body(const Geo& g, R* __restrict__ theta, c
                 for (int p = 0; p < 2; ++p) {
                     int accepted;
                     switch (mu) {
-                    case 0: accepted = slab_class<R, LC, 0>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
-                    case 1: accepted = slab_class<R, LC, 1>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
-                    case 2: accepted = slab_class<R, LC, 2>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
-                    default: accepted = slab_class<R, LC, 3>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
+                    case 0: accepted = slab_class<R, LC, TC, NZC, 0>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
+                    case 1: accepted = slab_class<R, LC, TC, NZC, 1>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
+                    case 2: accepted = slab_class<R, LC, TC, NZC, 2>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
+                    default: accepted = slab_class<R, LC, TC, NZC, 3>(S, th, g, L, z0, t0, p, metro, pass, a.u); break;
                     }
                     if (metro) {
 #pragma unroll
@@ -331,7 +336,7 @@ __device__ __forceinline__ void slab_body(const Geo& g, R* __restrict__ theta, c
             if (metro) pass += 1;
         }
         if (!a.skip_measure) {
-            slab_measure<R, LC>(S, g, L, z0, t0, s, a.slot0 + unit, a);
+            slab_measure<R, LC, TC, NZC>(S, g, L, z0, t0, s, a.slot0 + unit, a);
             cl.sync(); // the next updates may change links that other CTAs just measured
         }
     }
@@ -345,11 +350,13 @@ __device__ __forceinline__ void slab_body(const Geo& g, R* __restrict__ theta, c
     }
 }
 
-template <typename R, int LC>
-__global__ void __launch_bounds__(1024, 1) slab_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs,
-                                                        SlabArgs a)
+// The block has one thread per half-site of a CTA's planes (rounded up to warps): the
+// compile-time shape bounds it exactly.
+template <typename R, int LC, int TC = 0, int NZC = 0>
+__global__ void __launch_bounds__((LC && NZC) ? (LC * LC * NZC / 2 + 31) / 32 * 32 : 1024, 1)
+    slab_kernel(Geo g, R* __restrict__ theta, cs_t<R>* __restrict__ cs, SlabArgs a)
 {
-    slab_body<R, LC>(g, theta, cs, a);
+    slab_body<R, LC, TC, NZC>(g, theta, cs, a);
 }
 
 // The same slab-resident level for several lattices of one shape in one launch: the grid's
@@ -370,10 +377,14 @@ __global__ void __launch_bounds__(1024, 1) slab_jobs_kernel(Geo g, SlabArgs a, c
     slab_body<R, LC>(g, static_cast<R*>(j.theta), static_cast<cs_t<R>*>(j.cs), b);
 }
 
-// Kernel instances for extent L (compile-time extents for the common sizes).
+// Kernel instances for extent L (compile-time extents for the common sizes; for FP32 links
+// at L = 24 with slabs of 2 slices and 3 z planes per CTA, the benchmark's shape, also the
+// slab thickness and the planes per CTA).
 template <typename R>
-auto slab_kernel_for(int L)
+auto slab_kernel_for(int L, int tau = 0, int nz = 0)
 {
+    if constexpr (sizeof(R) == 4)
+        if (L == 24 && tau == 2 && nz == 3) return slab_kernel<R, 24, 2, 3>;
     switch (L) {
     case 16: return slab_kernel<R, 16>;
     case 24: return slab_kernel<R, 24>;
@@ -439,7 +450,7 @@ cudaError_t slab_plan(const Geo& g, int tau, int force_cluster, int* cluster, in
     int nt = ((Ph + 31) / 32) * 32; // one half index per thread in each class
     nt = nt > 1024 ? 1024 : nt;
     const size_t smem = slab_smem_bytes<R>(g.L, nz, tau);
-    auto fn = slab_kernel_for<R>(g.L);
+    auto fn = slab_kernel_for<R>(g.L, tau, nz);
     auto fnj = slab_jobs_kernel_for<R>(g.L);
     // the attribute is an upper bound shared by every shape that uses this kernel instance:
     // the device's opt-in maximum, so that no later plan lowers it below another's need
@@ -510,7 +521,7 @@ cudaError_t launch_slab(const Geo& g, R* theta, void* cs, const SlabArgs& a, int
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, slab_kernel_for<R>(g.L), g, theta, static_cast<cs_t<R>*>(cs), a);
+    return cudaLaunchKernelEx(&cfg, slab_kernel_for<R>(g.L, a.u.slab_t, a.nz), g, theta, static_cast<cs_t<R>*>(cs), a);
 }
 
 } // namespace ul
