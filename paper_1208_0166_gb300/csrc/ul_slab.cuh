@@ -72,6 +72,23 @@ struct SlabLinks {
         }
         return Cx<R>{v.x, v.y};
     }
+    // The same by half index hh = li >> 1 of the site in this CTA's numbering; edge: the
+    // site before the z step lies on the CTA's last (ZS > 0) or first (ZS < 0) plane, so
+    // the step leaves the CTA (the neighbour's half index is hh -+ Ph).
+    template <int ZS>
+    __device__ __forceinline__ Cx<R> ldh(int dir, int tl, int hh, int par, bool edge) const
+    {
+        const int base = (slot(dir, tl) * 2 + par) * Ph();
+        cs_t<R> v;
+        if constexpr (ZS > 0) {
+            v = edge ? up[base + hh - Ph()] : own[base + hh];
+        } else if constexpr (ZS < 0) {
+            v = edge ? dn[base + hh + Ph()] : own[base + hh];
+        } else {
+            v = own[base + hh];
+        }
+        return Cx<R>{v.x, v.y};
+    }
 };
 
 // Local-index offsets of the +1 / -1 steps from site (x, y) (periodic in x and y; a z step
@@ -98,23 +115,53 @@ struct SlabSteps {
     }
 };
 
+// Half-index offsets of the +1 / -1 steps from site (x, y): a step s of the local index li
+// moves the half index h = li >> 1 to (li + s) >> 1 = h + ((b + s) >> 1), b = x & 1, so an
+// even step (in y or z) moves it by s / 2 and two steps add their offsets (at most one of
+// them in x).  A z step moves it by L^2 / 2 (leaving the CTA on its edge planes).
+struct SlabHalfSteps {
+    int xu, xd, yu, yd, zs;
+    __device__ __forceinline__ SlabHalfSteps(int x, int y, int L)
+    {
+        const int b = x & 1;
+        xu = x == L - 1 ? (b - (L - 1)) >> 1 : (b + 1) >> 1;
+        xd = x == 0 ? (b + L - 1) >> 1 : (b - 1) >> 1;
+        yu = y == L - 1 ? -(L - 1) * L / 2 : L / 2;
+        yd = y == 0 ? (L - 1) * L / 2 : -L / 2;
+        zs = L * L / 2;
+    }
+    template <int D>
+    __device__ __forceinline__ int up() const
+    {
+        return D == 0 ? 0 : (D == 1 ? xu : (D == 2 ? yu : zs));
+    }
+    template <int D>
+    __device__ __forceinline__ int dn() const
+    {
+        return D == 0 ? 0 : (D == 1 ? xd : (D == 2 ? yd : -zs));
+    }
+};
+
+// One plane's staple contribution by half indices (the loads of slab_staple_term):
+// zup / zdn: the site lies on the CTA's last / first z plane.
 template <typename R, int LC, int TC, int NZC, int MU, int NU>
-__device__ __forceinline__ void slab_staple_term(Cx<R>& A, const SlabLinks<R, LC, TC, NZC>& S, const SlabSteps& st, int tl,
-                                                 int li, int p)
+__device__ __forceinline__ void slab_staple_term_h(Cx<R>& A, const SlabLinks<R, LC, TC, NZC>& S,
+                                                   const SlabHalfSteps& hs, int tl, int h, int p, bool zup, bool zdn)
 {
     constexpr int ZM = MU == 3 ? 1 : 0;
     constexpr int ZN = NU == 3 ? 1 : 0;
     constexpr int TM = MU == 0 ? 1 : 0;
     constexpr int TN = NU == 0 ? 1 : 0;
+    constexpr int ZD = ZM - ZN; // z step of the diagonal site x + mu - nu
     const int q = p ^ 1;
-    const int li_mu = li + st.up<MU>();
-    const int li_nu = li + st.up<NU>();
-    const int li_nd = li + st.dn<NU>();
-    const int li_dg = li_mu + st.dn<NU>();
-    staple_acc_fwd(A, S.template ld<ZM>(NU, tl + TM, li_mu, q), S.template ld<ZN>(MU, tl + TN, li_nu, q),
-                   S.template ld<0>(NU, tl, li, p));
-    staple_acc_bwd(A, S.template ld<ZM - ZN>(NU, tl + TM - TN, li_dg, p), S.template ld<-ZN>(MU, tl - TN, li_nd, q),
-                   S.template ld<-ZN>(NU, tl - TN, li_nd, q));
+    const int h_mu = h + hs.up<MU>();
+    const int h_nu = h + hs.up<NU>();
+    const int h_nd = h + hs.dn<NU>();
+    const int h_dg = h_mu + hs.dn<NU>();
+    staple_acc_fwd(A, S.template ldh<ZM>(NU, tl + TM, h_mu, q, zup), S.template ldh<ZN>(MU, tl + TN, h_nu, q, zup),
+                   S.template ldh<0>(NU, tl, h, p, false));
+    staple_acc_bwd(A, S.template ldh<ZD>(NU, tl + TM - TN, h_dg, p, ZD > 0 ? zup : zdn),
+                   S.template ldh<-ZN>(MU, tl - TN, h_nd, q, zdn), S.template ldh<-ZN>(NU, tl - TN, h_nd, q, zdn));
 }
 
 // Global offset in [dir][parity][h] of link dir at site (x, y, zg, tg).
@@ -132,6 +179,7 @@ __device__ __forceinline__ int slab_class(const SlabLinks<R, LC, TC, NZC>& S, R*
                                           int t0, int p, bool metro, uint64_t pass, const UpdateArgs& a)
 {
     const int Lh = L / 2, tau = S.tau(), Ph = S.Ph();
+    const int nz = S.P() / (L * L);
     const int nsl = MU == 0 ? tau : tau - 1;
     int accepted = 0;
     for (int hl = static_cast<int>(threadIdx.x); hl < Ph; hl += static_cast<int>(blockDim.x)) {
@@ -142,13 +190,13 @@ __device__ __forceinline__ int slab_class(const SlabLinks<R, LC, TC, NZC>& S, R*
         for (int sl = 0; sl < nsl; ++sl) {
             const int tl = MU == 0 ? sl : sl + 1;
             const int x = 2 * xh + ((p + y + z0 + zl + t0 + tl) & 1);
-            const int li = x + L * (y + L * zl);
-            const SlabSteps st(x, y, L);
+            const SlabHalfSteps hs(x, y, L);
+            const bool zup = zl == nz - 1, zdn = zl == 0;
             Cx<R> A{R(0), R(0)};
-            if (MU != 0) slab_staple_term<R, LC, TC, NZC, MU, 0>(A, S, st, tl, li, p);
-            if (MU != 1) slab_staple_term<R, LC, TC, NZC, MU, 1>(A, S, st, tl, li, p);
-            if (MU != 2) slab_staple_term<R, LC, TC, NZC, MU, 2>(A, S, st, tl, li, p);
-            if (MU != 3) slab_staple_term<R, LC, TC, NZC, MU, 3>(A, S, st, tl, li, p);
+            if (MU != 0) slab_staple_term_h<R, LC, TC, NZC, MU, 0>(A, S, hs, tl, hl, p, zup, zdn);
+            if (MU != 1) slab_staple_term_h<R, LC, TC, NZC, MU, 1>(A, S, hs, tl, hl, p, zup, zdn);
+            if (MU != 2) slab_staple_term_h<R, LC, TC, NZC, MU, 2>(A, S, hs, tl, hl, p, zup, zdn);
+            if (MU != 3) slab_staple_term_h<R, LC, TC, NZC, MU, 3>(A, S, hs, tl, hl, p, zup, zdn);
             const int ph_idx = (S.slot(MU, tl) * 2 + p) * Ph + hl;
             const int th_slot = MU == 0 ? tl : tau + (MU - 1) * (tau - 1) + tl - 1;
             const int th_idx = (th_slot * 2 + p) * Ph + hl;
