@@ -706,8 +706,9 @@ int ul_init_ex(ul_lattice** out, int L, int Nt, double beta, uint64_t seed, int 
     // graph replay measured faster on GB300 than the persistent kernel with grid barriers
     // (24^4, 100 sweeps: 5.05 against 6.43 us per FP32 class)
     h->use_persistent = false;
-    // programmatic dependent launch: measured faster for FP32 classes (4.94 -> 4.60 us at 24^4)
-    // and slower for FP64 classes (51.8 -> 56.5 us), so on by default for FP32 only
+    // programmatic dependent launch: measured faster for FP32 classes (4.94 -> 4.60 us at 24^4);
+    // for FP64 faster in compound sweeps and slower in the sub-sample passes (which alternate
+    // with measurements), so there mode 2 (compound sweeps only)
     h->use_pdl = precision == UL_FP32_ACC64 ? 1 : 2;
     // slab-resident sub-samples: measured faster for FP32 at 24^4 (step 57.4 -> 49.8 ms); the
     // FP64 form is bound by the FP64 pipe and a cluster form leaves a third of the SMs idle
