@@ -353,6 +353,11 @@ __global__ void __launch_bounds__(kContractItems, kContractBlocksPerSM)
 // instructions.
 // ---------------------------------------------------------------------------
 constexpr int kDsBatch = 4;
+// Threads per block of the double-single kernel: small blocks (2 L ny kd threads, at most
+// kDsItems) that fit beside the FP64 class updates of the next chunk (a full 24^4 class holds
+// about 50 K of an SM's 64 K registers), so that the contraction on the FP32 pipes runs
+// during the FP64-pipe-bound updates instead of between them.
+constexpr int kDsItems = 96;
 
 // Paired FP32 arithmetic on (re, im) lanes (FFMA2 / FADD2 / FMUL2: two IEEE single
 // operations per instruction, each lane rounded as the scalar operation would be).
@@ -603,7 +608,7 @@ bool launch_contract_tiled(const Geo& g, int S, int r_max, int nd, int count, co
                            long long wait_cycles)
 {
     if constexpr (sizeof(R) == 8) {
-        const ContractTile t = contract_tile_ds(g, r_max, nd, kContractItems, kContractSmem);
+        const ContractTile t = contract_tile_ds(g, r_max, nd, kDsItems, kContractSmem);
         if (sym || !t.ok || count < 1 || (t.smem > 48 * 1024 && !g_contract_prepared<R>.load())) return false;
         const long blocks = static_cast<long>(S) * g.L * t.ytiles * t.groups * t.dsubs;
         insertion_contract_ds_kernel<double><<<static_cast<unsigned int>(blocks), t.threads, t.smem, st>>>(
