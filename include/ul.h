@@ -311,7 +311,8 @@ int ul_free(ul_lattice* h);
  *                  A staging-copy wait that reaches its time limit (about a second) is
  *                  reported as UL_ETIMEOUT by the level's result call.
  *   "copy_stall_test"  0 (default), or n > 0 (integer <= 2e9): a test of the timeout path
- *                  of the tiled contraction.  Each block's first staged batch then waits for
+ *                  of the tiled contraction (the FP32 kernel of UL_FP32_ACC64 and the
+ *                  double-single kernel of UL_FP64).  Each block's first staged batch then waits for
  *                  16 bytes more than its copies deliver, so that wait gives up after n SM
  *                  cycles; the block reports the timeout, waits (up to the full limit, about
  *                  a second) while the copies it issued land, and leaves.  The level fails
