@@ -293,8 +293,9 @@ int ul_free(ul_lattice* h);
  *                  A size whose slab share does not fit falls back to one launch per class.
  *   "insertion_chunk_mb"  bound (MiB, default 16384) on the buffers that hold the
  *                  per-sample transporters and channel sums between insertion contractions
- *                  (a level is contracted in chunks of a quarter of its sub-samples but at
- *                  least 48, smaller where the bound requires; in the slab-resident form one chunk's
+ *                  (UL_FP32_ACC64: a level is contracted in chunks of a quarter of its
+ *                  sub-samples but at least 48; UL_FP64: in one chunk; smaller where the
+ *                  bound requires; in the slab-resident form one chunk's
  *                  contraction overlaps the next chunk's updates); fewer MiB means more,
  *                  smaller contractions (results change only by rounding)
  *   "contract_tiled"  1 (default): the insertion contraction runs in a tiled form (per

@@ -337,14 +337,17 @@ int check_device_status(ul_lattice* h)
 // contraction launch has a fixed cost, the FP64 read-modify-write of the field sums: with
 // fewer samples the overlapped contractions fall behind the slab-resident updates, and a
 // level of fewer samples is contracted once), bounded so that two chunk buffers fit into
-// the option "insertion_chunk_mb".  The same chunks in every launch mode, so that the
-// modes give the same sums.
+// the option "insertion_chunk_mb".  FP64 links: the whole level (the double-single
+// contraction does not run beside the FP64 updates, which hold the SMs, so chunks would only
+// add epilogues and read-modify-writes of the sums), within the same bound.  The same
+// chunks in every launch mode, so that the modes give the same sums.
 constexpr int kMinChunkSamples = 48;
 
 int chunk_samples(const ul_lattice* h, int n_sub, size_t per_sample)
 {
     const size_t cap = (static_cast<size_t>(h->chunk_mb) << 20) / 2;
-    const size_t quarter = std::max<size_t>((static_cast<size_t>(n_sub) + 3) / 4, kMinChunkSamples);
+    const size_t quarter = is_f64(h) ? static_cast<size_t>(n_sub)
+                                     : std::max<size_t>((static_cast<size_t>(n_sub) + 3) / 4, kMinChunkSamples);
     return static_cast<int>(std::max<size_t>(1, std::min<size_t>({quarter, static_cast<size_t>(n_sub), cap / per_sample})));
 }
 
